@@ -1,0 +1,163 @@
+"""The augmented subspace iteration, step by step (Alg. 1, Alg. 2, Alg. 3 of the paper).
+
+One iteration ("Correction", Alg. 1; steps 3-6 of Alg. 3), with U = [u_1..u_m] the
+current block and Lambda its Ritz values:
+
+ (a) linear solve   A_h w_i = lambda_i M_h u_i from the initial guess u_i     (Alg. 3 step 3)
+ (b) projection     aH = P^T A_h W, bH = P^T M_h W, GA = W^T A_h W, GM = W^T M_h W
+                    (the blocks a_h, b_h, alpha, beta of Alg. 3 step 4)
+ (c) augmented eig  [[A_H, aH],[aH^T, GA]] c = lambda [[M_H, bH],[bH^T, GM]] c,
+                    the m smallest pairs, B-normalised                        (Alg. 3 step 5)
+ (d) prolongation   U <- P C_H + W C_W                                        (Alg. 3 step 6)
+
+Readings taken where the paper is silent or garbled:
+* Alg. 3 step 6 prints the product as gamma u-hat; the shapes (N x k times k x k)
+  force u-hat gamma, i.e. W C_W.
+* One linear-solve phase per Rayleigh-Ritz (Alg. 1); the post-solve of Alg. 3 step 7
+  is folded into the next iteration's step 3.
+* Vectors are M-normalised (U^T M U = I) rather than a(u,u) = 1; the two differ by the
+  factor sqrt(lambda) per column.
+* Convergence is ||A u - lambda M u||_2 / (lambda ||M u||_2) <= tol for the first nev
+  columns (the paper's §6 criterion divides by |lambda| only).
+* With a random start the first iteration skips step (a) and uses W = U0, which gives
+  coarse-quality Ritz pairs at once.
+"""
+import numpy as np
+import scipy.linalg as sl
+
+from .mg import Hierarchy, cg
+
+
+def relative_residuals(A, M, U, lam):
+    """||A u_i - lam_i M u_i||_2 / (lam_i ||M u_i||_2) for every column."""
+    AU = A @ U
+    MU = M @ U
+    R = AU - MU * lam
+    return np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(MU, axis=0))
+
+
+def rayleigh_quotients(A, M, U):
+    return np.einsum("ij,ij->j", U, A @ U) / np.einsum("ij,ij->j", U, M @ U)
+
+
+def linear_solve(A, M, U, lam, s, hier=None, solver="vcycle"):
+    """Step (a): W with A W = M U Lambda approximately, initial guess U.
+
+    V-cycle form: correction E from s V-cycles on A E = M U Lambda - A U, E0 = 0, then
+    W = U + E (the same iterate as s V-cycles from the initial guess U).
+    CG form: s CG steps per column from the initial guess U.
+    """
+    F = (M @ U) * lam
+    if solver == "vcycle":
+        R = F - A @ U
+        E = hier.solve(R, s)
+        return U + E
+    return cg(A, F, U, s)
+
+
+def projection(A, M, P, W):
+    """Step (b): aH = P^T A W, bH = P^T M W, GA = W^T A W, GM = W^T M W."""
+    AW = A @ W
+    MW = M @ W
+    return P.T @ AW, P.T @ MW, W.T @ AW, W.T @ MW
+
+
+def augmented_pencil(A_H, M_H, aH, bH, GA, GM):
+    """The composite matrices A_Hh, B_Hh of Alg. 3 step 4, dense."""
+    Ahat = np.block([[A_H.toarray(), aH], [aH.T, GA]])
+    Bhat = np.block([[M_H.toarray(), bH], [bH.T, GM]])
+    return 0.5 * (Ahat + Ahat.T), 0.5 * (Bhat + Bhat.T)
+
+
+def augmented_eig(A_H, M_H, aH, bH, GA, GM, m):
+    """Step (c): the m smallest pairs of the augmented pencil (dense LAPACK).
+
+    Returns (lam[m], C_H[N_H][m], C_W[m][m]) with [C_H; C_W] B_Hh-orthonormal.
+    """
+    Ahat, Bhat = augmented_pencil(A_H, M_H, aH, bH, GA, GM)
+    lam, Y = sl.eigh(Ahat, Bhat, subset_by_index=[0, m - 1])
+    NH = A_H.shape[0]
+    return lam, Y[:NH], Y[NH:]
+
+
+def precond_a(A_H, M_H, aH, bH, GA, GM):
+    """PRECOND-A (§4, Alg. 5 step 1): the congruence with [[I, A_H^-1 aH],[0, I]].
+
+    Returns (ahat, alpha_t, b_t, beta_t) where ahat = A_H^-1 aH,
+    alpha_t = GA - ahat^T aH, b_t = bH - M_H ahat,
+    beta_t = GM - bH^T ahat - ahat^T bH + ahat^T M_H ahat.
+    The transformed pencil is [[A_H, 0],[0, alpha_t]], [[M_H, b_t],[b_t^T, beta_t]].
+    """
+    ahat = sl.cho_solve(sl.cho_factor(A_H.toarray()), aH)
+    alpha_t = GA - ahat.T @ aH
+    b_t = bH - M_H @ ahat
+    beta_t = GM - bH.T @ ahat - ahat.T @ bH + ahat.T @ (M_H @ ahat)
+    return ahat, alpha_t, b_t, beta_t
+
+
+def precond_a_back(ahat, uH_t, gamma_t):
+    """Alg. 5 step 3: u_H = u~_H - ahat gamma~, gamma = gamma~."""
+    return uH_t - ahat @ gamma_t, gamma_t
+
+
+def prolongate(P, W, C_H, C_W):
+    """Step (d): U = P C_H + W C_W."""
+    return P @ C_H + W @ C_W
+
+
+def coarse_start(A_H, M_H, P, m):
+    """Alg. 3 steps 1-2: coarse eigenpairs, interpolated to the fine space."""
+    lam, UH = sl.eigh(A_H.toarray(), M_H.toarray(), subset_by_index=[0, m - 1])
+    return lam, P @ UH
+
+
+class Solver:
+    """The whole method (Alg. 2 / Alg. 3) on one pencil, dense step (c)."""
+
+    def __init__(self, A, M, chain, coarse_level=None, omega=2.0 / 3.0, nu1=2, nu2=2):
+        self.A, self.M = A.tocsr(), M.tocsr()
+        self.chain = chain
+        self.coarse_level = len(chain) if coarse_level is None else coarse_level
+        P = None
+        for k in range(self.coarse_level):
+            P = chain[k] if P is None else P @ chain[k]
+        self.P = P.tocsr()
+        self.hier = Hierarchy(self.A, chain, omega, nu1, nu2)
+        self.A_H = (self.P.T @ self.A @ self.P).tocsr()
+        self.M_H = (self.P.T @ self.M @ self.P).tocsr()
+
+    def iteration(self, U, lam, s, solve=True, solver="vcycle"):
+        """One augmented subspace iteration; returns (lam, U, intermediates)."""
+        m = U.shape[1]
+        W = linear_solve(self.A, self.M, U, lam, s, self.hier, solver) if solve else U
+        aH, bH, GA, GM = projection(self.A, self.M, self.P, W)
+        lam_new, C_H, C_W = augmented_eig(self.A_H, self.M_H, aH, bH, GA, GM, m)
+        U_new = prolongate(self.P, W, C_H, C_W)
+        return lam_new, U_new, dict(W=W, aH=aH, bH=bH, GA=GA, GM=GM, C_H=C_H, C_W=C_W)
+
+    def solve(self, nev, m, tol, U0=None, s=2, max_iter=100, solver="vcycle"):
+        """Iterate from U0 (random start, first step (a) skipped) or from the coarse
+        start until the first nev relative residuals are <= tol."""
+        if U0 is None:
+            lam, U = coarse_start(self.A_H, self.M_H, self.P, m)
+            first_solve = True
+        else:
+            U, lam = U0, None
+            first_solve = False
+        history = []
+        it = 0
+        for it in range(1, max_iter + 1):
+            lam, U, _ = self.iteration(U, lam, s, solve=first_solve or it > 1, solver=solver)
+            res = relative_residuals(self.A, self.M, U, lam)
+            history.append(res.copy())
+            if np.all(res[:nev] <= tol):
+                break
+        return lam, U, dict(iterations=it, history=history, converged=bool(np.all(history[-1][:nev] <= tol)))
+
+
+def normalise_signs(U):
+    """Flip each column so that its largest-|entry| (lowest index on ties) is positive."""
+    idx = np.argmax(np.abs(U), axis=0)
+    s = np.sign(U[idx, np.arange(U.shape[1])])
+    s[s == 0] = 1.0
+    return U * s
