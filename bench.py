@@ -1,0 +1,307 @@
+#!/usr/bin/env python
+"""Benchmark of the augmented subspace iteration on one GB300.
+
+Workload: 3D Laplace on the unit cube, trilinear Q1 elements on a uniform 128^3 mesh
+(127^3 = 2,048,383 interior DOFs, 27 nonzeros per row), nested 16^3 coarse mesh
+(3,375 DOFs), nev = 50 (block width 56), FP64 block multigrid (2 V-cycles of damped
+Jacobi, 2+2 sweeps, Galerkin levels 128/64/32/16/8/4), seeded random start block.
+
+A step is one augmented subspace iteration (residual, step (a) linear solve, step (b)
+projection, step (c) augmented eigensolve, step (d) prolongation) on that workload.
+value = DOF*nev per second (N_h * nev / step time), summed over ranks.
+
+Extra keys: the whole solve to relative residual 1e-8 in FP64 and in the mixed form
+(FP32 V-cycle inside FP64 refinement) with the speedup per converged eigenpair, the
+roofline of the hot sparse kernel, the oracle timed on the host cores (cpu_baseline),
+and an end-to-end number through the C ABI with host buffers.
+
+--impl reference times the FP64 CPU oracle (one oracle iteration per step) instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D, NFINE, NCOARSE, NEV, SEED = 3, 128, 16, 50, 0
+WORKLOAD = "laplace3d_q1_128_coarse16_nev50"
+METRIC = "DOF*nev/s per augmented-subspace iteration (3D Q1 128^3, nev 50, FP64)"
+UNIT = "DOF*nev/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_workload():
+    import pase_inputs as pin
+    pb = pin.build_problem(D, NFINE, NCOARSE, mg_min=4)
+    m = pin.guard_columns(NEV)
+    return pb, m
+
+
+def cpu_oracle_iteration_seconds(pb, m, steps=1, warmup=0):
+    """The oracle as it stands: one augmented subspace iteration per step on the full
+    workload (random start; the timed steps run the linear solve)."""
+    import numpy as np
+    import pase_inputs as pin
+    from oracle import pase as opase
+    S = opase.Solver(pb.A, pb.M, pb.chain, coarse_level=pb.coarse_level)
+    U = pin.start_vectors(SEED, pb.N, m)
+    lam, U, _ = S.iteration(U, None, 2, solve=False)
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        lam, U, _ = S.iteration(U, lam, 2, solve=True)
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    return times
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    pb, m = build_workload()
+    times = cpu_oracle_iteration_seconds(pb, m, steps=args.steps, warmup=args.warmup)
+    t = max(1e-12, sum(times) / len(times))
+    value = pb.N * NEV / t
+    sample = "one oracle augmented subspace iteration (full 128^3 workload, nev 50, block 56) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Q1 matrices, SplitMix64 start block)",
+            "config": {"workload": WORKLOAD, "N_h": pb.N, "N_H": pb.N_H, "nev": NEV, "block": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import pase_inputs as pin
+    from paper_2502_04589_gb300 import pase as P
+
+    rank, world, local = _env_rank()
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    pb, m = build_workload()
+
+    def make(precision):
+        opt = P.pase_default_options()
+        opt.precision = precision
+        opt.coarse_level = pb.coarse_level
+        h = P.pase_create(opt, stream.cuda_stream)
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        P.pase_reserve(h, m)
+        return h
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    h = make(P.PASE_PREC_FP64)
+    U0h = pin.start_vectors(SEED + rank, pb.N, m)
+    U0 = torch.from_numpy(U0h).cuda()
+    U = U0.clone()
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    relres = torch.zeros(m, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        P.pase_iterate(h, m, U, lam, False)  # first iteration: W = U0
+        for _ in range(args.warmup):
+            P.pase_iterate(h, m, U, lam, True, relres)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    k0 = P.pase_kernel_count(h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        P.pase_iterate(h, m, U, lam, True, relres)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = (P.pase_kernel_count(h) - k0) // max(1, args.steps)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * pb.N * NEV / (ms * 1e-3)
+
+    # dominant-kernel roofline: the fused A_h / M_h product (one pass over the pattern)
+    X = U.clone()
+    AX, MX = torch.empty_like(X), torch.empty_like(X)
+    reps = 10
+    for _ in range(3):
+        P.pase_spmm_am(h, m, X, AX, MX)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        P.pase_spmm_am(h, m, X, AX, MX)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmm_ms = e0.elapsed_time(e1) / reps
+    nnz = pb.A.nnz
+    spmm_flops = 4.0 * nnz * m
+    spmm_bytes = nnz * (4 + 16) + 8 * (pb.N + 1) + 3 * pb.N * m * 8
+    peak_fp64 = 1.25e12
+    roofline = {"bound": "alu", "kernel": "k_csr<double, MV_AM> (fused A_h/M_h SpMM, FP64)",
+                "achieved": spmm_flops / (spmm_ms * 1e-3) / 1e12, "peak": peak_fp64 / 1e12,
+                "unit": "TFLOP/s", "frac": spmm_flops / (spmm_ms * 1e-3) / peak_fp64,
+                "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)",
+                "algorithmic_bytes": spmm_bytes,
+                "achieved_gbs": spmm_bytes / (spmm_ms * 1e-3) / 1e9, "ms": spmm_ms}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()
+    lh = torch.from_numpy(lam.cpu().numpy()).pin_memory()
+    rh = torch.zeros(m, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.pase_iterate(h, m, Uh.numpy(), lh.numpy(), True, rh.numpy())
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world * pb.N * NEV / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(pb.N * m * 8 + m * 8),
+           "d2h_bytes_per_step": int(pb.N * m * 8 + 2 * m * 8)}
+    P.pase_destroy(h)
+
+    # whole solve to 1e-8, FP64 and mixed
+    solves = {}
+    if not args.no_solve:
+        for name, prec in (("fp64", P.PASE_PREC_FP64), ("mixed", P.PASE_PREC_MIXED)):
+            hs = make(prec)
+            Uo = torch.empty_like(U0)
+            lo = torch.empty(m, dtype=torch.float64, device="cuda")
+            barrier()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            rc, st = P.pase_solve(hs, NEV, 1e-8, m, U0, lo, Uo)
+            s1.record(stream)
+            barrier()
+            sec = s0.elapsed_time(s1) * 1e-3
+            solves[name] = {"status": rc, "iterations": st["iterations"], "seconds": sec,
+                            "max_relres": st["max_residual"], "dof_nev_per_s": pb.N * NEV / sec,
+                            "ms_per_iteration": 1e3 * sec / max(1, st["iterations"]),
+                            "phase_ms": st["phase_ms"], "aug_iterations": st["aug_iterations"]}
+            if name == "fp64":
+                lam_fp64 = lo[:NEV].cpu().numpy()
+            else:
+                lam_mixed = lo[:NEV].cpu().numpy()
+            P.pase_destroy(hs)
+        if "fp64" in solves and "mixed" in solves:
+            solves["mixed_speedup_per_converged_pair"] = solves["fp64"]["seconds"] / solves["mixed"]["seconds"]
+            solves["mixed_vs_fp64_max_rel_eig_diff"] = float(np.max(np.abs(lam_mixed - lam_fp64) / lam_fp64))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        times = cpu_oracle_iteration_seconds(pb, m, steps=1)
+        cpu = {"value": pb.N * NEV / times[0], "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": "one oracle augmented subspace iteration on the full 128^3 workload (nev 50, block 56)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Q1 matrices, SplitMix64 start block)",
+                "config": {"workload": WORKLOAD, "N_h": pb.N, "nnz": pb.A.nnz, "N_H": pb.N_H, "nev": NEV,
+                           "block": m, "linear_solve": "2 V-cycles, damped Jacobi 2+2, omega 2/3",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (block 0.92 GB)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "solve": solves}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * pase.h - C ABI of a GB300 (sm_103a) implementation of the augmented subspace
+ * eigensolver of Liao, Liu, Xie and Wang, "PASE: A Massively Parallel Augmented
+ * Subspace Eigensolver for Large Scale Eigenvalue Problems" (arXiv 2502.04589).
+ *
+ * Problem (paper §2.1, §3 Alg. 3 "Require/Ensure"): the nev smallest eigenpairs of the
+ * symmetric-definite pencil A_h u = lambda M_h u (M_h is the paper's B_h), given a
+ * coarse space V_H subset V_h through an interpolation chain P (the paper's I_H^h; its
+ * transpose is the restriction I_h^H) and the coarse pencil (A_H, M_H).
+ *
+ * One augmented subspace iteration (Alg. 1; Alg. 3 steps 3-6) on the block U [N][m]:
+ *   (a) W  = linear solve of A_h w_i = lambda_i M_h u_i from the guess u_i   (pase_linear_solve)
+ *   (b) aH = P^T A_h W, bH = P^T M_h W, GA = W^T A_h W, GM = W^T M_h W      (pase_project)
+ *   (c) the m smallest pairs of [[A_H, aH],[aH^T, GA]], [[M_H, bH],[bH^T, GM]] (pase_augmented_eig)
+ *   (d) U  = P C_H + W C_W                                                  (pase_prolongate)
+ * with the residual R = M_h U Lambda - A_h U and the relative residuals
+ * ||A u - lambda M u||_2 / (lambda ||M u||_2) feeding (a) and the stopping test (pase_residual).
+ *
+ * Conventions for every call:
+ *  - Return value: PASE_OK (0) or a negative PASE_ERR_* code; no call aborts, traps or
+ *    throws.  pase_status_string() names a code; pase_last_error() gives a message.
+ *  - Multivectors are dense, row-major ("node-major"): element (i, j) of an [N][m]
+ *    block is at p[i*m + j]; the m entries of one node are contiguous.  m is the block
+ *    width nev_w (nev plus guard columns) and must be a multiple of 8 and at most 256.
+ *  - Pointers to multivectors, lambda and small matrices may be device or host
+ *    memory; the library detects which (cudaPointerGetAttributes).  Host inputs are
+ *    copied in and host outputs copied back inside the call, on the handle's stream.
+ *  - All device work runs on the CUDA stream given to pase_create; calls return after
+ *    the stream has been synchronised, so outputs are ready on return.
+ *  - Borrowed inputs are only read during the call.  The handle owns all of its device
+ *    memory (pase_setup, pase_reserve) and frees it in pase_destroy.
+ */
+#ifndef PASE_H
+#define PASE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------------- */
+#define PASE_OK 0
+#define PASE_ERR_INVALID_ARG (-1)      /* null pointer, bad size, m not a multiple of 8 ...  */
+#define PASE_ERR_SHAPE_MISMATCH (-2)   /* matrix shapes do not chain                           */
+#define PASE_ERR_PATTERN_MISMATCH (-3) /* A_h and M_h (or A_H, M_H) differ in sparsity pattern */
+#define PASE_ERR_NOT_SPD (-4)          /* a Cholesky pivot was not positive                   */
+#define PASE_ERR_NAN (-5)              /* a NaN / Inf was produced or given                    */
+#define PASE_ERR_NOT_CONVERGED (-6)    /* max_iter reached; outputs are still written          */
+#define PASE_ERR_TIMEOUT (-7)          /* a device-side wait exceeded its limit                */
+#define PASE_ERR_CUDA (-8)             /* a CUDA runtime call failed                           */
+#define PASE_ERR_OUT_OF_MEMORY (-9)    /* device allocation failed                             */
+#define PASE_ERR_STATE (-10)           /* call out of order (e.g. solve before setup)          */
+#define PASE_ERR_BAD_CSR (-11)         /* row pointers not monotone, column out of range/unsorted */
+
+/* ---- options ------------------------------------------------------------------------ */
+#define PASE_PREC_FP64 0  /* every step in FP64                                            */
+#define PASE_PREC_MIXED 1 /* step (a) in FP32 storage and arithmetic inside FP64 residual
+                             correction (w = u + V32(r64)); (b)-(d) and residuals in FP64  */
+
+#define PASE_SOLVER_VCYCLE 0 /* s V-cycles: damped Jacobi, Galerkin levels, dense coarsest */
+#define PASE_SOLVER_CG 1     /* s CG steps per column                                        */
+
+typedef struct {
+  int precision;       /* PASE_PREC_FP64 (default) or PASE_PREC_MIXED                          */
+  int linear_solver;   /* PASE_SOLVER_VCYCLE (default) or PASE_SOLVER_CG                       */
+  int inner_steps;     /* s: V-cycles / CG steps per iteration (default 2)                     */
+  int nu1, nu2;        /* damped-Jacobi pre / post sweeps (default 2, 2)                       */
+  double omega;        /* Jacobi damping (default 2/3)                                         */
+  int coarse_level;    /* level of the P chain that is V_H; -1 (default) = the last level      */
+  int max_iter;        /* outer iterations (default 100)                                       */
+  int aug_max_iter;    /* inner iterations of the step-(c) block eigensolver (default 60)      */
+  double aug_tol;      /* inner relative residual target (default 1e-13)                       */
+  int verbose;         /* 0 silent, 1 per-iteration line on stderr                             */
+} pase_options;
+
+/* Per-solve statistics (all times in milliseconds, device-event timed). */
+typedef struct {
+  int iterations;        /* outer augmented subspace iterations                                */
+  int converged;         /* how many of the first nev pairs met tol                            */
+  double max_residual;   /* largest relative residual among the first nev                      */
+  double solve_ms;       /* whole pase_solve                                                   */
+  double phase_ms[5];    /* (a) linear solve, (b) projection, (c) augmented eig, (d) prolongation,
+                            residual/convergence                                              */
+  int aug_iterations;    /* inner block-eigensolver iterations, summed                         */
+  int kernel_launches;   /* library kernels launched                                           */
+} pase_stats;
+
+/* Sparse matrix in CSR (borrowed).  rowptr has nrows+1 entries, rowptr[0] = 0;
+ * colind is sorted ascending inside each row.  Values are FP64. */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+  int on_device; /* 0: the three arrays are host memory, 1: device memory */
+} pase_csr;
+
+typedef struct pase_ctx* pase_handle;
+
+/* Fill *opt with the defaults above. */
+void pase_default_options(pase_options* opt);
+
+/* Create a handle that runs on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current device.  *opt is copied; NULL means defaults. */
+int pase_create(pase_handle* h, const pase_options* opt, void* cuda_stream);
+
+/* Alg. 3 "Require": fine pencil (A_h, M_h), the interpolation chain and the coarse pencil.
+ * P[k] (k = 0..n_interp-1) interpolates level k+1 to level k, level 0 being V_h; their
+ * product P[0] P[1] ... P[c-1], c = coarse_level, is I_H^h (§3: "a sequence of
+ * interpolation matrices").  Levels below c serve the multigrid solver only.  A_H and
+ * M_H live on level c.  A_h and M_h must share one sparsity pattern (as do A_H, M_H).
+ * Setup validates the CSR arrays, builds the Galerkin multigrid levels
+ * A_{k+1} = P[k]^T A_k P[k], the direct interpolation I_H^h and its transpose, a dense
+ * inverse of the coarsest multigrid operator, and uploads everything to the device. */
+int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_interp,
+               const pase_csr* P, const pase_csr* A_H, const pase_csr* M_H);
+
+/* Allocate the workspace for block width m (done implicitly by the calls below). */
+int pase_reserve(pase_handle h, int m);
+
+/* Solve for the nev smallest pairs to relative residual tol (Alg. 2 / Alg. 3).
+ * U0: the start block [N][m] (m = the block width; row-major) or NULL for the coarse
+ * start of Alg. 3 steps 1-2.  A given U0 makes the first iteration skip step (a).
+ * m: block width (multiple of 8, >= nev + 1); 0 = nev + max(4, ceil(nev/10)) rounded up to 8.
+ * lambda [m] and U [N][m] receive the Ritz values (ascending) and M_h-orthonormal
+ * vectors; the first nev are the result.  st may be NULL.
+ * Returns PASE_ERR_NOT_CONVERGED (outputs written) if max_iter is reached. */
+int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, double* lambda,
+               double* U, pase_stats* st);
+
+/* ---- the steps of one iteration, for callers that drive the loop themselves ---------- */
+
+/* Residual block R = M_h U diag(lambda) - A_h U and relres[j] =
+ * ||A u_j - lambda_j M u_j||_2 / (lambda_j ||M u_j||_2).  R may be NULL (norms only). */
+int pase_residual(pase_handle h, int m, const double* U, const double* lambda, double* R,
+                  double* relres);
+
+/* Step (a): W = U + E where E approximates A_h^-1 R after `inner_steps` V-cycles (or CG
+ * steps on A_h w = M_h u lambda from w = u), R from pase_residual. */
+int pase_linear_solve(pase_handle h, int m, const double* U, const double* lambda,
+                      const double* R, double* W);
+
+/* Step (b): aH = P^T A_h W, bH = P^T M_h W ([N_H][m]), GA = W^T A_h W, GM = W^T M_h W ([m][m]). */
+int pase_project(pase_handle h, int m, const double* W, double* aH, double* bH, double* GA,
+                 double* GM);
+
+/* Step (c): the m smallest pairs of the augmented pencil, B-orthonormal, warm-started
+ * at C_H = 0, C_W = I (§3).  Outputs lambda [m], C_H [N_H][m], C_W [m][m].
+ * aug_iters (may be NULL) receives the inner iteration count. */
+int pase_augmented_eig(pase_handle h, int m, const double* aH, const double* bH,
+                       const double* GA, const double* GM, double* lambda, double* C_H,
+                       double* C_W, int* aug_iters);
+
+/* Step (d): U = P C_H + W C_W. */
+int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H,
+                    const double* C_W, double* U);
+
+/* One whole iteration in place: residual of (U, lambda) -> relres (if not NULL), then
+ * (a) unless do_linear_solve == 0, (b), (c), (d); U and lambda are overwritten. */
+int pase_iterate(pase_handle h, int m, double* U, double* lambda, int do_linear_solve,
+                 double* relres);
+
+/* Fused A_h / M_h product on the fine level: AX = A_h X, MX = M_h X (device pointers,
+ * [N][m]).  The hot kernel of steps (b) and the residual; exposed for measurement. */
+int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
+
+/* Number of library kernels launched by this handle so far. */
+int64_t pase_kernel_count(pase_handle h);
+
+/* Release everything the handle owns.  NULL is accepted. */
+int pase_destroy(pase_handle h);
+
+const char* pase_status_string(int code);
+/* Message of the last error on this thread (empty if none). */
+const char* pase_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASE_H */

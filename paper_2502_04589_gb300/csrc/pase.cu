@@ -1,0 +1,1034 @@
+// The C ABI and the host-side driver of the augmented subspace iteration.
+//
+// pase_setup builds the device data (paper §3 Alg. 3 "Require": A_h, B_h = M_h, the
+// interpolation chain I_H^h, A_H, B_H); pase_solve runs Alg. 2 / Alg. 3 with one
+// "Correction" (Alg. 1) per outer iteration:
+//   residual   R = M U Lambda - A U, relative residuals            (convergence test, §6)
+//   (a)        W = U + V-cycles(R)  [FP64, or FP32 inside FP64 refinement]  (Alg. 3 step 3)
+//   (b)        aH = P^T A W, bH = P^T M W, GA = W^T A W, GM = W^T M W      (Alg. 3 step 4)
+//   (c)        m smallest pairs of the augmented pencil, warm start u_H = 0, gamma = I
+//              (Alg. 3 step 5; solved by a block eigensolver in the spirit of GCG_AUG,
+//              Alg. 4, with a preconditioner built from the PRECOND-A factors of §4)
+//   (d)        U = P C_H + W C_W                                             (Alg. 3 step 6)
+// Every arithmetic step is a kernel of this library; the host only sequences launches and
+// reads back m residual norms per iteration.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "pase_internal.h"
+
+namespace pase {
+const char* last_error_cstr();
+
+int dev_alloc(pase_ctx* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? PASE_ERR_OUT_OF_MEMORY : PASE_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  h->allocations.push_back(*p);
+  return PASE_OK;
+}
+
+int upload_csr(pase_ctx* h, const HostCSR& a, DevCSR& d, bool with_fp32, bool share,
+               const DevCSR* src) {
+  d.nrows = a.nrows;
+  d.ncols = a.ncols;
+  d.nnz = a.nnz();
+  if (share && src) {
+    d.rowptr = src->rowptr;
+    d.col = src->col;
+  } else {
+    PASE_TRY(dev_alloc_t(h, &d.rowptr, a.nrows + 1));
+    PASE_TRY(dev_alloc_t(h, &d.col, std::max<int64_t>(1, a.nnz())));
+    PASE_CUDA(cudaMemcpy(d.rowptr, a.rowptr.data(), sizeof(int64_t) * (a.nrows + 1), cudaMemcpyHostToDevice));
+    if (a.nnz()) PASE_CUDA(cudaMemcpy(d.col, a.col.data(), sizeof(int32_t) * a.nnz(), cudaMemcpyHostToDevice));
+  }
+  PASE_TRY(dev_alloc_t(h, &d.val, std::max<int64_t>(1, a.nnz())));
+  if (a.nnz()) PASE_CUDA(cudaMemcpy(d.val, a.val.data(), sizeof(double) * a.nnz(), cudaMemcpyHostToDevice));
+  if (with_fp32) {
+    std::vector<float> v32(a.val.begin(), a.val.end());
+    PASE_TRY(dev_alloc_t(h, &d.val32, std::max<int64_t>(1, a.nnz())));
+    if (a.nnz()) PASE_CUDA(cudaMemcpy(d.val32, v32.data(), sizeof(float) * a.nnz(), cudaMemcpyHostToDevice));
+  }
+  return PASE_OK;
+}
+
+template <typename T>
+static int upload_vec(pase_ctx* h, const std::vector<T>& v, T** d) {
+  PASE_TRY(dev_alloc_t(h, d, std::max<size_t>(1, v.size())));
+  if (!v.empty()) PASE_CUDA(cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return PASE_OK;
+}
+
+// ------------------------------------------------------------------ pointer staging
+// Inputs/outputs of the ABI may be host or device memory; host ones go through a
+// device staging buffer owned by the handle.
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Stage {
+  pase_ctx* h;
+  std::vector<std::pair<void*, std::pair<void*, size_t>>> outs;  // (dev, (host, bytes))
+  std::vector<void*> temps;
+  explicit Stage(pase_ctx* hh) : h(hh) {}
+  ~Stage() {
+    for (void* t : temps) cudaFree(t);
+  }
+  // device view of an input
+  int in(const void* p, size_t bytes, const void** dev) {
+    if (!p) {
+      *dev = nullptr;
+      return PASE_OK;
+    }
+    if (is_device_ptr(p)) {
+      *dev = p;
+      return PASE_OK;
+    }
+    void* t = nullptr;
+    PASE_CUDA(cudaMalloc(&t, std::max<size_t>(bytes, 16)));
+    temps.push_back(t);
+    PASE_CUDA(cudaMemcpyAsync(t, p, bytes, cudaMemcpyHostToDevice, h->stream));
+    *dev = t;
+    return PASE_OK;
+  }
+  // device view of an output (copied back by finish()); inout copies in as well
+  int out(void* p, size_t bytes, void** dev, bool inout = false) {
+    if (!p) {
+      *dev = nullptr;
+      return PASE_OK;
+    }
+    if (is_device_ptr(p)) {
+      *dev = p;
+      return PASE_OK;
+    }
+    void* t = nullptr;
+    PASE_CUDA(cudaMalloc(&t, std::max<size_t>(bytes, 16)));
+    temps.push_back(t);
+    if (inout) PASE_CUDA(cudaMemcpyAsync(t, p, bytes, cudaMemcpyHostToDevice, h->stream));
+    outs.push_back({t, {p, bytes}});
+    *dev = t;
+    return PASE_OK;
+  }
+  int finish() {
+    for (auto& o : outs)
+      PASE_CUDA(cudaMemcpyAsync(o.second.first, o.first, o.second.second, cudaMemcpyDeviceToHost, h->stream));
+    PASE_CUDA(cudaStreamSynchronize(h->stream));
+    return PASE_OK;
+  }
+};
+
+// ------------------------------------------------------------------ workspace
+static int reserve(pase_ctx* h, int m) {
+  if (!h->ready) return fail(PASE_ERR_STATE, "pase_setup has not completed");
+  if (m <= 0 || m % 8 != 0 || m > 256) return fail(PASE_ERR_INVALID_ARG, "block width m must be a positive multiple of 8, <= 256");
+  if (h->w.m == m) return PASE_OK;
+  if (h->w.m != 0) return fail(PASE_ERR_STATE, "a handle serves one block width; create another handle for a different m");
+  Work& w = h->w;
+  w.m = m;
+  w.N = h->N;
+  const int64_t N = h->N, NH = h->NH;
+  const size_t nm = (size_t)N * m;
+  PASE_TRY(dev_alloc_t(h, &w.R, nm));
+  PASE_TRY(dev_alloc_t(h, &w.E, nm));
+  PASE_TRY(dev_alloc_t(h, &w.T1, nm));
+  PASE_TRY(dev_alloc_t(h, &w.T2, nm));
+  PASE_TRY(dev_alloc_t(h, &w.W, nm));
+  PASE_TRY(dev_alloc_t(h, &w.U, nm));
+  PASE_TRY(dev_alloc_t(h, &w.lam, m));
+  w.lb.assign(h->L, nullptr);
+  w.lx.assign(h->L, nullptr);
+  w.lt1.assign(h->L, nullptr);
+  w.lt2.assign(h->L, nullptr);
+  for (int l = 1; l < h->L; ++l) {
+    const size_t k = (size_t)h->lv[l].A.nrows * m;
+    PASE_TRY(dev_alloc_t(h, &w.lb[l], k));
+    PASE_TRY(dev_alloc_t(h, &w.lx[l], k));
+    PASE_TRY(dev_alloc_t(h, &w.lt1[l], k));
+    PASE_TRY(dev_alloc_t(h, &w.lt2[l], k));
+  }
+  if (h->opt.precision == PASE_PREC_MIXED) {
+    w.fb.assign(h->L, nullptr);
+    w.fx.assign(h->L, nullptr);
+    w.ft1.assign(h->L, nullptr);
+    w.ft2.assign(h->L, nullptr);
+    for (int l = 0; l < h->L; ++l) {
+      const size_t k = (size_t)h->lv[l].A.nrows * m;
+      PASE_TRY(dev_alloc_t(h, &w.fb[l], k));
+      PASE_TRY(dev_alloc_t(h, &w.fx[l], k));
+      PASE_TRY(dev_alloc_t(h, &w.ft1[l], k));
+      PASE_TRY(dev_alloc_t(h, &w.ft2[l], k));
+    }
+  }
+  const int64_t m3 = 3 * (int64_t)m;
+  int64_t pd = std::max<int64_t>((int64_t)kReduceBlocksHost * 2 * m, std::min<int64_t>(608 * m3 * m3, 32ll << 20));
+  pd = std::max<int64_t>(pd, m3 * m3 * 4);
+  w.partial_bytes = pd * sizeof(double);
+  PASE_TRY(dev_alloc(h, (void**)&w.partial, w.partial_bytes));
+  PASE_TRY(dev_alloc_t(h, &w.norms, 4 * m));
+  PASE_TRY(dev_alloc_t(h, &w.relres, m));
+  PASE_TRY(dev_alloc_t(h, &w.aH, (size_t)NH * m));
+  PASE_TRY(dev_alloc_t(h, &w.bH, (size_t)NH * m));
+  PASE_TRY(dev_alloc_t(h, &w.GA, (size_t)m * m));
+  PASE_TRY(dev_alloc_t(h, &w.GM, (size_t)m * m));
+  PASE_TRY(dev_alloc_t(h, &w.CH, (size_t)NH * m));
+  PASE_TRY(dev_alloc_t(h, &w.CW, (size_t)m * m));
+  const size_t nc = (size_t)(NH + m);
+  PASE_TRY(dev_alloc_t(h, &w.S, nc * m3));
+  PASE_TRY(dev_alloc_t(h, &w.AS, nc * m3));
+  PASE_TRY(dev_alloc_t(h, &w.BS, nc * m3));
+  PASE_TRY(dev_alloc_t(h, &w.Xn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.AXn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.BXn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.Pn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.APn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.BPn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.Gq, (size_t)m3 * m3));
+  PASE_TRY(dev_alloc_t(h, &w.Gb, (size_t)m3 * m3));
+  PASE_TRY(dev_alloc_t(h, &w.Cs, (size_t)m3 * m));
+  PASE_TRY(dev_alloc_t(h, &w.Rn, nc * m));
+  PASE_TRY(dev_alloc_t(h, &w.coef, (size_t)m * m));
+  PASE_TRY(dev_alloc_t(h, &w.ahat, (size_t)NH * m));
+  PASE_TRY(dev_alloc_t(h, &w.schur, (size_t)m * m));
+  w.eigwork_doubles = small_sygv_work_doubles((int)m3, m) + 64;
+  PASE_TRY(dev_alloc_t(h, &w.eigwork, w.eigwork_doubles));
+  PASE_TRY(dev_alloc_t(h, &w.smallvec, (size_t)16 * m));
+  PASE_TRY(dev_alloc_t(h, &w.status, 8));
+  PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
+  PASE_CUDA(cudaMallocHost(&w.h_status, sizeof(int) * 8));
+  return PASE_OK;
+}
+
+// ------------------------------------------------------------------ multigrid
+// One V-cycle for A_l x = b on level l (Alg. 1's linear solve): nu1 damped-Jacobi sweeps,
+// residual, restriction P^T, recursion, prolongation P, nu2 sweeps; dense solve on the
+// coarsest level.  x_zero: start from x = 0.  Level-l temporaries t1, t2 are used.
+template <typename T>
+struct LevelBufs {
+  std::vector<T*> b, x, t1, t2;
+};
+
+template <typename T>
+static const T* aval(const DevCSR& A);
+template <>
+const double* aval<double>(const DevCSR& A) {
+  return A.val;
+}
+template <>
+const float* aval<float>(const DevCSR& A) {
+  return A.val32;
+}
+template <typename T>
+static const T* dinv_of(const Level& L);
+template <>
+const double* dinv_of<double>(const Level& L) {
+  return L.dinv;
+}
+template <>
+const float* dinv_of<float>(const Level& L) {
+  return L.dinv32;
+}
+template <typename T>
+static const T* cinv_of(pase_ctx* h);
+template <>
+const double* cinv_of<double>(pase_ctx* h) {
+  return h->cinv;
+}
+template <>
+const float* cinv_of<float>(pase_ctx* h) {
+  return h->cinv32;
+}
+
+// damped Jacobi sweeps from x (or from zero), result in `dst` (x or tmp), returns where
+template <typename T>
+static int jacobi_sweeps(pase_ctx* h, const Level& L, int m, const T* b, T* x, T* tmp, int sweeps,
+                         bool x_zero, T** result) {
+  const double om = h->opt.omega;
+  T* cur = x;
+  T* other = tmp;
+  int s = 0;
+  if (x_zero) {
+    if (sweeps == 0) {
+      PASE_TRY(launch_fill(h, 0, 0.0, nullptr));
+      *result = nullptr;  // caller handles zero
+      return PASE_OK;
+    }
+    // choose the first target so that the last sweep lands in x
+    T* first = (sweeps % 2 == 1) ? x : tmp;
+    PASE_TRY(launch_scale_dinv<T>(h, L.A.nrows, m, dinv_of<T>(L), om, b, first));
+    cur = first;
+    other = (first == x) ? tmp : x;
+    s = 1;
+  }
+  for (; s < sweeps; ++s) {
+    PASE_TRY(launch_csr<T>(h, CSR_JACOBI, m, L.A, aval<T>(L.A), nullptr, cur, nullptr, b, dinv_of<T>(L),
+                           nullptr, om, other, nullptr, nullptr, nullptr));
+    std::swap(cur, other);
+  }
+  *result = cur;
+  return PASE_OK;
+}
+
+template <typename T>
+static int vcycle(pase_ctx* h, LevelBufs<T>& B, int l, int m, bool x_zero) {
+  const int Lc = h->L - 1;
+  T* b = B.b[l];
+  T* x = B.x[l];
+  if (l == Lc) {
+    return dense_mm<T>(h, h->ncoarsest, m, cinv_of<T>(h), b, x);
+  }
+  const Level& L = h->lv[l];
+  T* cur = nullptr;
+  PASE_TRY(jacobi_sweeps<T>(h, L, m, b, x, B.t1[l], h->opt.nu1, x_zero, &cur));
+  if (cur == nullptr) {  // nu1 == 0 from zero
+    PASE_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * L.A.nrows * m, h->stream));
+    cur = x;
+  }
+  // residual r = b - A cur  -> t2 ; restrict b_{l+1} = P^T r
+  PASE_TRY(launch_csr<T>(h, CSR_RESID, m, L.A, aval<T>(L.A), nullptr, cur, nullptr, b, nullptr, nullptr,
+                         0.0, B.t2[l], nullptr, nullptr, nullptr));
+  PASE_TRY(launch_csr<T>(h, CSR_MV, m, L.PT, aval<T>(L.PT), nullptr, B.t2[l], nullptr, nullptr, nullptr,
+                         nullptr, 0.0, B.b[l + 1], nullptr, nullptr, nullptr));
+  PASE_TRY(vcycle<T>(h, B, l + 1, m, true));
+  // cur += P x_{l+1}
+  PASE_TRY(launch_csr<T>(h, CSR_ADD, m, L.P, aval<T>(L.P), nullptr, B.x[l + 1], nullptr, cur, nullptr,
+                         nullptr, 0.0, cur, nullptr, nullptr, nullptr));
+  T* tmp = (cur == x) ? B.t1[l] : x;
+  T* res = nullptr;
+  // post-smoothing must end in x
+  if (h->opt.nu2 > 0) {
+    T* a = cur;
+    T* o = tmp;
+    for (int s = 0; s < h->opt.nu2; ++s) {
+      PASE_TRY(launch_csr<T>(h, CSR_JACOBI, m, L.A, aval<T>(L.A), nullptr, a, nullptr, b, dinv_of<T>(L),
+                             nullptr, h->opt.omega, o, nullptr, nullptr, nullptr));
+      std::swap(a, o);
+    }
+    res = a;
+  } else {
+    res = cur;
+  }
+  if (res != x) PASE_CUDA(cudaMemcpyAsync(x, res, sizeof(T) * L.A.nrows * m, cudaMemcpyDeviceToDevice, h->stream));
+  return PASE_OK;
+}
+
+static LevelBufs<double> fp64_bufs(pase_ctx* h) {
+  LevelBufs<double> B;
+  Work& w = h->w;
+  B.b = w.lb;
+  B.x = w.lx;
+  B.t1 = w.lt1;
+  B.t2 = w.lt2;
+  B.b[0] = w.R;
+  B.x[0] = w.E;
+  B.t1[0] = w.T1;
+  B.t2[0] = w.T2;
+  return B;
+}
+static LevelBufs<float> fp32_bufs(pase_ctx* h) {
+  LevelBufs<float> B;
+  Work& w = h->w;
+  B.b = w.fb;
+  B.x = w.fx;
+  B.t1 = w.ft1;
+  B.t2 = w.ft2;
+  return B;
+}
+
+// Step (a): W = U + E, E from s V-cycles on A E = R (R already in w.R).
+static int step_linear_solve(pase_ctx* h, const double* U, double* W) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int s = std::max(1, h->opt.inner_steps);
+  const size_t nm = (size_t)h->N * m;
+  if (h->opt.linear_solver != PASE_SOLVER_VCYCLE)
+    return fail(PASE_ERR_INVALID_ARG, "only the V-cycle linear solver is available");
+  if (h->opt.precision == PASE_PREC_MIXED) {
+    LevelBufs<float> B = fp32_bufs(h);
+    PASE_TRY(launch_f64_to_f32(h, nm, w.R, B.b[0]));
+    for (int c = 0; c < s; ++c) PASE_TRY(vcycle<float>(h, B, 0, m, c == 0));
+    PASE_TRY(launch_add_f32_to_f64(h, nm, U, B.x[0], W));
+  } else {
+    LevelBufs<double> B = fp64_bufs(h);
+    for (int c = 0; c < s; ++c) PASE_TRY(vcycle<double>(h, B, 0, m, c == 0));
+    PASE_TRY(launch_axpy(h, nm, 1.0, w.E, U, W));
+  }
+  return PASE_OK;
+}
+
+// Residual R = M U Lambda - A U and relative residuals into w.relres (device).
+static int step_residual(pase_ctx* h, const double* U, const double* lam, double* R) {
+  Work& w = h->w;
+  const int m = w.m;
+  int nb = 0;
+  PASE_TRY(launch_csr<double>(h, CSR_EIGRES, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, U, nullptr, nullptr,
+                              nullptr, lam, 0.0, R, nullptr, w.partial, &nb));
+  PASE_TRY(launch_reduce_partials(h, nb, 2 * m, w.partial, w.norms));
+  PASE_TRY(launch_relres(h, m, w.norms, lam, w.relres));
+  return PASE_OK;
+}
+
+// Step (b): aH = P^T A W, bH = P^T M W, GA = W^T A W, GM = W^T M W.
+static int step_project(pase_ctx* h, const double* W, double* aH, double* bH, double* GA, double* GM) {
+  Work& w = h->w;
+  const int m = w.m;
+  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, W, nullptr, nullptr,
+                              nullptr, nullptr, 0.0, w.T1, w.T2, nullptr, nullptr));
+  PASE_TRY(launch_csr<double>(h, CSR_MV2, m, h->PdT, h->PdT.val, nullptr, w.T1, w.T2, nullptr, nullptr,
+                              nullptr, 0.0, aH, bH, nullptr, nullptr));
+  PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T1, m, GA, m, true));
+  PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T2, m, GM, m, true));
+  return PASE_OK;
+}
+
+// Step (d): U = W C_W + P C_H.
+static int step_prolongate(pase_ctx* h, const double* W, const double* CH, const double* CW, double* U) {
+  const int m = h->w.m;
+  PASE_TRY(ts_gemm(h, h->N, m, m, 1.0, W, m, CW, m, 0.0, U, m));
+  PASE_TRY(launch_csr<double>(h, CSR_ADD, m, h->Pd, h->Pd.val, nullptr, CH, nullptr, U, nullptr, nullptr, 0.0,
+                              U, nullptr, nullptr, nullptr));
+  return PASE_OK;
+}
+
+// ------------------------------------------------------------------ step (c)
+// The augmented pencil acts on blocks Y [n_c][ld] (rows 0..N_H-1: coarse coefficients,
+// rows N_H..N_H+m-1: coefficients of W), k columns:
+//   A^ Y = [A_H Y1 + aH Y2 ; aH^T Y1 + GA Y2],  B^ Y = [M_H Y1 + bH Y2 ; bH^T Y1 + GM Y2]
+// (the block product of §4, computed without forming the dense pencil).
+static int aug_apply(pase_ctx* h, int k, const double* Y, int ld, double* AY, double* BY, int ldo,
+                     const double* aH, const double* bH, const double* GA, const double* GM) {
+  const int m = h->w.m;
+  const int64_t NH = h->NH;
+  if (k % 8 != 0) return fail(PASE_ERR_INVALID_ARG, "aug_apply: k must be a multiple of 8");
+  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, k, h->AH, h->AH.val, h->MH_val, Y, nullptr, nullptr, nullptr,
+                              nullptr, 0.0, AY, BY, nullptr, nullptr, ld, ldo));
+  const double* Y2 = Y + NH * ld;
+  PASE_TRY(ts_gemm(h, NH, m, k, 1.0, aH, m, Y2, ld, 1.0, AY, ldo));
+  PASE_TRY(ts_gemm(h, NH, m, k, 1.0, bH, m, Y2, ld, 1.0, BY, ldo));
+  PASE_TRY(ts_gram(h, NH, m, k, aH, m, Y, ld, AY + NH * ldo, ldo, false));
+  PASE_TRY(ts_gram(h, NH, m, k, bH, m, Y, ld, BY + NH * ldo, ldo, false));
+  PASE_TRY(small_gemm(h, m, k, m, 1.0, GA, m, false, Y2, ld, 1.0, AY + NH * ldo, ldo));
+  PASE_TRY(small_gemm(h, m, k, m, 1.0, GM, m, false, Y2, ld, 1.0, BY + NH * ldo, ldo));
+  return PASE_OK;
+}
+
+// A_H^-1 approximated by a V-cycle from the coarse level (exact when V_H is the coarsest
+// multigrid level): y = Ainv(r) for r [N_H][ld] (first m columns) -> y [N_H][ldo].
+static int coarse_apply(pase_ctx* h, const double* r, int ld, double* y, int ldo) {
+  const int m = h->w.m;
+  const int c = h->coarse_level;
+  LevelBufs<double> B = fp64_bufs(h);
+  PASE_TRY(launch_copy_cols(h, h->NH, m, r, ld, B.b[c], m));
+  PASE_TRY(vcycle<double>(h, B, c, m, true));
+  PASE_TRY(launch_copy_cols(h, h->NH, m, B.x[c], m, y, ldo));
+  return PASE_OK;
+}
+
+
+// Preconditioner T ~ A^^-1 from the block factorisation behind PRECOND-A (§4, Alg. 5
+// step 1): with ahat = Ainv aH and S = GA - aH^T ahat (PRECOND-A's alpha~),
+//   y1' = Ainv r1,  y2 = S^-1 (r2 - aH^T y1'),  y1 = y1' - ahat y2.
+// Ainv is the coarse V-cycle, so T is symmetric positive definite.
+static int aug_precond(pase_ctx* h, const double* R, int ld, double* Y, int ldo, const double* aH) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int64_t NH = h->NH;
+  PASE_TRY(coarse_apply(h, R, ld, Y, ldo));
+  double* y2 = Y + NH * ldo;
+  PASE_TRY(ts_gram(h, NH, m, m, aH, m, Y, ldo, w.coef, m, false));
+  PASE_TRY(launch_geam(h, m, m, 1.0, R + NH * ld, ld, -1.0, w.coef, m, y2, ldo));
+  PASE_TRY(small_chol_solve(h, m, m, w.schur, m, y2, ldo, w.status + 2, false));
+  PASE_TRY(ts_gemm(h, NH, m, m, -1.0, w.ahat, m, y2, ldo, 1.0, Y, ldo));
+  return PASE_OK;
+}
+
+static int aug_precond_setup(pase_ctx* h, const double* aH, const double* GA) {
+  Work& w = h->w;
+  const int m = w.m;
+  PASE_TRY(coarse_apply(h, aH, m, w.ahat, m));
+  PASE_TRY(ts_gram(h, h->NH, m, m, aH, m, w.ahat, m, w.coef, m, false));
+  PASE_TRY(launch_geam(h, m, m, 1.0, GA, m, -1.0, w.coef, m, w.schur, m));
+  // factor (the Cholesky reads the lower triangle only)
+  PASE_TRY(small_chol_solve(h, m, 0, w.schur, m, nullptr, 0, w.status + 1, true));
+  return PASE_OK;
+}
+
+// Operators of the block eigensolver.
+struct BlockOp {
+  int64_t n;
+  int kind;  // 0: augmented pencil, 1: coarse pencil (A_H, M_H)
+  const double *aH, *bH, *GA, *GM;
+};
+
+static int op_apply(pase_ctx* h, const BlockOp& op, const double* Y, int ld, double* AY, double* BY, int ldo) {
+  if (op.kind == 0) return aug_apply(h, h->w.m, Y, ld, AY, BY, ldo, op.aH, op.bH, op.GA, op.GM);
+  return launch_csr<double>(h, CSR_MV_AM, h->w.m, h->AH, h->AH.val, h->MH_val, Y, nullptr, nullptr, nullptr,
+                            nullptr, 0.0, AY, BY, nullptr, nullptr, ld, ldo);
+}
+static int op_precond(pase_ctx* h, const BlockOp& op, const double* R, int ld, double* Y, int ldo) {
+  if (op.kind == 0) return aug_precond(h, R, ld, Y, ldo, op.aH);
+  return coarse_apply(h, R, ld, Y, ldo);
+}
+
+static int sync_small(pase_ctx* h, const double* dsrc, int count, const int* dstatus, int nstatus) {
+  Work& w = h->w;
+  if (count) PASE_CUDA(cudaMemcpyAsync(w.h_small, dsrc, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
+  if (nstatus) PASE_CUDA(cudaMemcpyAsync(w.h_status, dstatus, sizeof(int) * nstatus, cudaMemcpyDeviceToHost, h->stream));
+  PASE_CUDA(cudaStreamSynchronize(h->stream));
+  return PASE_OK;
+}
+
+// Block eigensolver for the m smallest pairs of (A, B): locally optimal block
+// preconditioned iteration on the basis [X, W, P] (W = T R, P = previous step), each
+// step a Rayleigh-Ritz on the basis (the X, P, W blocks and the Rayleigh-Ritz of GCG_AUG,
+// Alg. 4; P is the last update direction).  On entry S[:, 0:m] holds the start block; on
+// exit S[:, 0:m] = X (B-orthonormal), lam (device) its Ritz values.  Returns iterations.
+static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double tol, int maxit, int nconv,
+                             int* iters_out) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int m3 = 3 * m;
+  const int64_t n = op.n;
+  double *S = w.S, *AS = w.AS, *BS = w.BS;
+  if (nconv <= 0 || nconv > m) nconv = m;
+  // initial Rayleigh-Ritz on the start block
+  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
+  PASE_TRY(ts_gram(h, n, m, m, S, m3, AS, m3, w.Gq, m3, true));
+  PASE_TRY(ts_gram(h, n, m, m, S, m3, BS, m3, w.Gb, m3, true));
+  PASE_TRY(small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, lam, w.Cs, m, w.status));
+  PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
+  if (w.h_status[0] != 0) return fail(PASE_ERR_NOT_SPD, "block eigensolver: start block is not B-independent");
+  PASE_TRY(ts_gemm(h, n, m, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
+  PASE_TRY(ts_gemm(h, n, m, m, 1.0, AS, m3, w.Cs, m, 0.0, w.AXn, m));
+  PASE_TRY(ts_gemm(h, n, m, m, 1.0, BS, m3, w.Cs, m, 0.0, w.BXn, m));
+  PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
+  PASE_TRY(launch_copy_cols(h, n, m, w.AXn, m, AS, m3));
+  PASE_TRY(launch_copy_cols(h, n, m, w.BXn, m, BS, m3));
+  bool haveP = false;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    // residual and convergence
+    int nb = 0;
+    PASE_TRY(launch_block_resid(h, n, m, AS, BS, m3, lam, w.Rn, m, &nb));
+    PASE_TRY(launch_reduce_partials(h, nb, 2 * m, w.partial, w.norms));
+    PASE_TRY(launch_relres(h, m, w.norms, lam, w.smallvec));
+    PASE_TRY(sync_small(h, w.smallvec, m, nullptr, 0));
+    double worst = 0.0;
+    for (int j = 0; j < nconv; ++j) worst = std::max(worst, w.h_small[j]);
+    if (!(worst == worst)) return fail(PASE_ERR_NAN, "block eigensolver: NaN residual");
+    if (worst <= tol) break;
+    // W = T R, B-orthogonal to X
+    double* Wb = S + m;
+    PASE_TRY(op_precond(h, op, w.Rn, m, Wb, m3));
+    PASE_TRY(ts_gram(h, n, m, m, BS, m3, Wb, m3, w.coef, m, false));
+    PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, Wb, m3));
+    PASE_TRY(op_apply(h, op, Wb, m3, AS + m, BS + m, m3));
+    int nbw = 2 * m;
+    if (haveP) {
+      PASE_TRY(ts_gram(h, n, m, m, BS, m3, w.Pn, m, w.coef, m, false));
+      PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, w.Pn, m));
+      PASE_TRY(ts_gemm(h, n, m, m, -1.0, AS, m3, w.coef, m, 1.0, w.APn, m));
+      PASE_TRY(ts_gemm(h, n, m, m, -1.0, BS, m3, w.coef, m, 1.0, w.BPn, m));
+      PASE_TRY(launch_copy_cols(h, n, m, w.Pn, m, S + 2 * m, m3));
+      PASE_TRY(launch_copy_cols(h, n, m, w.APn, m, AS + 2 * m, m3));
+      PASE_TRY(launch_copy_cols(h, n, m, w.BPn, m, BS + 2 * m, m3));
+      nbw = m3;
+    }
+    PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, AS, m3, w.Gq, m3, true));
+    PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, BS, m3, w.Gb, m3, true));
+    PASE_TRY(small_sygv(h, nbw, m, w.Gq, m3, w.Gb, m3, w.smallvec + m, w.Cs, m, w.status));
+    PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
+    if (w.h_status[0] != 0 && nbw == m3) {
+      nbw = 2 * m;  // drop P: the basis became numerically dependent
+      PASE_TRY(small_sygv(h, nbw, m, w.Gq, m3, w.Gb, m3, w.smallvec + m, w.Cs, m, w.status));
+      PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
+    }
+    if (w.h_status[0] != 0) break;  // W itself is dependent on X: nothing left to gain
+    // X = S C, P = S[:, m:] C[m:, :]
+    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
+    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, AS, m3, w.Cs, m, 0.0, w.AXn, m));
+    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, BS, m3, w.Cs, m, 0.0, w.BXn, m));
+    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, S + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.Pn, m));
+    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, AS + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.APn, m));
+    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, BS + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.BPn, m));
+    haveP = true;
+    PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
+    PASE_TRY(launch_copy_cols(h, n, m, w.AXn, m, AS, m3));
+    PASE_TRY(launch_copy_cols(h, n, m, w.BXn, m, BS, m3));
+    PASE_CUDA(cudaMemcpyAsync(lam, w.smallvec + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (iters_out) *iters_out = std::min(it, maxit);
+  return PASE_OK;
+}
+
+// Step (c): the m smallest pairs of the augmented pencil, warm start u_H = 0, gamma = I.
+static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, const double* GA,
+                              const double* GM, double* lam, double* CH, double* CW, int* iters) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int m3 = 3 * m;
+  const int64_t NH = h->NH, nc = NH + m;
+  PASE_TRY(aug_precond_setup(h, aH, GA));
+  // start block [0; I]
+  PASE_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * nc * m3, h->stream));
+  PASE_TRY(launch_set_identity_rows(h, NH, m, m3, w.S));
+  BlockOp op{nc, 0, aH, bH, GA, GM};
+  const double tol = h->aug_tol_now > 0 ? h->aug_tol_now : h->opt.aug_tol;
+  PASE_TRY(block_eigensolver(h, op, lam, tol, h->opt.aug_max_iter, h->aug_nconv, iters));
+  PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, CH, m));
+  PASE_TRY(launch_copy_cols(h, m, m, w.S + NH * m3, m3, CW, m));
+  return PASE_OK;
+}
+
+// Alg. 3 steps 1-2: coarse eigenpairs of (A_H, M_H), interpolated: U = I_H^h u_H.
+static int coarse_start(pase_ctx* h, double* U, double* lam, int* iters) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int m3 = 3 * m;
+  const int64_t NH = h->NH;
+  if (NH < m) return fail(PASE_ERR_INVALID_ARG, "coarse start needs N_H >= m");
+  PASE_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * (NH + m) * m3, h->stream));
+  PASE_TRY(launch_hash_fill(h, NH, m, m3, 12345u, w.S));
+  BlockOp op{NH, 1, nullptr, nullptr, nullptr, nullptr};
+  PASE_TRY(block_eigensolver(h, op, lam, 1e-12, 10 * h->opt.aug_max_iter, m, iters));
+  PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, w.CH, m));
+  PASE_TRY(launch_csr<double>(h, CSR_MV, m, h->Pd, h->Pd.val, nullptr, w.CH, nullptr, nullptr, nullptr, nullptr,
+                              0.0, U, nullptr, nullptr, nullptr));
+  return PASE_OK;
+}
+
+// One outer iteration after the residual has been formed in w.R (or with W = U when
+// do_solve is false): (a) (b) (c) (d); U and lam are overwritten.
+static int iterate_body(pase_ctx* h, double* U, double* lam, bool do_solve, pase_stats* st,
+                        cudaEvent_t* ev) {
+  Work& w = h->w;
+  const size_t nm = (size_t)h->N * w.m;
+  if (ev) PASE_CUDA(cudaEventRecord(ev[0], h->stream));
+  if (do_solve) PASE_TRY(step_linear_solve(h, U, w.W));
+  else PASE_CUDA(cudaMemcpyAsync(w.W, U, sizeof(double) * nm, cudaMemcpyDeviceToDevice, h->stream));
+  if (ev) PASE_CUDA(cudaEventRecord(ev[1], h->stream));
+  PASE_TRY(step_project(h, w.W, w.aH, w.bH, w.GA, w.GM));
+  if (ev) PASE_CUDA(cudaEventRecord(ev[2], h->stream));
+  int it = 0;
+  PASE_TRY(step_augmented_eig(h, w.aH, w.bH, w.GA, w.GM, lam, w.CH, w.CW, &it));
+  if (st) st->aug_iterations += it;
+  if (ev) PASE_CUDA(cudaEventRecord(ev[3], h->stream));
+  PASE_TRY(step_prolongate(h, w.W, w.CH, w.CW, U));
+  if (ev) PASE_CUDA(cudaEventRecord(ev[4], h->stream));
+  return PASE_OK;
+}
+
+}  // namespace pase
+
+using namespace pase;
+
+// ====================================================================== C ABI
+extern "C" {
+
+void pase_default_options(pase_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = PASE_PREC_FP64;
+  o->linear_solver = PASE_SOLVER_VCYCLE;
+  o->inner_steps = 2;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 2.0 / 3.0;
+  o->coarse_level = -1;
+  o->max_iter = 100;
+  o->aug_max_iter = 60;
+  o->aug_tol = 1e-12;
+  o->verbose = 0;
+}
+
+const char* pase_status_string(int code) {
+  switch (code) {
+    case PASE_OK: return "ok";
+    case PASE_ERR_INVALID_ARG: return "invalid argument";
+    case PASE_ERR_SHAPE_MISMATCH: return "shape mismatch";
+    case PASE_ERR_PATTERN_MISMATCH: return "sparsity pattern mismatch";
+    case PASE_ERR_NOT_SPD: return "matrix not symmetric positive definite";
+    case PASE_ERR_NAN: return "NaN or Inf encountered";
+    case PASE_ERR_NOT_CONVERGED: return "not converged";
+    case PASE_ERR_TIMEOUT: return "device wait timed out";
+    case PASE_ERR_CUDA: return "CUDA error";
+    case PASE_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PASE_ERR_STATE: return "call out of order";
+    case PASE_ERR_BAD_CSR: return "malformed CSR matrix";
+    default: return "unknown status";
+  }
+}
+
+const char* pase_last_error(void) { return pase::last_error_cstr(); }
+
+int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
+  if (!out) return fail(PASE_ERR_INVALID_ARG, "pase_create: null handle pointer");
+  *out = nullptr;
+  pase_ctx* h = new (std::nothrow) pase_ctx();
+  if (!h) return fail(PASE_ERR_OUT_OF_MEMORY, "pase_create: host allocation failed");
+  if (opt) h->opt = *opt;
+  else pase_default_options(&h->opt);
+  const pase_options& o = h->opt;
+  if ((o.precision != PASE_PREC_FP64 && o.precision != PASE_PREC_MIXED) || o.inner_steps < 1 || o.nu1 < 0 ||
+      o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||
+      !(o.aug_tol > 0.0)) {
+    delete h;
+    return fail(PASE_ERR_INVALID_ARG, "pase_create: invalid options");
+  }
+  h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(PASE_ERR_CUDA, "pase_create: no CUDA device");
+  }
+  *out = h;
+  return PASE_OK;
+}
+
+int pase_destroy(pase_handle h) {
+  if (!h) return PASE_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->w.h_small) cudaFreeHost(h->w.h_small);
+  if (h->w.h_status) cudaFreeHost(h->w.h_status);
+  delete h;
+  return PASE_OK;
+}
+
+int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_interp, const pase_csr* P,
+               const pase_csr* A_H, const pase_csr* M_H) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "pase_setup: null handle");
+  if (h->ready) return fail(PASE_ERR_STATE, "pase_setup: handle already set up");
+  if (n_interp < 1 || !P) return fail(PASE_ERR_INVALID_ARG, "pase_setup: need at least one interpolation matrix");
+  HostCSR A0, M0, AHc, MHc;
+  PASE_TRY(csr_from_abi(A_h, A0, "A_h"));
+  PASE_TRY(csr_from_abi(M_h, M0, "M_h"));
+  PASE_TRY(csr_from_abi(A_H, AHc, "A_H"));
+  PASE_TRY(csr_from_abi(M_H, MHc, "M_H"));
+  std::vector<HostCSR> Pc(n_interp);
+  for (int k = 0; k < n_interp; ++k) PASE_TRY(csr_from_abi(&P[k], Pc[k], "P"));
+  if (A0.nrows != A0.ncols || A0.nrows == 0) return fail(PASE_ERR_SHAPE_MISMATCH, "A_h must be square and non-empty");
+  if (!same_pattern(A0, M0)) return fail(PASE_ERR_PATTERN_MISMATCH, "A_h and M_h must share one sparsity pattern");
+  if (!same_pattern(AHc, MHc)) return fail(PASE_ERR_PATTERN_MISMATCH, "A_H and M_H must share one sparsity pattern");
+  int c = h->opt.coarse_level < 0 ? n_interp : h->opt.coarse_level;
+  if (c < 1 || c > n_interp) return fail(PASE_ERR_INVALID_ARG, "coarse_level out of range");
+  int64_t rows = A0.nrows;
+  for (int k = 0; k < n_interp; ++k) {
+    if (Pc[k].nrows != rows || Pc[k].ncols <= 0) return fail(PASE_ERR_SHAPE_MISMATCH, "P chain shapes do not match");
+    rows = Pc[k].ncols;
+  }
+  // levels
+  h->L = n_interp + 1;
+  h->coarse_level = c;
+  std::vector<HostCSR> Al(h->L);
+  Al[0] = A0;
+  for (int k = 0; k < n_interp; ++k) Al[k + 1] = csr_galerkin(Pc[k], Al[k]);
+  if (AHc.nrows != Al[c].nrows || AHc.ncols != Al[c].nrows)
+    return fail(PASE_ERR_SHAPE_MISMATCH, "A_H does not match the size of the coarse level");
+  const HostCSR& Ac = Al[h->L - 1];
+  if (Ac.nrows > 8192) return fail(PASE_ERR_INVALID_ARG, "coarsest multigrid level too large for a dense solve (> 8192)");
+  std::vector<double> cinv;
+  if (!dense_spd_inverse(Ac, cinv)) return fail(PASE_ERR_NOT_SPD, "coarsest multigrid operator is not SPD");
+  HostCSR Pd = Pc[0];
+  for (int k = 1; k < c; ++k) Pd = csr_multiply(Pd, Pc[k]);
+  const bool mixed = h->opt.precision == PASE_PREC_MIXED;
+  h->N = A0.nrows;
+  h->NH = AHc.nrows;
+  h->lv.resize(h->L);
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    PASE_TRY(upload_csr(h, Al[l], L.A, mixed, false, nullptr));
+    std::vector<double> dinv(Al[l].nrows);
+    for (int64_t i = 0; i < Al[l].nrows; ++i) {
+      double dg = 0.0;
+      for (int64_t k = Al[l].rowptr[i]; k < Al[l].rowptr[i + 1]; ++k)
+        if (Al[l].col[k] == i) dg = Al[l].val[k];
+      if (!(dg > 0.0)) return fail(PASE_ERR_NOT_SPD, "non-positive diagonal entry in a multigrid level");
+      dinv[i] = 1.0 / dg;
+    }
+    PASE_TRY(upload_vec(h, dinv, &L.dinv));
+    if (mixed) {
+      std::vector<float> d32(dinv.begin(), dinv.end());
+      PASE_TRY(upload_vec(h, d32, &L.dinv32));
+    }
+    if (l < n_interp) {
+      PASE_TRY(upload_csr(h, Pc[l], L.P, mixed, false, nullptr));
+      PASE_TRY(upload_csr(h, csr_transpose(Pc[l]), L.PT, mixed, false, nullptr));
+    }
+  }
+  {
+    DevCSR Mtmp;
+    PASE_TRY(upload_csr(h, M0, Mtmp, mixed, true, &h->lv[0].A));
+    h->M0_val = Mtmp.val;
+    h->M0_val32 = Mtmp.val32;
+  }
+  PASE_TRY(upload_csr(h, Pd, h->Pd, false, false, nullptr));
+  PASE_TRY(upload_csr(h, csr_transpose(Pd), h->PdT, false, false, nullptr));
+  PASE_TRY(upload_csr(h, AHc, h->AH, false, false, nullptr));
+  {
+    DevCSR Mtmp;
+    PASE_TRY(upload_csr(h, MHc, Mtmp, false, true, &h->AH));
+    h->MH_val = Mtmp.val;
+  }
+  h->ncoarsest = Ac.nrows;
+  PASE_TRY(upload_vec(h, cinv, &h->cinv));
+  if (mixed) {
+    std::vector<float> c32(cinv.begin(), cinv.end());
+    PASE_TRY(upload_vec(h, c32, &h->cinv32));
+  }
+  PASE_CUDA(cudaDeviceSynchronize());
+  h->ready = true;
+  return PASE_OK;
+}
+
+int pase_reserve(pase_handle h, int m) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  return reserve(h, m);
+}
+
+static int check_m(pase_handle h, int m) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  return reserve(h, m);
+}
+
+int pase_residual(pase_handle h, int m, const double* U, const double* lambda, double* R, double* relres) {
+  PASE_TRY(check_m(h, m));
+  if (!U || !lambda) return fail(PASE_ERR_INVALID_ARG, "pase_residual: null input");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double);
+  const void *dU, *dl;
+  void *dR, *drr;
+  PASE_TRY(st.in(U, nm, &dU));
+  PASE_TRY(st.in(lambda, m * sizeof(double), &dl));
+  PASE_TRY(st.out(R, nm, &dR));
+  PASE_TRY(st.out(relres, m * sizeof(double), &drr));
+  PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, dR ? (double*)dR : h->w.R));
+  if (drr) PASE_CUDA(cudaMemcpyAsync(drr, h->w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return st.finish();
+}
+
+int pase_linear_solve(pase_handle h, int m, const double* U, const double* lambda, const double* R, double* W) {
+  PASE_TRY(check_m(h, m));
+  if (!U || !lambda || !W) return fail(PASE_ERR_INVALID_ARG, "pase_linear_solve: null argument");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double);
+  const void *dU, *dl, *dRin;
+  void* dW;
+  PASE_TRY(st.in(U, nm, &dU));
+  PASE_TRY(st.in(lambda, m * sizeof(double), &dl));
+  PASE_TRY(st.in(R, nm, &dRin));
+  PASE_TRY(st.out(W, nm, &dW));
+  if (dRin) PASE_CUDA(cudaMemcpyAsync(h->w.R, dRin, nm, cudaMemcpyDeviceToDevice, h->stream));
+  else PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, h->w.R));
+  PASE_TRY(step_linear_solve(h, (const double*)dU, (double*)dW));
+  return st.finish();
+}
+
+int pase_project(pase_handle h, int m, const double* W, double* aH, double* bH, double* GA, double* GM) {
+  PASE_TRY(check_m(h, m));
+  if (!W || !aH || !bH || !GA || !GM) return fail(PASE_ERR_INVALID_ARG, "pase_project: null argument");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double), hm = (size_t)h->NH * m * sizeof(double),
+               mm = (size_t)m * m * sizeof(double);
+  const void* dW;
+  void *da, *db, *dga, *dgm;
+  PASE_TRY(st.in(W, nm, &dW));
+  PASE_TRY(st.out(aH, hm, &da));
+  PASE_TRY(st.out(bH, hm, &db));
+  PASE_TRY(st.out(GA, mm, &dga));
+  PASE_TRY(st.out(GM, mm, &dgm));
+  PASE_TRY(step_project(h, (const double*)dW, (double*)da, (double*)db, (double*)dga, (double*)dgm));
+  return st.finish();
+}
+
+int pase_augmented_eig(pase_handle h, int m, const double* aH, const double* bH, const double* GA,
+                       const double* GM, double* lambda, double* C_H, double* C_W, int* aug_iters) {
+  PASE_TRY(check_m(h, m));
+  if (!aH || !bH || !GA || !GM || !lambda || !C_H || !C_W) return fail(PASE_ERR_INVALID_ARG, "pase_augmented_eig: null argument");
+  Stage st(h);
+  const size_t hm = (size_t)h->NH * m * sizeof(double), mm = (size_t)m * m * sizeof(double);
+  const void *da, *db, *dga, *dgm;
+  void *dl, *dch, *dcw;
+  PASE_TRY(st.in(aH, hm, &da));
+  PASE_TRY(st.in(bH, hm, &db));
+  PASE_TRY(st.in(GA, mm, &dga));
+  PASE_TRY(st.in(GM, mm, &dgm));
+  PASE_TRY(st.out(lambda, m * sizeof(double), &dl));
+  PASE_TRY(st.out(C_H, hm, &dch));
+  PASE_TRY(st.out(C_W, mm, &dcw));
+  int it = 0;
+  PASE_TRY(step_augmented_eig(h, (const double*)da, (const double*)db, (const double*)dga, (const double*)dgm,
+                              (double*)dl, (double*)dch, (double*)dcw, &it));
+  if (aug_iters) *aug_iters = it;
+  return st.finish();
+}
+
+int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H, const double* C_W, double* U) {
+  PASE_TRY(check_m(h, m));
+  if (!W || !C_H || !C_W || !U) return fail(PASE_ERR_INVALID_ARG, "pase_prolongate: null argument");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double), hm = (size_t)h->NH * m * sizeof(double),
+               mm = (size_t)m * m * sizeof(double);
+  const void *dW, *dch, *dcw;
+  void* dU;
+  PASE_TRY(st.in(W, nm, &dW));
+  PASE_TRY(st.in(C_H, hm, &dch));
+  PASE_TRY(st.in(C_W, mm, &dcw));
+  PASE_TRY(st.out(U, nm, &dU));
+  if (dU == dW) return fail(PASE_ERR_INVALID_ARG, "pase_prolongate: U must not alias W");
+  PASE_TRY(step_prolongate(h, (const double*)dW, (const double*)dch, (const double*)dcw, (double*)dU));
+  return st.finish();
+}
+
+int pase_iterate(pase_handle h, int m, double* U, double* lambda, int do_linear_solve, double* relres) {
+  PASE_TRY(check_m(h, m));
+  if (!U || !lambda) return fail(PASE_ERR_INVALID_ARG, "pase_iterate: null argument");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double);
+  void *dU, *dl, *drr;
+  PASE_TRY(st.out(U, nm, &dU, true));
+  PASE_TRY(st.out(lambda, m * sizeof(double), &dl, true));
+  PASE_TRY(st.out(relres, m * sizeof(double), &drr));
+  if (do_linear_solve || drr) {
+    PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, h->w.R));
+    if (drr) PASE_CUDA(cudaMemcpyAsync(drr, h->w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  PASE_TRY(iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr));
+  return st.finish();
+}
+
+int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX) {
+  PASE_TRY(check_m(h, m));
+  if (!is_device_ptr(X) || !is_device_ptr(AX) || !is_device_ptr(MX))
+    return fail(PASE_ERR_INVALID_ARG, "pase_spmm_am: device pointers required");
+  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, X, nullptr, nullptr,
+                              nullptr, nullptr, 0.0, AX, MX, nullptr, nullptr));
+  PASE_CUDA(cudaStreamSynchronize(h->stream));
+  return PASE_OK;
+}
+
+int64_t pase_kernel_count(pase_handle h) { return h ? h->launches : 0; }
+
+int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, double* lambda, double* U,
+               pase_stats* stp) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (!h->ready) return fail(PASE_ERR_STATE, "pase_setup has not completed");
+  if (nev < 1 || !(tol > 0.0) || !lambda || !U) return fail(PASE_ERR_INVALID_ARG, "pase_solve: bad arguments");
+  if (m == 0) {
+    int g = nev + std::max(4, (nev + 9) / 10);
+    m = (g + 7) / 8 * 8;
+  }
+  if (m <= nev) return fail(PASE_ERR_INVALID_ARG, "pase_solve: m must exceed nev");
+  PASE_TRY(reserve(h, m));
+  Work& w = h->w;
+  pase_stats st;
+  memset(&st, 0, sizeof(st));
+  const int64_t launches0 = h->launches;
+  Stage sg(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double);
+  const void* dU0;
+  void *dl, *dU;
+  PASE_TRY(sg.in(U0, nm, &dU0));
+  PASE_TRY(sg.out(lambda, m * sizeof(double), &dl));
+  PASE_TRY(sg.out(U, nm, &dU));
+  cudaEvent_t ev[6];
+  for (auto& e : ev) PASE_CUDA(cudaEventCreate(&e));
+  PASE_CUDA(cudaEventRecord(ev[5], h->stream));
+  auto t0 = std::chrono::steady_clock::now();
+  bool first_solve = true;
+  if (dU0) {
+    PASE_CUDA(cudaMemcpyAsync(w.U, dU0, nm, cudaMemcpyDeviceToDevice, h->stream));
+    first_solve = false;
+  } else {
+    int it = 0;
+    PASE_TRY(coarse_start(h, w.U, w.lam, &it));
+    st.aug_iterations += it;
+  }
+  h->aug_nconv = std::min(m, nev + std::max(1, (m - nev) / 2));
+  int rc = PASE_OK;
+  double worst = INFINITY;
+  int iter = 0;
+  for (iter = 0; iter <= h->opt.max_iter; ++iter) {
+    const bool do_solve = (iter > 0) || first_solve;
+    if (do_solve) {
+      // residual + convergence test of the current block
+      cudaEvent_t r0, r1;
+      PASE_CUDA(cudaEventCreate(&r0));
+      PASE_CUDA(cudaEventCreate(&r1));
+      PASE_CUDA(cudaEventRecord(r0, h->stream));
+      PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+      PASE_CUDA(cudaEventRecord(r1, h->stream));
+      PASE_TRY(sync_small(h, w.relres, m, nullptr, 0));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r0, r1);
+      st.phase_ms[4] += ms;
+      cudaEventDestroy(r0);
+      cudaEventDestroy(r1);
+      worst = 0.0;
+      int conv = 0;
+      for (int j = 0; j < nev; ++j) {
+        const double r = w.h_small[j];
+        if (!(r == r)) {
+          worst = NAN;
+          break;
+        }
+        worst = std::max(worst, r);
+        if (r <= tol) ++conv;
+      }
+      st.converged = conv;
+      st.max_residual = worst;
+      if (!(worst == worst)) {
+        rc = fail(PASE_ERR_NAN, "NaN in the eigen-residual");
+        break;
+      }
+      if (h->opt.verbose)
+        fprintf(stderr, "[pase] iter %d  max relres(first %d) %.3e  aug_iters %d\n", iter, nev, worst, st.aug_iterations);
+      if (worst <= tol) break;
+      if (iter == h->opt.max_iter) {
+        rc = PASE_ERR_NOT_CONVERGED;
+        pase::set_error("maximum number of iterations reached");
+        break;
+      }
+      h->aug_tol_now = std::max(h->opt.aug_tol, 1e-3 * worst);
+    } else {
+      h->aug_tol_now = 1e-6;
+    }
+    PASE_TRY(iterate_body(h, w.U, w.lam, do_solve, &st, ev));
+    PASE_CUDA(cudaEventSynchronize(ev[4]));
+    for (int p = 0; p < 4; ++p) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
+      st.phase_ms[p] += ms;
+    }
+    st.iterations++;
+  }
+  PASE_CUDA(cudaMemcpyAsync(dl, w.lam, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  PASE_CUDA(cudaMemcpyAsync(dU, w.U, nm, cudaMemcpyDeviceToDevice, h->stream));
+  PASE_TRY(sg.finish());
+  auto t1 = std::chrono::steady_clock::now();
+  st.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  st.kernel_launches = (int)(h->launches - launches0);
+  for (auto& e : ev) cudaEventDestroy(e);
+  h->aug_tol_now = 0;
+  h->aug_nconv = 0;
+  if (stp) *stp = st;
+  return rc;
+}
+
+}  // extern "C"

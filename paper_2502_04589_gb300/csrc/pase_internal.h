@@ -1,0 +1,200 @@
+// Internal declarations shared by the translation units of libpase.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pase.h"
+
+namespace pase {
+
+// ------------------------------------------------------------------ error plumbing
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define PASE_CUDA(call)                                                                 \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::pase::fail(e_ == cudaErrorMemoryAllocation ? PASE_ERR_OUT_OF_MEMORY      \
+                                                          : PASE_ERR_CUDA,              \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+#define PASE_TRY(expr)        \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != PASE_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------------ host CSR
+struct HostCSR {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+int csr_from_abi(const pase_csr* in, HostCSR& out, const char* name);
+HostCSR csr_transpose(const HostCSR& a);
+HostCSR csr_multiply(const HostCSR& a, const HostCSR& b);  // a * b
+HostCSR csr_galerkin(const HostCSR& P, const HostCSR& A);   // P^T A P
+bool same_pattern(const HostCSR& a, const HostCSR& b);
+// dense inverse of an SPD CSR matrix (row-major n x n); returns false if not SPD
+bool dense_spd_inverse(const HostCSR& a, std::vector<double>& inv);
+
+// ------------------------------------------------------------------ device CSR
+struct DevCSR {
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;   // FP64 values
+  float* val32 = nullptr;  // FP32 copy (mixed precision), may be null
+};
+
+struct Level {
+  DevCSR A;                  // A_l (level 0: A_h; shares col/rowptr with M)
+  double* dinv = nullptr;    // 1 / diag(A_l)
+  float* dinv32 = nullptr;
+  DevCSR P;                  // interpolation level l+1 -> l  (rows n_l)
+  DevCSR PT;                 // its transpose (rows n_{l+1})
+};
+
+// Per-block-width workspace.
+struct Work {
+  int m = 0;
+  int64_t N = 0;
+  // fine level multivectors [N][m]
+  double *R = nullptr, *E = nullptr, *T1 = nullptr, *T2 = nullptr, *W = nullptr, *U = nullptr;
+  double* lam = nullptr;                     // [m]
+  // per level (l >= 1) multivectors: b, x, t1, t2  [n_l][m]
+  std::vector<double*> lb, lx, lt1, lt2;
+  // FP32 copies for the mixed-precision solve, all levels (level 0 included)
+  std::vector<float*> fb, fx, ft1, ft2;
+  // reductions
+  double* partial = nullptr;  // scratch for two-stage reductions
+  size_t partial_bytes = 0;
+  double* norms = nullptr;    // [4m]
+  double* relres = nullptr;   // [m]
+  // projection outputs
+  double *aH = nullptr, *bH = nullptr, *GA = nullptr, *GM = nullptr;
+  double *CH = nullptr, *CW = nullptr;
+  // augmented eigensolver (n_c = N_H + m rows, up to 3m wide)
+  double *S = nullptr, *AS = nullptr, *BS = nullptr;   // [n_c][3m]
+  double *Xn = nullptr, *AXn = nullptr, *BXn = nullptr;  // [n_c][m]
+  double *Pn = nullptr, *APn = nullptr, *BPn = nullptr;  // [n_c][m]
+  double *Gq = nullptr, *Gb = nullptr, *Cs = nullptr;   // small dense [3m][3m], C [3m][m]
+  double *ahat = nullptr, *schur = nullptr;             // [N_H][m], [m][m]
+  double* eigwork = nullptr;                            // small eigensolver scratch
+  size_t eigwork_doubles = 0;
+  double* smallvec = nullptr;                           // [16m]
+  double *Rn = nullptr, *coef = nullptr;                // [n_c][m], [m][m]
+  int* status = nullptr;                                // device status words [8]
+  // host pinned mirror for small readbacks
+  double* h_small = nullptr;
+  int* h_status = nullptr;
+};
+
+}  // namespace pase
+
+struct pase_ctx {
+  pase_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool ready = false;
+  int L = 0;             // number of levels (chain length + 1)
+  int coarse_level = 0;  // which level is V_H
+  int64_t N = 0, NH = 0;
+  std::vector<pase::Level> lv;
+  double* M0_val = nullptr;  // M_h values (pattern of A_h)
+  float* M0_val32 = nullptr;
+  pase::DevCSR Pd, PdT;      // direct interpolation V_H -> V_h and its transpose
+  pase::DevCSR AH;           // coarse pencil as given: A_H with values, M_H values below
+  double* MH_val = nullptr;
+  int64_t ncoarsest = 0;     // dense inverse of the coarsest multigrid operator
+  double* cinv = nullptr;
+  float* cinv32 = nullptr;
+  pase::Work w;
+  int64_t launches = 0;
+  int aug_nconv = 0;         // columns the step-(c) solver must converge (0 = all)
+  double aug_tol_now = 0;    // current inner tolerance
+  std::vector<void*> allocations;
+};
+
+namespace pase {
+
+// ------------------------------------------------------------------ memory helpers
+int dev_alloc(pase_ctx* h, void** p, size_t bytes);
+template <typename T>
+int dev_alloc_t(pase_ctx* h, T** p, size_t count) {
+  return dev_alloc(h, (void**)p, count * sizeof(T));
+}
+int upload_csr(pase_ctx* h, const HostCSR& a, DevCSR& d, bool with_fp32, bool share_pattern_from,
+               const DevCSR* src_pattern);
+
+// ------------------------------------------------------------------ sparse kernels
+// Modes of the generic CSR x multivector kernel.
+enum CsrMode {
+  CSR_MV = 0,       // Y1 = A X
+  CSR_MV_AM = 1,    // Y1 = A X, Y2 = M X (shared pattern, second value array vm)
+  CSR_RESID = 2,    // Y1 = B - A X
+  CSR_JACOBI = 3,   // Y1 = X + omega dinv (B - A X)
+  CSR_EIGRES = 4,   // Y1 = (M X) diag(lam) - A X, partial column sums of |Y1|^2, |MX|^2
+  CSR_MV2 = 5,      // Y1 = A X, Y2 = A X2 (two inputs, one matrix)
+  CSR_ADD = 6,      // Y1 = B + A X
+};
+
+template <typename T>
+int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const T* vm,
+               const T* X, const T* X2, const T* B, const T* dinv, const double* lam, double omega,
+               T* Y1, T* Y2, double* partial, int* nblocks_out, int64_t ldx = 0,
+               int64_t ldy = 0);
+
+// elementwise
+template <typename T>
+int launch_scale_dinv(pase_ctx* h, int64_t n, int m, const T* dinv, double omega, const T* B,
+                      T* Y);  // Y = omega dinv B
+int launch_axpy(pase_ctx* h, int64_t count, double a, const double* x, const double* y,
+                double* z);  // z = a x + y
+int launch_f64_to_f32(pase_ctx* h, int64_t count, const double* x, float* y);
+int launch_add_f32_to_f64(pase_ctx* h, int64_t count, const double* u, const float* e,
+                          double* w);  // w = u + e
+int launch_copy_cols(pase_ctx* h, int64_t n, int k, const double* src, int lds, double* dst,
+                     int ldd);
+int launch_fill(pase_ctx* h, int64_t count, double v, double* x);
+int launch_hash_fill(pase_ctx* h, int64_t rows, int cols, int64_t ld, unsigned seed, double* X);
+int launch_set_identity_rows(pase_ctx* h, int64_t row0, int k, int64_t ld, double* X);
+int launch_geam(pase_ctx* h, int64_t rows, int cols, double a, const double* A, int64_t lda,
+                double b, const double* B, int64_t ldb, double* C, int64_t ldc);  // C = aA + bB
+
+// reductions
+int launch_reduce_partials(pase_ctx* h, int nblk, int width, const double* partial,
+                           double* out);  // out[j] = sum_b partial[b*width + j]
+int launch_relres(pase_ctx* h, int m, const double* norms, const double* lam, double* relres);
+
+// dense tall-skinny
+int ts_gram(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int ldx, const double* Y,
+            int ldy, double* G, int ldg, bool sym);  // G = X^T Y (k1 x k2)
+int ts_gemm(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const double* X, int ldx,
+            const double* C, int ldc, double beta, double* Y, int ldy);  // Y = a X C + b Y
+template <typename T>
+int dense_mm(pase_ctx* h, int64_t n, int m, const T* Ainv, const T* B, T* X);  // X = Ainv B
+
+// small dense matrices on one CTA
+int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,
+               double* lam, double* C, int ldc, int* status_dev);
+int small_gemm(pase_ctx* h, int m, int n, int k, double alpha, const double* A, int lda,
+               bool transA, const double* B, int ldb, double beta, double* C, int ldc);
+int small_chol_solve(pase_ctx* h, int n, int nrhs, double* S, int lds, double* B, int ldb,
+                     int* status_dev, bool factor);  // [S <- chol(S) (lower)], B <- S^-1 B
+size_t small_sygv_work_doubles(int n, int k);
+constexpr int kReduceBlocksHost = 152 * 8;
+// column-wise residual of a block eigenproblem: R = AX - BX diag(lam), partial norms
+int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const double* BX,
+                       int64_t ldin, const double* lam, double* R, int64_t ldr, int* nblk_out);
+
+}  // namespace pase

@@ -1,0 +1,233 @@
+"""ctypes binding of libpase.so (include/pase.h): argument marshalling only.
+
+Array arguments may be numpy arrays (host memory), CPU torch tensors, or CUDA torch
+tensors (device memory); they must be C-contiguous float64 (int64/int32 for CSR index
+arrays).  Multivectors are row-major [N][m].
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpase.so")
+
+PASE_OK = 0
+PASE_ERR_NOT_CONVERGED = -6
+PASE_PREC_FP64 = 0
+PASE_PREC_MIXED = 1
+PASE_SOLVER_VCYCLE = 0
+PASE_SOLVER_CG = 1
+
+
+class PaseCSR(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class PaseOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("linear_solver", ctypes.c_int),
+                ("inner_steps", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega", ctypes.c_double), ("coarse_level", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
+                ("aug_tol", ctypes.c_double), ("verbose", ctypes.c_int)]
+
+
+class PaseStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 5), ("aug_iterations", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "converged": self.converged,
+                "max_residual": self.max_residual, "solve_ms": self.solve_ms,
+                "phase_ms": list(self.phase_ms), "aug_iterations": self.aug_iterations,
+                "kernel_launches": self.kernel_launches}
+
+
+class PaseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pase error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
+            "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
+            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_kernel_count",
+            "pase_destroy", "pase_status_string", "pase_last_error"]
+
+
+def load_library(path=LIB_PATH):
+    """Load libpase.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(python paper_2502_04589_gb300/build.py); no CPU fallback exists")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.pase_default_options.argtypes = [ctypes.POINTER(PaseOptions)]
+    L.pase_default_options.restype = None
+    L.pase_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PaseOptions), vp]
+    L.pase_setup.argtypes = [vp, ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR), i32,
+                             ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR)]
+    L.pase_reserve.argtypes = [vp, i32]
+    L.pase_solve.argtypes = [vp, i32, dbl, i32, vp, vp, vp, ctypes.POINTER(PaseStats)]
+    L.pase_residual.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.pase_linear_solve.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.pase_project.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.pase_augmented_eig.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]
+    L.pase_prolongate.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.pase_iterate.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
+    L.pase_kernel_count.argtypes = [vp]
+    L.pase_kernel_count.restype = i64
+    L.pase_destroy.argtypes = [vp]
+    L.pase_status_string.argtypes = [i32]
+    L.pase_status_string.restype = ctypes.c_char_p
+    L.pase_last_error.argtypes = []
+    L.pase_last_error.restype = ctypes.c_char_p
+    for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_residual",
+                 "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
+                 "pase_iterate", "pase_spmm_am", "pase_destroy"]:
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc, allow=()):
+    if rc != PASE_OK and rc not in allow:
+        L = load_library()
+        raise PaseError(rc, f"{L.pase_status_string(rc).decode()}: {L.pase_last_error().decode()}")
+    return rc
+
+
+def _ptr(a, dtype=np.float64):
+    """Raw pointer of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    # torch tensor
+    if not a.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    want = {np.float64: "torch.float64", np.int64: "torch.int64", np.int32: "torch.int32"}[dtype]
+    if str(a.dtype) != want:
+        raise TypeError(f"expected {want}, got {a.dtype}")
+    return a.data_ptr()
+
+
+def _is_device(a):
+    return (not isinstance(a, np.ndarray)) and getattr(a, "is_cuda", False)
+
+
+def make_csr(indptr, indices, data, shape):
+    """PaseCSR view of CSR arrays (numpy host arrays or torch tensors, all on one side).
+    The caller keeps the arrays alive for the duration of the call."""
+    dev = _is_device(data)
+    return PaseCSR(int(shape[0]), int(shape[1]), int(len(indices)), _ptr(indptr, np.int64),
+                   _ptr(indices, np.int32), _ptr(data, np.float64), 1 if dev else 0)
+
+
+def csr_from_scipy(A):
+    """(PaseCSR, keep-alive tuple) for a scipy CSR matrix."""
+    indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(A.indices, dtype=np.int32)
+    data = np.ascontiguousarray(A.data, dtype=np.float64)
+    return make_csr(indptr, indices, data, A.shape), (indptr, indices, data)
+
+
+def pase_default_options():
+    o = PaseOptions()
+    load_library().pase_default_options(ctypes.byref(o))
+    return o
+
+
+def pase_create(opt=None, stream=None):
+    """Handle on the given CUDA stream (int handle, torch.cuda.Stream, or None)."""
+    L = load_library()
+    h = ctypes.c_void_p()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(L.pase_create(ctypes.byref(h), ctypes.byref(opt) if opt is not None else None,
+                         ctypes.c_void_p(s) if s else None))
+    return h
+
+
+def pase_setup(h, A_h, M_h, P, A_H, M_H):
+    """A_h, M_h, A_H, M_H: scipy CSR; P: list of scipy CSR (the interpolation chain)."""
+    keep = []
+    def conv(X):
+        c, k = csr_from_scipy(X)
+        keep.append(k)
+        return c
+    cA, cM, cAH, cMH = conv(A_h), conv(M_h), conv(A_H), conv(M_H)
+    arr = (PaseCSR * len(P))(*[conv(p) for p in P])
+    return _check(load_library().pase_setup(h, ctypes.byref(cA), ctypes.byref(cM), len(P), arr,
+                                            ctypes.byref(cAH), ctypes.byref(cMH)))
+
+
+def pase_reserve(h, m):
+    return _check(load_library().pase_reserve(h, m))
+
+
+def pase_solve(h, nev, tol, m, U0, lam, U):
+    """Returns (status, stats dict); status may be PASE_ERR_NOT_CONVERGED."""
+    st = PaseStats()
+    rc = _check(load_library().pase_solve(h, nev, tol, m, _ptr(U0), _ptr(lam), _ptr(U),
+                                          ctypes.byref(st)), allow=(PASE_ERR_NOT_CONVERGED,))
+    return rc, st.as_dict()
+
+
+def pase_residual(h, m, U, lam, R, relres):
+    return _check(load_library().pase_residual(h, m, _ptr(U), _ptr(lam), _ptr(R), _ptr(relres)))
+
+
+def pase_linear_solve(h, m, U, lam, R, W):
+    return _check(load_library().pase_linear_solve(h, m, _ptr(U), _ptr(lam), _ptr(R), _ptr(W)))
+
+
+def pase_project(h, m, W, aH, bH, GA, GM):
+    return _check(load_library().pase_project(h, m, _ptr(W), _ptr(aH), _ptr(bH), _ptr(GA), _ptr(GM)))
+
+
+def pase_augmented_eig(h, m, aH, bH, GA, GM, lam, C_H, C_W):
+    it = ctypes.c_int(0)
+    _check(load_library().pase_augmented_eig(h, m, _ptr(aH), _ptr(bH), _ptr(GA), _ptr(GM),
+                                             _ptr(lam), _ptr(C_H), _ptr(C_W), ctypes.byref(it)))
+    return it.value
+
+
+def pase_prolongate(h, m, W, C_H, C_W, U):
+    return _check(load_library().pase_prolongate(h, m, _ptr(W), _ptr(C_H), _ptr(C_W), _ptr(U)))
+
+
+def pase_iterate(h, m, U, lam, do_linear_solve=True, relres=None):
+    return _check(load_library().pase_iterate(h, m, _ptr(U), _ptr(lam), 1 if do_linear_solve else 0,
+                                              _ptr(relres)))
+
+
+def pase_spmm_am(h, m, X, AX, MX):
+    return _check(load_library().pase_spmm_am(h, m, _ptr(X), _ptr(AX), _ptr(MX)))
+
+
+def pase_kernel_count(h):
+    return int(load_library().pase_kernel_count(h))
+
+
+def pase_destroy(h):
+    return _check(load_library().pase_destroy(h))
+
+
+def pase_status_string(code):
+    return load_library().pase_status_string(code).decode()
+
+
+def pase_last_error():
+    return load_library().pase_last_error().decode()

@@ -1,0 +1,320 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
+
+Tolerances (FP64 path): kernels that only reorder a sum (sparse products, Gram blocks,
+restriction, prolongation, V-cycle) agree to 1e-12 relative in the norm of each column;
+eigenvalues to 1e-10 relative (the accuracy target of the method); eigenvectors by
+subspace (degenerate Laplace pairs may come back rotated); relative residuals of the
+returned pairs <= the requested tolerance, recomputed on the CPU by the oracle.
+"""
+import numpy as np
+import pytest
+
+import pase_inputs as pin
+from oracle import dense, mg, pase as opase, spectrum
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2502_04589_gb300.pase")
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _colrel(a, b):
+    return np.max(np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300))
+
+
+class Ctx:
+    def __init__(self, pb, precision=P.PASE_PREC_FP64, **kw):
+        self.pb = pb
+        opt = P.pase_default_options()
+        opt.precision = precision
+        opt.coarse_level = pb.coarse_level
+        for k, v in kw.items():
+            setattr(opt, k, v)
+        self.h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+        try:
+            P.pase_setup(self.h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        except Exception:
+            P.pase_destroy(self.h)
+            raise
+
+    def close(self):
+        P.pase_destroy(self.h)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def p2d():
+    return pin.build_problem(2, 64, 8, mg_min=4)
+
+
+@pytest.fixture(scope="module")
+def p3d():
+    return pin.build_problem(3, 32, 8, kappa_seed=5, mg_min=4)
+
+
+@pytest.mark.parametrize("which,m", [("p2d", 8), ("p2d", 24), ("p3d", 16), ("p3d", 40)])
+def test_spmm_am_parity(which, m, request):
+    pb = request.getfixturevalue(which)
+    c = Ctx(pb)
+    try:
+        X = pin.start_vectors(3, pb.N, m)
+        AX = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        MX = torch.empty_like(AX)
+        P.pase_spmm_am(c.h, m, dev(X), AX, MX)
+        assert _colrel(host(AX), pb.A @ X) < 1e-13
+        assert _colrel(host(MX), pb.M @ X) < 1e-13
+    finally:
+        c.close()
+
+
+def test_residual_parity(p3d):
+    pb = p3d
+    m = 16
+    c = Ctx(pb)
+    try:
+        U = pin.start_vectors(4, pb.N, m)
+        lam = np.linspace(10.0, 200.0, m)
+        R = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        rr = torch.empty(m, dtype=torch.float64, device="cuda")
+        P.pase_residual(c.h, m, dev(U), dev(lam), R, rr)
+        Rref = (pb.M @ U) * lam - pb.A @ U
+        assert _colrel(host(R), Rref) < 1e-13
+        np.testing.assert_allclose(host(rr), opase.relative_residuals(pb.A, pb.M, U, lam), rtol=1e-12)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("which", ["p2d", "p3d"])
+def test_linear_solve_parity(which, request):
+    pb = request.getfixturevalue(which)
+    m = 16
+    c = Ctx(pb)
+    try:
+        U = pin.start_vectors(5, pb.N, m)
+        lam = np.linspace(20.0, 300.0, m)
+        W = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        P.pase_linear_solve(c.h, m, dev(U), dev(lam), None, W)
+        hier = mg.Hierarchy(pb.A, pb.chain)
+        Wref = opase.linear_solve(pb.A, pb.M, U, lam, 2, hier)
+        assert _colrel(host(W) - U, Wref - U) < 1e-11
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("which", ["p2d", "p3d"])
+def test_project_parity(which, request):
+    pb = request.getfixturevalue(which)
+    m = 24
+    c = Ctx(pb)
+    try:
+        W = pin.start_vectors(6, pb.N, m)
+        aH = torch.empty(pb.N_H, m, dtype=torch.float64, device="cuda")
+        bH, GA, GM = torch.empty_like(aH), torch.empty(m, m, dtype=torch.float64, device="cuda"), None
+        GM = torch.empty_like(GA)
+        P.pase_project(c.h, m, dev(W), aH, bH, GA, GM)
+        ra, rb, rga, rgm = opase.projection(pb.A, pb.M, pb.P, W)
+        assert _colrel(host(aH), ra) < 1e-12
+        assert _colrel(host(bH), rb) < 1e-12
+        assert _rel(host(GA), rga) < 1e-12
+        assert _rel(host(GM), rgm) < 1e-12
+        assert np.array_equal(host(GA), host(GA).T)  # exactly symmetric
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("which,m", [("p2d", 8), ("p2d", 16), ("p3d", 24)])
+def test_augmented_eig_parity(which, m, request):
+    pb = request.getfixturevalue(which)
+    c = Ctx(pb)
+    try:
+        lam_d, U_d = dense.smallest_pairs(pb.A, pb.M, m)
+        W = U_d + 1e-3 * pin.start_vectors(7, pb.N, m)  # near-converged block, as in late iterations
+        ra, rb, rga, rgm = opase.projection(pb.A, pb.M, pb.P, W)
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        CH = torch.empty(pb.N_H, m, dtype=torch.float64, device="cuda")
+        CW = torch.empty(m, m, dtype=torch.float64, device="cuda")
+        it = P.pase_augmented_eig(c.h, m, dev(ra), dev(rb), dev(rga), dev(rgm), lam, CH, CW)
+        lref, CHref, CWref = opase.augmented_eig(pb.A_H, pb.M_H, ra, rb, rga, rgm, m)
+        np.testing.assert_allclose(host(lam), lref, rtol=1e-10)
+        U = opase.prolongate(pb.P, W, host(CH), host(CW))
+        Uref = opase.prolongate(pb.P, W, CHref, CWref)
+        # M-orthonormal, and the same invariant subspaces (compare M-projectors)
+        np.testing.assert_allclose(U.T @ (pb.M @ U), np.eye(m), atol=1e-10)
+        G = Uref.T @ (pb.M @ U)
+        np.testing.assert_allclose(G.T @ G, np.eye(m), atol=1e-8)
+        assert it >= 0
+    finally:
+        c.close()
+
+
+def test_prolongate_parity(p3d):
+    pb = p3d
+    m = 16
+    c = Ctx(pb)
+    try:
+        W = pin.start_vectors(8, pb.N, m)
+        CH = pin.start_vectors(9, pb.N_H, m)
+        CW = pin.start_vectors(10, m, m)
+        U = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        P.pase_prolongate(c.h, m, dev(W), dev(CH), dev(CW), U)
+        assert _colrel(host(U), opase.prolongate(pb.P, W, CH, CW)) < 1e-13
+    finally:
+        c.close()
+
+
+def test_one_iteration_parity(p2d):
+    """One whole iteration from identical inputs: Ritz values and vectors vs the oracle."""
+    pb = p2d
+    m = 8
+    c = Ctx(pb)
+    try:
+        S = opase.Solver(pb.A, pb.M, pb.chain, coarse_level=pb.coarse_level)
+        U0 = pin.start_vectors(0, pb.N, m)
+        lam1, U1, _ = S.iteration(U0, None, 2, solve=False)  # first iteration: W = U0
+        lam2, U2, inter = S.iteration(U1, lam1, 2, solve=True)
+        Ug = dev(U0)
+        lg = torch.zeros(m, dtype=torch.float64, device="cuda")
+        P.pase_iterate(c.h, m, Ug, lg, False)
+        np.testing.assert_allclose(host(lg), lam1, rtol=1e-9)
+        # continue from the oracle's block so both see the same input
+        Ug = dev(U1)
+        lg = dev(lam1)
+        P.pase_iterate(c.h, m, Ug, lg, True)
+        np.testing.assert_allclose(host(lg), lam2, rtol=1e-10)
+        G = U2.T @ (pb.M @ host(Ug))
+        np.testing.assert_allclose(np.abs(G.T @ G), np.eye(m), atol=1e-7)
+    finally:
+        c.close()
+
+
+def test_iterate_host_pointers_match_device(p2d):
+    pb = p2d
+    m = 8
+    c = Ctx(pb)
+    try:
+        U0 = pin.start_vectors(11, pb.N, m)
+        Uh = U0.copy()
+        lh = np.zeros(m)
+        P.pase_iterate(c.h, m, Uh, lh, False)
+        Ud = dev(U0)
+        ld = torch.zeros(m, dtype=torch.float64, device="cuda")
+        P.pase_iterate(c.h, m, Ud, ld, False)
+        np.testing.assert_array_equal(lh, host(ld))
+        np.testing.assert_array_equal(Uh, host(Ud))
+    finally:
+        c.close()
+
+
+def _solve(pb, nev, tol=1e-9, precision=P.PASE_PREC_FP64, m=None, seed=0, **kw):
+    m = m or pin.guard_columns(nev)
+    c = Ctx(pb, precision, **kw)
+    try:
+        U0 = dev(pin.start_vectors(seed, pb.N, m))
+        U = torch.empty_like(U0)
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        rc, st = P.pase_solve(c.h, nev, tol, m, U0, lam, U)
+        return rc, st, host(lam), host(U)
+    finally:
+        c.close()
+
+
+def _check_pairs(pb, lam, U, nev, ref, tol):
+    np.testing.assert_allclose(lam[:nev], ref[:nev], rtol=1e-10)
+    res = opase.relative_residuals(pb.A, pb.M, U[:, :nev], lam[:nev])
+    assert np.all(res <= tol), res
+    np.testing.assert_allclose(U.T @ (pb.M @ U), np.eye(U.shape[1]), atol=1e-10)
+
+
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_solve_laplace_2d_128(precision):
+    """Config 1: 2D Q1 128x128, coarse 16x16, nev 10, two V-cycles per iteration."""
+    pb = pin.build_problem(2, 128, 16, mg_min=4)
+    rc, st, lam, U = _solve(pb, 10, 1e-8, precision)
+    assert rc == P.PASE_OK, st
+    _check_pairs(pb, lam, U, 10, spectrum.q1_laplace_eigenvalues(2, 128, 10), 1e-8)
+
+
+def test_solve_variable_kappa_2d():
+    pb = pin.build_problem(2, 64, 8, kappa_seed=21, mg_min=4)
+    nev = 6
+    rc, st, lam, U = _solve(pb, nev, 1e-9)
+    assert rc == P.PASE_OK, st
+    ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+    _check_pairs(pb, lam, U, nev, ref, 1e-9)
+
+
+def test_solve_laplace_3d_32_cluster():
+    """3D with a degenerate cluster cut by the block: nev = 10 sits inside the 10..12
+    cluster? (k = (1,1,2) perms are 2..4, (1,2,2) 5..7, (1,1,3) 8..10, (2,2,2) 11)."""
+    pb = pin.build_problem(3, 32, 8, mg_min=4)
+    nev = 10
+    rc, st, lam, U = _solve(pb, nev, 1e-8)
+    assert rc == P.PASE_OK, st
+    _check_pairs(pb, lam, U, nev, spectrum.q1_laplace_eigenvalues(3, 32, nev), 1e-8)
+
+
+def test_coarse_start():
+    pb = pin.build_problem(2, 64, 8, mg_min=4)
+    nev, m = 5, 16
+    c = Ctx(pb)
+    try:
+        U = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        rc, st = P.pase_solve(c.h, nev, 1e-9, m, None, lam, U)
+        assert rc == P.PASE_OK
+        _check_pairs(pb, host(lam), host(U), nev, spectrum.q1_laplace_eigenvalues(2, 64, nev), 1e-9)
+    finally:
+        c.close()
+
+
+def test_minimum_block_and_nev1():
+    pb = pin.build_problem(2, 32, 4, mg_min=4)
+    rc, st, lam, U = _solve(pb, 1, 1e-9, m=8)
+    assert rc == P.PASE_OK
+    np.testing.assert_allclose(lam[0], spectrum.q1_laplace_eigenvalues(2, 32, 1)[0], rtol=1e-10)
+
+
+def test_not_converged_status():
+    pb = pin.build_problem(2, 64, 8, mg_min=4)
+    rc, st, lam, U = _solve(pb, 4, 1e-14, m=8, max_iter=2)
+    assert rc == P.PASE_ERR_NOT_CONVERGED and st["iterations"] == 2
+
+
+def test_errors_are_reported_not_raised_on_device(p2d):
+    pb = p2d
+    # pattern mismatch
+    opt = P.pase_default_options()
+    opt.coarse_level = pb.coarse_level
+    h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+    try:
+        M2 = pb.M.copy().tolil()
+        M2[0, 5] = 1e-3
+        M2[5, 0] = 1e-3
+        with pytest.raises(P.PaseError) as e:
+            P.pase_setup(h, pb.A, M2.tocsr(), pb.chain, pb.A_H, pb.M_H)
+        assert e.value.code == -3
+        # solve before setup
+        with pytest.raises(P.PaseError) as e:
+            P.pase_reserve(h, 8)
+        assert e.value.code == -10
+    finally:
+        P.pase_destroy(h)
+    c = Ctx(pb)
+    try:
+        with pytest.raises(P.PaseError) as e:
+            P.pase_reserve(c.h, 12)
+        assert e.value.code == -1
+    finally:
+        c.close()
