@@ -174,9 +174,9 @@ def run_ours(args):
     lam = torch.zeros(m, dtype=torch.float64, device="cuda")
     relres = torch.zeros(m, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
-        P.pase_iterate(h, m, U, lam, False)  # first iteration: W = U0
+        P.pase_iterate(h, NEV, m, U, lam, False)  # first iteration: W = U0
         for _ in range(args.warmup):
-            P.pase_iterate(h, m, U, lam, True, relres)
+            P.pase_iterate(h, NEV, m, U, lam, True, relres)
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
@@ -185,7 +185,7 @@ def run_ours(args):
     barrier()
     ev0.record(stream)
     for _ in range(args.steps):
-        P.pase_iterate(h, m, U, lam, True, relres)
+        P.pase_iterate(h, NEV, m, U, lam, True, relres)
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
@@ -229,7 +229,7 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        P.pase_iterate(h, m, Uh.numpy(), lh.numpy(), True, rh.numpy())
+        P.pase_iterate(h, NEV, m, Uh.numpy(), lh.numpy(), True, rh.numpy())
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": world * pb.N * NEV / e2e_s, "unit": UNIT,

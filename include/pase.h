@@ -70,8 +70,10 @@ typedef struct {
   int coarse_level;    /* level of the P chain that is V_H; -1 (default) = the last level      */
   int max_iter;        /* outer iterations (default 100)                                       */
   int aug_max_iter;    /* inner iterations of the step-(c) block eigensolver (default 60)      */
-  double aug_tol;      /* inner relative residual target (default 1e-13)                       */
-  int verbose;         /* 0 silent, 1 per-iteration line on stderr                             */
+  double aug_tol;      /* inner relative residual target (default 1e-12)                       */
+  int aug_adaptive;    /* 1 (default): inner target max(aug_tol, 1e-3 x current outer residual);
+                          0: always aug_tol                                                     */
+  int verbose;         /* 0 silent, 1 per-iteration line on stderr, 2 also inner iterations    */
 } pase_options;
 
 /* Per-solve statistics (all times in milliseconds, device-event timed). */
@@ -107,8 +109,8 @@ int pase_create(pase_handle* h, const pase_options* opt, void* cuda_stream);
 
 /* Alg. 3 "Require": fine pencil (A_h, M_h), the interpolation chain and the coarse pencil.
  * P[k] (k = 0..n_interp-1) interpolates level k+1 to level k, level 0 being V_h; their
- * product P[0] P[1] ... P[c-1], c = coarse_level, is I_H^h (§3: "a sequence of
- * interpolation matrices").  Levels below c serve the multigrid solver only.  A_H and
+ * product P[0] P[1] ... P[c-1], c = coarse_level, is I_H^h (§3 lets the interpolation be
+ * one matrix or a product of several).  Levels below c serve the multigrid solver only.  A_H and
  * M_H live on level c.  A_h and M_h must share one sparsity pattern (as do A_H, M_H).
  * Setup validates the CSR arrays, builds the Galerkin multigrid levels
  * A_{k+1} = P[k]^T A_k P[k], the direct interpolation I_H^h and its transpose, a dense
@@ -157,8 +159,10 @@ int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H,
                     const double* C_W, double* U);
 
 /* One whole iteration in place: residual of (U, lambda) -> relres (if not NULL), then
- * (a) unless do_linear_solve == 0, (b), (c), (d); U and lambda are overwritten. */
-int pase_iterate(pase_handle h, int m, double* U, double* lambda, int do_linear_solve,
+ * (a) unless do_linear_solve == 0, (b), (c), (d); U and lambda are overwritten.  nev
+ * (1 <= nev <= m) names the wanted pairs: step (c) converges the first
+ * nev + (m - nev)/2 columns, to the adaptive inner target when opt.aug_adaptive is set. */
+int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int do_linear_solve,
                  double* relres);
 
 /* Fused A_h / M_h product on the fine level: AX = A_h X, MX = M_h X (device pointers,

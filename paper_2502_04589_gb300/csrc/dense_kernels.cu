@@ -329,9 +329,10 @@ int small_chol_solve(pase_ctx* h, int n, int nrhs, double* S, int lds, double* B
 // K = L^-1 (D GA D) L^-T; Householder tridiagonalisation Q^T K Q = T; eigenvalues of T by
 // bisection on Sturm counts; eigenvectors of T by inverse iteration (vectors of one
 // cluster re-orthogonalised against each other); back-transform c = D L^-T Q z.
-// Output C (n x k, ldc) is GB-orthonormal.  status[0] = 1 if the scaled GB has a
-// Cholesky pivot below piv_tol (numerically dependent basis).
-constexpr double kPivTol = 1e-11;
+// Output C (n x k, ldc) is GB-orthonormal.  Directions of a numerically dependent basis
+// (scaled Cholesky pivot below kPivTol) are dropped; status[0] = 1 only if fewer than k
+// directions remain.
+constexpr double kPivTol = 1e-10;
 
 __device__ int sturm_count(int n, const double* d, const double* e, double x) {
   // number of eigenvalues of T strictly below x
@@ -422,11 +423,11 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
   int* ipiv = reinterpret_cast<int*>(iw + (int64_t)4 * n * k);  // n k
   if (tid == 0) s_fail = 0;
   __syncthreads();
-  // 1. scaling
+  // 1. scaling; a zero column (a locked search direction) gets scale 0 and is dropped
   for (int i = tid; i < n; i += nt) {
     const double g = GB[(int64_t)i * ldb + i];
-    if (!(g > 0.0) || !isfinite(g)) s_fail = 1;
-    sc[i] = (g > 0.0) ? rsqrt(g) : 1.0;
+    if (!(g >= 0.0) || !isfinite(g)) s_fail = 1;
+    sc[i] = (g > 0.0) ? rsqrt(g) : 0.0;
   }
   __syncthreads();
   if (s_fail) {
@@ -440,26 +441,40 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
     L[idx] = s * 0.5 * (GB[(int64_t)i * ldb + j] + GB[(int64_t)j * ldb + i]);
   }
   __syncthreads();
-  // 2. Cholesky (lower, in place in L)
+  // 2. Cholesky (lower, in place in L) with dropping: a pivot below kPivTol (relative to
+  //    the unit diagonal after scaling) marks a direction numerically dependent on the
+  //    earlier ones; its column is zeroed, L[j][j] = 1, and the direction is later given an
+  //    eigenvalue above the whole spectrum so that no returned vector uses it.
+  __shared__ int s_drop;
+  if (tid == 0) s_drop = 0;
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
+    const double dj = L[(int64_t)j * n + j];
+    const bool drop = !(dj > kPivTol) || !isfinite(dj);
+    __syncthreads();
     if (tid == 0) {
-      const double dj = L[(int64_t)j * n + j];
-      if (!(dj > kPivTol) || !isfinite(dj)) s_fail = 1;
-      else L[(int64_t)j * n + j] = sqrt(dj);
+      L[(int64_t)j * n + j] = drop ? 1.0 : sqrt(dj);
+      if (drop) {
+        ++s_drop;
+        tau[j] = 1.0;  // tau doubles as the drop mask until step 4
+      } else {
+        tau[j] = 0.0;
+      }
     }
     __syncthreads();
-    if (s_fail) break;
     const double ljj = L[(int64_t)j * n + j];
-    for (int i = j + 1 + tid; i < n; i += nt) L[(int64_t)i * n + j] /= ljj;
+    for (int i = j + 1 + tid; i < n; i += nt) L[(int64_t)i * n + j] = drop ? 0.0 : L[(int64_t)i * n + j] / ljj;
     __syncthreads();
-    const int len = n - j - 1;
-    for (int idx = tid; idx < len * len; idx += nt) {
-      const int i = j + 1 + idx / len, l = j + 1 + idx % len;
-      if (l <= i) L[(int64_t)i * n + l] -= L[(int64_t)i * n + j] * L[(int64_t)l * n + j];
+    if (!drop) {
+      const int len = n - j - 1;
+      for (int idx = tid; idx < len * len; idx += nt) {
+        const int i = j + 1 + idx / len, l = j + 1 + idx % len;
+        if (l <= i) L[(int64_t)i * n + l] -= L[(int64_t)i * n + j] * L[(int64_t)l * n + j];
+      }
     }
     __syncthreads();
   }
-  if (s_fail) {
+  if (n - s_drop < k) {
     if (tid == 0) status[0] = 1;
     return;
   }
@@ -492,6 +507,17 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
     }
   }
   __syncthreads();
+  if (s_drop > 0) {
+    double part = 0.0;
+    for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) part = fmax(part, fabs(K[idx]));
+    // block max via sum of squares bound (cheap and safe as an upper bound of |K|_max)
+    const double big = 1e3 * (sqrt(block_sum(part * part, red)) * n + 1.0);
+    for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
+      const int i = (int)(idx / n), j = (int)(idx % n);
+      if (tau[i] != 0.0 || tau[j] != 0.0) K[idx] = (i == j) ? big : 0.0;
+    }
+    __syncthreads();
+  }
   // 4. Householder tridiagonalisation; reflector j acts on rows/cols j+1..n-1 and its
   //    vector (v[0] = 1 implicit) is kept in K[(j+1..n-1)*n + j], tau[j].
   for (int j = 0; j + 2 < n; ++j) {

@@ -496,8 +496,11 @@ static int sync_small(pase_ctx* h, const double* dsrc, int count, const int* dst
 // Block eigensolver for the m smallest pairs of (A, B): locally optimal block
 // preconditioned iteration on the basis [X, W, P] (W = T R, P = previous step), each
 // step a Rayleigh-Ritz on the basis (the X, P, W blocks and the Rayleigh-Ritz of GCG_AUG,
-// Alg. 4; P is the last update direction).  On entry S[:, 0:m] holds the start block; on
-// exit S[:, 0:m] = X (B-orthonormal), lam (device) its Ritz values.  Returns iterations.
+// Alg. 4; P is the last update direction).  W and P are B-orthogonalised against X twice
+// and every operator product is recomputed (implicit updates lose accuracy once the
+// block has converged past ~1e-9); converged columns are soft-locked.
+// On entry S[:, 0:m] holds the start block; on exit S[:, 0:m] = X (B-orthonormal), lam
+// (device) its Ritz values.
 static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double tol, int maxit, int nconv,
                              int* iters_out) {
   Work& w = h->w;
@@ -514,13 +517,11 @@ static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double
   PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
   if (w.h_status[0] != 0) return fail(PASE_ERR_NOT_SPD, "block eigensolver: start block is not B-independent");
   PASE_TRY(ts_gemm(h, n, m, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
-  PASE_TRY(ts_gemm(h, n, m, m, 1.0, AS, m3, w.Cs, m, 0.0, w.AXn, m));
-  PASE_TRY(ts_gemm(h, n, m, m, 1.0, BS, m3, w.Cs, m, 0.0, w.BXn, m));
   PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
-  PASE_TRY(launch_copy_cols(h, n, m, w.AXn, m, AS, m3));
-  PASE_TRY(launch_copy_cols(h, n, m, w.BXn, m, BS, m3));
+  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
   bool haveP = false;
   int it = 0;
+  std::vector<double> hist;
   for (it = 1; it <= maxit; ++it) {
     // residual and convergence
     int nb = 0;
@@ -531,45 +532,43 @@ static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double
     double worst = 0.0;
     for (int j = 0; j < nconv; ++j) worst = std::max(worst, w.h_small[j]);
     if (!(worst == worst)) return fail(PASE_ERR_NAN, "block eigensolver: NaN residual");
+    if (h->opt.verbose >= 2) fprintf(stderr, "[pase]   block eigensolver it %d worst %.3e (tol %.1e)\n", it, worst, tol);
     if (worst <= tol) break;
-    // W = T R, B-orthogonal to X
+    // stagnation at the attainable accuracy of the pencil: no halving in 6 iterations
+    hist.push_back(worst);
+    if (hist.size() > 6 && worst > 0.5 * hist[hist.size() - 7] && worst < 1e-6) break;
+    // soft locking: converged columns contribute no new search direction
+    PASE_TRY(launch_zero_cols_if(h, n, m, m, w.smallvec, tol, w.Rn));
+    // W = T R, B-orthogonal to X (two Gram-Schmidt passes), products computed afresh
     double* Wb = S + m;
     PASE_TRY(op_precond(h, op, w.Rn, m, Wb, m3));
-    PASE_TRY(ts_gram(h, n, m, m, BS, m3, Wb, m3, w.coef, m, false));
-    PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, Wb, m3));
+    for (int pass = 0; pass < 2; ++pass) {
+      PASE_TRY(ts_gram(h, n, m, m, BS, m3, Wb, m3, w.coef, m, false));
+      PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, Wb, m3));
+    }
     PASE_TRY(op_apply(h, op, Wb, m3, AS + m, BS + m, m3));
     int nbw = 2 * m;
     if (haveP) {
-      PASE_TRY(ts_gram(h, n, m, m, BS, m3, w.Pn, m, w.coef, m, false));
-      PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, w.Pn, m));
-      PASE_TRY(ts_gemm(h, n, m, m, -1.0, AS, m3, w.coef, m, 1.0, w.APn, m));
-      PASE_TRY(ts_gemm(h, n, m, m, -1.0, BS, m3, w.coef, m, 1.0, w.BPn, m));
-      PASE_TRY(launch_copy_cols(h, n, m, w.Pn, m, S + 2 * m, m3));
-      PASE_TRY(launch_copy_cols(h, n, m, w.APn, m, AS + 2 * m, m3));
-      PASE_TRY(launch_copy_cols(h, n, m, w.BPn, m, BS + 2 * m, m3));
+      double* Pb = S + 2 * m;
+      PASE_TRY(launch_copy_cols(h, n, m, w.Pn, m, Pb, m3));
+      for (int pass = 0; pass < 2; ++pass) {
+        PASE_TRY(ts_gram(h, n, m, m, BS, m3, Pb, m3, w.coef, m, false));
+        PASE_TRY(ts_gemm(h, n, m, m, -1.0, S, m3, w.coef, m, 1.0, Pb, m3));
+      }
+      PASE_TRY(op_apply(h, op, Pb, m3, AS + 2 * m, BS + 2 * m, m3));
       nbw = m3;
     }
     PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, AS, m3, w.Gq, m3, true));
     PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, BS, m3, w.Gb, m3, true));
     PASE_TRY(small_sygv(h, nbw, m, w.Gq, m3, w.Gb, m3, w.smallvec + m, w.Cs, m, w.status));
     PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
-    if (w.h_status[0] != 0 && nbw == m3) {
-      nbw = 2 * m;  // drop P: the basis became numerically dependent
-      PASE_TRY(small_sygv(h, nbw, m, w.Gq, m3, w.Gb, m3, w.smallvec + m, w.Cs, m, w.status));
-      PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
-    }
-    if (w.h_status[0] != 0) break;  // W itself is dependent on X: nothing left to gain
-    // X = S C, P = S[:, m:] C[m:, :]
+    if (w.h_status[0] != 0) break;  // fewer than m independent directions left
+    // X = S C, P = S[:, m:] C[m:, :]; products of X recomputed
     PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
-    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, AS, m3, w.Cs, m, 0.0, w.AXn, m));
-    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, BS, m3, w.Cs, m, 0.0, w.BXn, m));
     PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, S + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.Pn, m));
-    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, AS + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.APn, m));
-    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, BS + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.BPn, m));
     haveP = true;
     PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
-    PASE_TRY(launch_copy_cols(h, n, m, w.AXn, m, AS, m3));
-    PASE_TRY(launch_copy_cols(h, n, m, w.BXn, m, BS, m3));
+    PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
     PASE_CUDA(cudaMemcpyAsync(lam, w.smallvec + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
   }
   if (iters_out) *iters_out = std::min(it, maxit);
@@ -653,6 +652,7 @@ void pase_default_options(pase_options* o) {
   o->max_iter = 100;
   o->aug_max_iter = 60;
   o->aug_tol = 1e-12;
+  o->aug_adaptive = 1;
   o->verbose = 0;
 }
 
@@ -896,20 +896,34 @@ int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H, co
   return st.finish();
 }
 
-int pase_iterate(pase_handle h, int m, double* U, double* lambda, int do_linear_solve, double* relres) {
+int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int do_linear_solve,
+                 double* relres) {
   PASE_TRY(check_m(h, m));
-  if (!U || !lambda) return fail(PASE_ERR_INVALID_ARG, "pase_iterate: null argument");
+  if (!U || !lambda || nev < 1 || nev > m) return fail(PASE_ERR_INVALID_ARG, "pase_iterate: bad argument");
   Stage st(h);
   const size_t nm = (size_t)h->N * m * sizeof(double);
   void *dU, *dl, *drr;
   PASE_TRY(st.out(U, nm, &dU, true));
   PASE_TRY(st.out(lambda, m * sizeof(double), &dl, true));
   PASE_TRY(st.out(relres, m * sizeof(double), &drr));
+  h->aug_nconv = std::min(m, nev + std::max(1, (m - nev) / 2));
+  h->aug_tol_now = h->opt.aug_tol;
   if (do_linear_solve || drr) {
     PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, h->w.R));
     if (drr) PASE_CUDA(cudaMemcpyAsync(drr, h->w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (do_linear_solve && h->opt.aug_adaptive) {
+      PASE_TRY(sync_small(h, h->w.relres, m, nullptr, 0));
+      double worst = 0.0;
+      for (int j = 0; j < nev; ++j) worst = std::max(worst, h->w.h_small[j]);
+      h->aug_tol_now = std::max(h->opt.aug_tol, 1e-3 * worst);
+    }
+  } else if (h->opt.aug_adaptive) {
+    h->aug_tol_now = std::max(h->opt.aug_tol, 1e-6);
   }
-  PASE_TRY(iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr));
+  const int rc = iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr);
+  h->aug_tol_now = 0;
+  h->aug_nconv = 0;
+  PASE_TRY(rc);
   return st.finish();
 }
 
@@ -1005,9 +1019,9 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
         pase::set_error("maximum number of iterations reached");
         break;
       }
-      h->aug_tol_now = std::max(h->opt.aug_tol, 1e-3 * worst);
+      h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-3 * worst) : h->opt.aug_tol;
     } else {
-      h->aug_tol_now = 1e-6;
+      h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol;
     }
     PASE_TRY(iterate_body(h, w.U, w.lam, do_solve, &st, ev));
     PASE_CUDA(cudaEventSynchronize(ev[4]));

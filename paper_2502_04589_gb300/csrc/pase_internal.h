@@ -166,6 +166,8 @@ int launch_add_f32_to_f64(pase_ctx* h, int64_t count, const double* u, const flo
 int launch_copy_cols(pase_ctx* h, int64_t n, int k, const double* src, int lds, double* dst,
                      int ldd);
 int launch_fill(pase_ctx* h, int64_t count, double v, double* x);
+int launch_zero_cols_if(pase_ctx* h, int64_t n, int m, int64_t ld, const double* crit, double thresh,
+                        double* X);
 int launch_hash_fill(pase_ctx* h, int64_t rows, int cols, int64_t ld, unsigned seed, double* X);
 int launch_set_identity_rows(pase_ctx* h, int64_t row0, int k, int64_t ld, double* X);
 int launch_geam(pase_ctx* h, int64_t rows, int cols, double a, const double* A, int64_t lda,

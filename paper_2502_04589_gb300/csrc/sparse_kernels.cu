@@ -401,6 +401,25 @@ int launch_set_identity_rows(pase_ctx* h, int64_t row0, int k, int64_t ld, doubl
   return PASE_OK;
 }
 
+// Column j of X (rows 0..n-1, stride ld) is zeroed where crit[j] <= thresh.
+__global__ void k_zero_cols_if(int64_t n, int m, int64_t ld, const double* __restrict__ crit,
+                               double thresh, double* __restrict__ X) {
+  const int64_t total = n * m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % m);
+    if (crit[c] <= thresh) X[(i / m) * ld + c] = 0.0;
+  }
+}
+int launch_zero_cols_if(pase_ctx* h, int64_t n, int m, int64_t ld, const double* crit, double thresh,
+                        double* X) {
+  if (n * m == 0) return PASE_OK;
+  k_zero_cols_if<<<ew_grid(n * m), 256, 0, h->stream>>>(n, m, ld, crit, thresh, X);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
 // R = AX - BX diag(lam) over n rows of width m, with per-block column sums of |R|^2 and
 // |BX|^2 in partial[b][2m] (the residual test of the step-(c) block eigensolver).
 __global__ void __launch_bounds__(256) k_block_resid(int64_t n, int m, const double* __restrict__ AX,

@@ -31,7 +31,8 @@ class PaseOptions(ctypes.Structure):
                 ("inner_steps", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarse_level", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
-                ("aug_tol", ctypes.c_double), ("verbose", ctypes.c_int)]
+                ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
+                ("verbose", ctypes.c_int)]
 
 
 class PaseStats(ctypes.Structure):
@@ -83,7 +84,7 @@ def load_library(path=LIB_PATH):
     L.pase_project.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.pase_augmented_eig.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]
     L.pase_prolongate.argtypes = [vp, i32, vp, vp, vp, vp]
-    L.pase_iterate.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.pase_iterate.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
@@ -208,9 +209,9 @@ def pase_prolongate(h, m, W, C_H, C_W, U):
     return _check(load_library().pase_prolongate(h, m, _ptr(W), _ptr(C_H), _ptr(C_W), _ptr(U)))
 
 
-def pase_iterate(h, m, U, lam, do_linear_solve=True, relres=None):
-    return _check(load_library().pase_iterate(h, m, _ptr(U), _ptr(lam), 1 if do_linear_solve else 0,
-                                              _ptr(relres)))
+def pase_iterate(h, nev, m, U, lam, do_linear_solve=True, relres=None):
+    return _check(load_library().pase_iterate(h, nev, m, _ptr(U), _ptr(lam),
+                                              1 if do_linear_solve else 0, _ptr(relres)))
 
 
 def pase_spmm_am(h, m, X, AX, MX):
