@@ -85,9 +85,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def build_workload():
+def build_workload(nfine=NFINE):
     import pase_inputs as pin
-    pb = pin.build_problem(D, NFINE, NCOARSE, mg_min=4)
+    pb = pin.build_problem(D, nfine, NCOARSE, mg_min=4)
     m = pin.guard_columns(NEV)
     return pb, m
 
@@ -151,7 +151,7 @@ def run_ours(args):
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    pb, m = build_workload()
+    pb, m = build_workload(args.size)
 
     def make(precision):
         opt = P.pase_default_options()
@@ -171,6 +171,35 @@ def run_ours(args):
     U0h = pin.start_vectors(SEED + rank, pb.N, m)
     U0 = torch.from_numpy(U0h).cuda()
     U = U0.clone()
+    # dominant-kernel roofline: the fused A_h / M_h product (one pass over the pattern)
+    X = U0.clone()
+    AX, MX = torch.empty_like(X), torch.empty_like(X)
+    reps = 10
+    ksampler = ClockSampler(local)
+    ksampler.start()
+    for _ in range(3):
+        P.pase_spmm_am(h, m, X, AX, MX)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        P.pase_spmm_am(h, m, X, AX, MX)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kclocks = ksampler.stop()
+    spmm_ms = e0.elapsed_time(e1) / reps
+    nnz = pb.A.nnz
+    spmm_flops = 4.0 * nnz * m
+    spmm_bytes = nnz * (4 + 16) + 8 * (pb.N + 1) + 3 * pb.N * m * 8
+    peak_fp64 = 1.25e12
+    roofline = {"bound": "alu", "kernel": "k_csr<double, MV_AM> (fused A_h/M_h SpMM, FP64)",
+                "achieved": spmm_flops / (spmm_ms * 1e-3) / 1e12, "peak": peak_fp64 / 1e12,
+                "unit": "TFLOP/s", "frac": spmm_flops / (spmm_ms * 1e-3) / peak_fp64,
+                "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)",
+                "algorithmic_bytes": spmm_bytes,
+                "achieved_gbs": spmm_bytes / (spmm_ms * 1e-3) / 1e9, "ms": spmm_ms,
+                "clocks": kclocks}
+
     lam = torch.zeros(m, dtype=torch.float64, device="cuda")
     relres = torch.zeros(m, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
@@ -197,30 +226,15 @@ def run_ours(args):
     ms = float(t.item())
     value = world * pb.N * NEV / (ms * 1e-3)
 
-    # dominant-kernel roofline: the fused A_h / M_h product (one pass over the pattern)
-    X = U.clone()
-    AX, MX = torch.empty_like(X), torch.empty_like(X)
-    reps = 10
-    for _ in range(3):
-        P.pase_spmm_am(h, m, X, AX, MX)
+    # the same product on the iterated block (data-dependence check of the kernel time)
+    X.copy_(U)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
         P.pase_spmm_am(h, m, X, AX, MX)
     e1.record(stream)
     torch.cuda.synchronize()
-    spmm_ms = e0.elapsed_time(e1) / reps
-    nnz = pb.A.nnz
-    spmm_flops = 4.0 * nnz * m
-    spmm_bytes = nnz * (4 + 16) + 8 * (pb.N + 1) + 3 * pb.N * m * 8
-    peak_fp64 = 1.25e12
-    roofline = {"bound": "alu", "kernel": "k_csr<double, MV_AM> (fused A_h/M_h SpMM, FP64)",
-                "achieved": spmm_flops / (spmm_ms * 1e-3) / 1e12, "peak": peak_fp64 / 1e12,
-                "unit": "TFLOP/s", "frac": spmm_flops / (spmm_ms * 1e-3) / peak_fp64,
-                "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)",
-                "algorithmic_bytes": spmm_bytes,
-                "achieved_gbs": spmm_bytes / (spmm_ms * 1e-3) / 1e9, "ms": spmm_ms}
+    roofline["ms_on_iterated_block"] = e0.elapsed_time(e1) / reps
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()
@@ -236,6 +250,42 @@ def run_ours(args):
            "h2d_bytes_per_step": int(pb.N * m * 8 + m * 8),
            "d2h_bytes_per_step": int(pb.N * m * 8 + 2 * m * 8)}
     P.pase_destroy(h)
+
+    # per-kernel rooflines on the fine level (library-timed, CUDA events)
+    kernels = {}
+    peaks = {"hbm_gbs": 6783.8}
+    try:
+        peaks.update(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))))
+    except Exception:
+        pass
+    nnz, N = pb.A.nnz, pb.N
+
+    def kinfo(name, ms, flops, nbytes, bound):
+        d = {"ms": ms, "gflop": flops / 1e9, "gbytes": nbytes / 1e9,
+             "tflops": flops / (ms * 1e-3) / 1e12, "gbs": nbytes / (ms * 1e-3) / 1e9}
+        if bound == "alu":
+            d.update(bound="alu", frac=d["tflops"] / 1.25, peak="FP64 1.25 TFLOP/s nominal")
+        else:
+            d.update(bound="hbm", frac=d["gbs"] / peaks["hbm_gbs"], peak=f"HBM {peaks['hbm_gbs']} GB/s measured")
+        return d
+
+    hk = make(P.PASE_PREC_MIXED)
+    for name, flops, nbytes, bound in (
+            ("spmm_am_fp64", 4.0 * nnz * m, nnz * 20 + 8 * (N + 1) + 3 * N * m * 8, "alu"),
+            ("jacobi_fp64", 2.0 * nnz * m, nnz * 12 + 16 * N + 3 * N * m * 8, "alu"),
+            ("jacobi_fp32", 2.0 * nnz * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
+            ("gram_fp64", 1.0 * N * m * (m + 4), 2 * N * m * 8, "alu"),
+            ("prolong_fp64", 2.0 * N * m * m, 2 * N * m * 8, "alu")):
+        try:
+            ms_k = P.pase_time_kernel(hk, name, m, 10)
+            kernels[name] = kinfo(name, ms_k, flops, nbytes, bound)
+        except Exception as exc:  # pragma: no cover
+            kernels[name] = {"error": str(exc)}
+    try:
+        kernels["sygv_m"] = {"ms": P.pase_time_kernel(hk, "sygv", m, 5), "n": m, "k": m, "bound": "latency"}
+    except Exception as exc:  # pragma: no cover
+        kernels["sygv_m"] = {"error": str(exc)}
+    P.pase_destroy(hk)
 
     # whole solve to 1e-8, FP64 and mixed
     solves = {}
@@ -271,15 +321,16 @@ def run_ours(args):
                "sample": "one oracle augmented subspace iteration on the full 128^3 workload (nev 50, block 56)"}
 
     if rank == 0:
+        wl = WORKLOAD if args.size == NFINE else WORKLOAD.replace("128", str(args.size))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded Q1 matrices, SplitMix64 start block)",
-                "config": {"workload": WORKLOAD, "N_h": pb.N, "nnz": pb.A.nnz, "N_H": pb.N_H, "nev": NEV,
+                "config": {"workload": wl, "N_h": pb.N, "nnz": pb.A.nnz, "N_H": pb.N_H, "nev": NEV,
                            "block": m, "linear_solve": "2 V-cycles, damped Jacobi 2+2, omega 2/3",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (block 0.92 GB)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "solve": solves}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -295,6 +346,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size", type=int, default=NFINE,
+                    help="fine mesh size (elements per side); the bench workload is 128")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -169,6 +169,18 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
  * [N][m]).  The hot kernel of steps (b) and the residual; exposed for measurement. */
 int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
 
+/* Device time of one launch of a hot kernel on the fine level of the set-up problem, for
+ * roofline measurement: `reps` back-to-back launches after two warm-up launches, timed
+ * with CUDA events on the handle's stream; *ms_per_launch = the average.  Operands are
+ * deterministic pseudo-random blocks of width m held in the handle's workspace. */
+#define PASE_KERNEL_SPMM_AM_FP64 0  /* fused A_h X, M_h X (FP64)                        */
+#define PASE_KERNEL_JACOBI_FP64 1   /* one damped-Jacobi sweep on A_h (FP64)              */
+#define PASE_KERNEL_JACOBI_FP32 2   /* the same sweep in FP32 (needs PASE_PREC_MIXED)     */
+#define PASE_KERNEL_GRAM_FP64 3     /* W^T Y over N_h rows, symmetric (FP64)               */
+#define PASE_KERNEL_PROLONG_FP64 4  /* W C over N_h rows (FP64)                           */
+#define PASE_KERNEL_SYGV 5          /* small symmetric-definite eigensolver, n = k = m     */
+int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
+
 /* Number of library kernels launched by this handle so far. */
 int64_t pase_kernel_count(pase_handle h);
 

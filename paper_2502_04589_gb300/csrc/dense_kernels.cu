@@ -270,6 +270,22 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+__device__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
 // ------------------------------------------------------------------ small Cholesky solve
 // One CTA: S (n x n, lower used) <- its Cholesky factor L, then B (n x nrhs) <- S^-1 B.
 // status[0] = 1 if a pivot is not positive.
@@ -333,6 +349,7 @@ int small_chol_solve(pase_ctx* h, int n, int nrhs, double* S, int lds, double* B
 // (scaled Cholesky pivot below kPivTol) are dropped; status[0] = 1 only if fewer than k
 // directions remain.
 constexpr double kPivTol = 1e-10;
+constexpr int kClusterRR = 16;
 
 __device__ int sturm_count(int n, const double* d, const double* e, double x) {
   // number of eigenvalues of T strictly below x
@@ -508,10 +525,18 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
   }
   __syncthreads();
   if (s_drop > 0) {
+    // dropped directions get an eigenvalue just above the kept spectrum (Gershgorin
+    // bound of the kept rows), so they are never among the k smallest and do not
+    // inflate the norm that scales the inverse-iteration tolerances
     double part = 0.0;
-    for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) part = fmax(part, fabs(K[idx]));
-    // block max via sum of squares bound (cheap and safe as an upper bound of |K|_max)
-    const double big = 1e3 * (sqrt(block_sum(part * part, red)) * n + 1.0);
+    for (int i = tid; i < n; i += nt) {
+      if (tau[i] != 0.0) continue;
+      double r = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (tau[j] == 0.0) r += fabs(K[(int64_t)i * n + j]);
+      part = fmax(part, r);
+    }
+    const double big = 2.0 * block_max(part, red) + 1.0;
     for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
       const int i = (int)(idx / n), j = (int)(idx % n);
       if (tau[i] != 0.0 || tau[j] != 0.0) K[idx] = (i == j) ? big : 0.0;
@@ -605,9 +630,12 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
     lam[i] = 0.5 * (a + b);
   }
   __syncthreads();
-  // 6. inverse iteration; a cluster = consecutive eigenvalues closer than ctol, owned by
-  //    the thread of its first member
-  const double ctol = 1e-7 * tnorm;
+  // 6. inverse iteration.  Eigenvalues closer than ctol = 1e-6 |T| form a cluster, owned by
+  //    the thread of its first member: its vectors are re-orthogonalised against each
+  //    other (vectors of close eigenvalues computed independently lose orthogonality by
+  //    ~eps |T| / gap) and then rotated by a Rayleigh-Ritz step inside the cluster, so
+  //    that every returned pair has value = Rayleigh quotient of its vector.
+  const double ctol = 1e-6 * tnorm;
   const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
   for (int i = tid; i < k; i += nt) {
     if (i > 0 && lam[i] - lam[i - 1] <= ctol) continue;  // not a cluster head
@@ -621,14 +649,14 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
     for (int q = i; q <= last; ++q) {
       double* z = Z + q;  // column q, stride k
       for (int r = 0; r < n; ++r) bb[r] = hash_unit((unsigned)q, (unsigned)r) + 1e-3;
-      for (int it = 0; it < 4; ++it) {
+      for (int it = 0; it < 3; ++it) {
         tri_solve(n, d, e, lam[q], bb, u0, u1, u2, pv_, tiny);
-        // re-orthogonalise against earlier members of the cluster
-        for (int o = i; o < q; ++o) {
-          double dot = 0.0;
-          for (int r = 0; r < n; ++r) dot += bb[r] * Z[(int64_t)r * k + o];
-          for (int r = 0; r < n; ++r) bb[r] -= dot * Z[(int64_t)r * k + o];
-        }
+        for (int pass = 0; pass < 2; ++pass)
+          for (int o = i; o < q; ++o) {
+            double dot = 0.0;
+            for (int r = 0; r < n; ++r) dot += bb[r] * Z[(int64_t)r * k + o];
+            for (int r = 0; r < n; ++r) bb[r] -= dot * Z[(int64_t)r * k + o];
+          }
         double nrm = 0.0;
         for (int r = 0; r < n; ++r) nrm += bb[r] * bb[r];
         nrm = sqrt(nrm);
@@ -636,6 +664,69 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
         for (int r = 0; r < n; ++r) bb[r] *= inv;
       }
       for (int r = 0; r < n; ++r) z[(int64_t)r * k] = bb[r];
+    }
+    const int s = last - i + 1;
+    if (s >= 2 && s <= kClusterRR) {
+      // H = Q^T T Q for the cluster block Q = Z[:, i..last], then cyclic Jacobi on H
+      double H[kClusterRR * kClusterRR];
+      for (int a = 0; a < s; ++a)
+        for (int b = a; b < s; ++b) {
+          double acc = 0.0;
+          for (int r = 0; r < n; ++r) {
+            double tq = d[r] * Z[(int64_t)r * k + i + b];
+            if (r > 0) tq += e[r - 1] * Z[(int64_t)(r - 1) * k + i + b];
+            if (r < n - 1) tq += e[r] * Z[(int64_t)(r + 1) * k + i + b];
+            acc += Z[(int64_t)r * k + i + a] * tq;
+          }
+          H[a * s + b] = acc;
+          H[b * s + a] = acc;
+        }
+      for (int sweep = 0; sweep < 12; ++sweep) {
+        double off = 0.0;
+        for (int a = 0; a < s; ++a)
+          for (int b = a + 1; b < s; ++b) off += H[a * s + b] * H[a * s + b];
+        if (off <= 1e-32 * (tnorm * tnorm)) break;
+        for (int a = 0; a < s; ++a)
+          for (int b = a + 1; b < s; ++b) {
+            const double hab = H[a * s + b];
+            if (hab == 0.0) continue;
+            const double th = 0.5 * (H[b * s + b] - H[a * s + a]) / hab;
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+            for (int l = 0; l < s; ++l) {  // columns a, b of H
+              const double ha = H[l * s + a], hb = H[l * s + b];
+              H[l * s + a] = c * ha - sn * hb;
+              H[l * s + b] = sn * ha + c * hb;
+            }
+            for (int l = 0; l < s; ++l) {  // rows a, b
+              const double ha = H[a * s + l], hb = H[b * s + l];
+              H[a * s + l] = c * ha - sn * hb;
+              H[b * s + l] = sn * ha + c * hb;
+            }
+            for (int r = 0; r < n; ++r) {  // vectors
+              const double za = Z[(int64_t)r * k + i + a], zb = Z[(int64_t)r * k + i + b];
+              Z[(int64_t)r * k + i + a] = c * za - sn * zb;
+              Z[(int64_t)r * k + i + b] = sn * za + c * zb;
+            }
+          }
+      }
+      // sort the cluster ascending by its Rayleigh quotients
+      for (int a = 0; a < s; ++a) {
+        int best = a;
+        for (int b = a + 1; b < s; ++b)
+          if (H[b * s + b] < H[best * s + best]) best = b;
+        if (best != a) {
+          const double t = H[a * s + a];
+          H[a * s + a] = H[best * s + best];
+          H[best * s + best] = t;
+          for (int r = 0; r < n; ++r) {
+            const double za = Z[(int64_t)r * k + i + a];
+            Z[(int64_t)r * k + i + a] = Z[(int64_t)r * k + i + best];
+            Z[(int64_t)r * k + i + best] = za;
+          }
+        }
+        lam[i + a] = H[a * s + a];
+      }
     }
   }
   __syncthreads();

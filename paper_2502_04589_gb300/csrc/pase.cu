@@ -939,6 +939,65 @@ int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX) 
 
 int64_t pase_kernel_count(pase_handle h) { return h ? h->launches : 0; }
 
+int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch) {
+  PASE_TRY(check_m(h, m));
+  if (reps < 1 || !ms_per_launch) return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: bad arguments");
+  Work& w = h->w;
+  const size_t nm = (size_t)h->N * m;
+  const bool mixed = h->opt.precision == PASE_PREC_MIXED;
+  if (kernel == PASE_KERNEL_JACOBI_FP32 && !mixed)
+    return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
+  if (kernel < 0 || kernel > PASE_KERNEL_SYGV) return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
+  // deterministic operands
+  PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));
+  PASE_TRY(launch_hash_fill(h, h->N, m, m, 8u, w.R));
+  PASE_TRY(launch_hash_fill(h, m, m, m, 9u, w.CW));
+  if (mixed) {
+    PASE_TRY(launch_f64_to_f32(h, nm, w.W, w.fx[0]));
+    PASE_TRY(launch_f64_to_f32(h, nm, w.R, w.fb[0]));
+  }
+  const int m3 = 3 * m;
+  if (kernel == PASE_KERNEL_SYGV) {  // a generic symmetric-definite pair (distinct eigenvalues)
+    PASE_TRY(ts_gram(h, h->N, m, m, w.R, m, w.R, m, w.Gq, m3, true));
+    PASE_TRY(ts_gram(h, h->N, m, m, w.W, m, w.W, m, w.Gb, m3, true));
+  }
+  const Level& L0 = h->lv[0];
+  auto once = [&]() -> int {
+    switch (kernel) {
+      case PASE_KERNEL_SPMM_AM_FP64:
+        return launch_csr<double>(h, CSR_MV_AM, m, L0.A, L0.A.val, h->M0_val, w.W, nullptr, nullptr, nullptr,
+                                  nullptr, 0.0, w.T1, w.T2, nullptr, nullptr);
+      case PASE_KERNEL_JACOBI_FP64:
+        return launch_csr<double>(h, CSR_JACOBI, m, L0.A, L0.A.val, nullptr, w.W, nullptr, w.R, L0.dinv, nullptr,
+                                  h->opt.omega, w.T1, nullptr, nullptr, nullptr);
+      case PASE_KERNEL_JACOBI_FP32:
+        return launch_csr<float>(h, CSR_JACOBI, m, L0.A, L0.A.val32, nullptr, w.fx[0], nullptr, w.fb[0], L0.dinv32,
+                                 nullptr, h->opt.omega, w.ft1[0], nullptr, nullptr, nullptr);
+      case PASE_KERNEL_GRAM_FP64:
+        return ts_gram(h, h->N, m, m, w.W, m, w.R, m, w.GA, m, true);
+      case PASE_KERNEL_PROLONG_FP64:
+        return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
+      case PASE_KERNEL_SYGV:
+        return small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
+    }
+    return PASE_OK;
+  };
+  for (int i = 0; i < 2; ++i) PASE_TRY(once());
+  cudaEvent_t e0, e1;
+  PASE_CUDA(cudaEventCreate(&e0));
+  PASE_CUDA(cudaEventCreate(&e1));
+  PASE_CUDA(cudaEventRecord(e0, h->stream));
+  for (int i = 0; i < reps; ++i) PASE_TRY(once());
+  PASE_CUDA(cudaEventRecord(e1, h->stream));
+  PASE_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  PASE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = (double)ms / reps;
+  return PASE_OK;
+}
+
 int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, double* lambda, double* U,
                pase_stats* stp) {
   if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");

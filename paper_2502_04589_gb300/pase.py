@@ -58,7 +58,8 @@ _lib = None
 
 EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
-            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_kernel_count",
+            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_time_kernel",
+            "pase_kernel_count",
             "pase_destroy", "pase_status_string", "pase_last_error"]
 
 
@@ -86,6 +87,7 @@ def load_library(path=LIB_PATH):
     L.pase_prolongate.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pase_iterate.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
+    L.pase_time_kernel.argtypes = [vp, i32, i32, i32, ctypes.POINTER(dbl)]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
     L.pase_destroy.argtypes = [vp]
@@ -95,7 +97,8 @@ def load_library(path=LIB_PATH):
     L.pase_last_error.restype = ctypes.c_char_p
     for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
-                 "pase_iterate", "pase_spmm_am", "pase_destroy"]:
+                 "pase_iterate", "pase_spmm_am", "pase_time_kernel",
+                 "pase_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -216,6 +219,17 @@ def pase_iterate(h, nev, m, U, lam, do_linear_solve=True, relres=None):
 
 def pase_spmm_am(h, m, X, AX, MX):
     return _check(load_library().pase_spmm_am(h, m, _ptr(X), _ptr(AX), _ptr(MX)))
+
+
+KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
+           "prolong_fp64": 4, "sygv": 5}
+
+
+def pase_time_kernel(h, kernel, m, reps=10):
+    """Average device milliseconds of one launch of a named hot kernel."""
+    ms = ctypes.c_double(0.0)
+    _check(load_library().pase_time_kernel(h, KERNELS.get(kernel, kernel), m, reps, ctypes.byref(ms)))
+    return ms.value
 
 
 def pase_kernel_count(h):
