@@ -169,6 +169,28 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
  * [N][m]).  The hot kernel of steps (b) and the residual; exposed for measurement. */
 int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
 
+/* Residual of a block, for callers that cannot allocate device memory.  Has no
+ * counterpart in the paper: it is pase_residual without a handle and without any device
+ * allocation, for code that runs under a memory arena owning every device byte, inside
+ * another runtime's callbacks that forbid cudaMalloc, or on paths that must not allocate.
+ * Computes R = M U diag(lambda) - A U (R may be NULL) and relres[j] =
+ * ||A u_j - lambda_j M u_j||_2 / (lambda_j ||M u_j||_2) for an n x n pencil in CSR that
+ * shares one pattern (rowptr [n+1], colind [nnz], A_val / M_val [nnz]).
+ * Every pointer must be device memory (no host staging: staging would allocate); U and R
+ * are row-major [n][m] and 16-byte aligned; 8 <= m <= 64, m a multiple of 8 (larger m is
+ * rejected with PASE_ERR_INVALID_ARG).  Work is queued on cuda_stream (NULL = legacy
+ * default stream) and the call returns without synchronising.
+ * Scratch: a fixed 1.19 MiB array in device memory, part of the library image, held by
+ * every GPU that loads the library until the process exits.  The first call on each
+ * device looks up that array's device address (with that device current) and caches it;
+ * make that first call before any stream capture.  All calls on a device share the one
+ * array, so calls whose execution overlaps on the GPU (different streams, other host
+ * threads) race and give wrong results; serialise them.  Nothing from a previous call
+ * is read: each call writes every scratch entry it later reads. */
+int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t* colind,
+                          const double* A_val, const double* M_val, const double* U,
+                          const double* lambda, double* R, double* relres, void* cuda_stream);
+
 /* Device time of one launch of a hot kernel on the fine level of the set-up problem, for
  * roofline measurement: `reps` back-to-back launches after two warm-up launches, timed
  * with CUDA events on the handle's stream; *ms_per_launch = the average.  Operands are

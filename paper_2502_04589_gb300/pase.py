@@ -58,7 +58,8 @@ _lib = None
 
 EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
-            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_time_kernel",
+            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_residual_noalloc",
+            "pase_time_kernel",
             "pase_kernel_count",
             "pase_destroy", "pase_status_string", "pase_last_error"]
 
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
     L.pase_prolongate.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pase_iterate.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
+    L.pase_residual_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.pase_time_kernel.argtypes = [vp, i32, i32, i32, ctypes.POINTER(dbl)]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
@@ -97,7 +99,7 @@ def load_library(path=LIB_PATH):
     L.pase_last_error.restype = ctypes.c_char_p
     for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
-                 "pase_iterate", "pase_spmm_am", "pase_time_kernel",
+                 "pase_iterate", "pase_spmm_am", "pase_residual_noalloc", "pase_time_kernel",
                  "pase_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
@@ -219,6 +221,15 @@ def pase_iterate(h, nev, m, U, lam, do_linear_solve=True, relres=None):
 
 def pase_spmm_am(h, m, X, AX, MX):
     return _check(load_library().pase_spmm_am(h, m, _ptr(X), _ptr(AX), _ptr(MX)))
+
+
+def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres, stream=None):
+    """Residual without any device allocation; every array must be a CUDA tensor.
+    Queued on `stream` (int handle, torch.cuda.Stream or None) without synchronising."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(load_library().pase_residual_noalloc(
+        int(n), int(m), _ptr(rowptr, np.int64), _ptr(colind, np.int32), _ptr(A_val), _ptr(M_val),
+        _ptr(U), _ptr(lam), _ptr(R), _ptr(relres), ctypes.c_void_p(s) if s else None))
 
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
