@@ -281,10 +281,11 @@ def run_ours(args):
             kernels[name] = kinfo(name, ms_k, flops, nbytes, bound)
         except Exception as exc:  # pragma: no cover
             kernels[name] = {"error": str(exc)}
-    try:
-        kernels["sygv_m"] = {"ms": P.pase_time_kernel(hk, "sygv", m, 5), "n": m, "k": m, "bound": "latency"}
-    except Exception as exc:  # pragma: no cover
-        kernels["sygv_m"] = {"error": str(exc)}
+    for name, nn in (("sygv", m), ("sygv3", 3 * m)):
+        try:
+            kernels[name] = {"ms": P.pase_time_kernel(hk, name, m, 5), "n": nn, "k": m, "bound": "latency"}
+        except Exception as exc:  # pragma: no cover
+            kernels[name] = {"error": str(exc)}
     P.pase_destroy(hk)
 
     # whole solve to 1e-8, FP64 and mixed

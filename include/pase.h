@@ -201,6 +201,7 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_GRAM_FP64 3     /* W^T Y over N_h rows, symmetric (FP64)               */
 #define PASE_KERNEL_PROLONG_FP64 4  /* W C over N_h rows (FP64)                           */
 #define PASE_KERNEL_SYGV 5          /* small symmetric-definite eigensolver, n = k = m     */
+#define PASE_KERNEL_SYGV3 6         /* the same with n = 3m, k = m (step-(c) Rayleigh-Ritz) */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
 /* Number of library kernels launched by this handle so far. */

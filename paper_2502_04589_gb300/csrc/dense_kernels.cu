@@ -340,26 +340,52 @@ int small_chol_solve(pase_ctx* h, int n, int nrhs, double* S, int lds, double* B
 }
 
 // ------------------------------------------------------------------ small eigensolver
-// The k smallest pairs of GA c = lambda GB c (n x n symmetric, GB positive definite), one
-// CTA, FP64.  Steps: diagonal scaling D = diag(GB)^-1/2; Cholesky D GB D = L L^T;
-// K = L^-1 (D GA D) L^-T; Householder tridiagonalisation Q^T K Q = T; eigenvalues of T by
-// bisection on Sturm counts; eigenvectors of T by inverse iteration (vectors of one
-// cluster re-orthogonalised against each other); back-transform c = D L^-T Q z.
-// Output C (n x k, ldc) is GB-orthonormal.  Directions of a numerically dependent basis
-// (scaled Cholesky pivot below kPivTol) are dropped; status[0] = 1 only if fewer than k
-// directions remain.
+// The k smallest pairs of GA c = lambda GB c (n x n symmetric, GB positive semi-definite),
+// FP64, as five kernels so that only the inherently sequential parts run on one SM (FP64
+// issues at ~2 FMA/clock per SM on this part, so work spread over many SMs matters):
+//  1. (1 CTA)   scaling D = diag(GB)^-1/2 and Cholesky D GB D = L L^T with dropping of
+//               numerically dependent directions (scaled pivot below kPivTol; a zero
+//               diagonal, i.e. a locked search direction, is dropped too);
+//  2. (n CTAs)  K = L^-1 (D GA D) L^-T by two column-parallel forward substitutions;
+//  3. (1 CTA)   Householder tridiagonalisation Q^T K Q = T, then the k smallest
+//               eigenvalues of T located by multisection on FP32 Sturm counts;
+//  4. (k CTAs)  eigenvectors of T by inverse iteration with Rayleigh-quotient shifts (FP64
+//               accuracy); close eigenvalues form a cluster, re-orthogonalised and rotated
+//               by a Rayleigh-Ritz step inside the cluster; lam[i] = Rayleigh quotient;
+//  5. (k/4 CTAs) back-transform c = D L^-T Q z.
+// Output C (n x k, ldc) is GB-orthonormal.  Dropped directions get an eigenvalue above the
+// kept spectrum; status[0] = 1 only if fewer than k directions remain (or GB is invalid).
 constexpr double kPivTol = 1e-10;
 constexpr int kClusterRR = 16;
 
-__device__ int sturm_count(int n, const double* d, const double* e, double x) {
-  // number of eigenvalues of T strictly below x
+struct SygvWork {
+  double *K, *L, *Y, *Z, *d, *e, *tau, *sc, *lamx;
+  int* info;  // [0] dropped count, [1] cluster flag scratch
+};
+__device__ __host__ inline SygvWork sygv_work(double* w, int n, int k) {
+  SygvWork s;
+  s.K = w;
+  s.L = s.K + (size_t)n * n;
+  s.Y = s.L + (size_t)n * n;
+  s.Z = s.Y + (size_t)n * n;
+  s.d = s.Z + (size_t)n * k;
+  s.e = s.d + n;
+  s.tau = s.e + n;  // drop mask (1 = dropped) in kernels 1-2, reflector taus after kernel 3
+  s.sc = s.tau + n;
+  s.lamx = s.sc + n;
+  s.info = reinterpret_cast<int*>(s.lamx + k + 1);
+  return s;
+}
+
+__device__ int sturm_count_f32(int n, const float* d, const float* e2, float x) {
+  // FP32 count of eigenvalues below x (used only to locate eigenvalues to ~1e-6 |T|)
   int cnt = 0;
-  double q = d[0] - x;
-  if (q < 0) ++cnt;
+  float q = d[0] - x;
+  if (q < 0.f) ++cnt;
   for (int i = 1; i < n; ++i) {
-    if (q == 0.0) q = -DBL_MIN * 1e8;
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (q < 0) ++cnt;
+    if (q == 0.f) q = -1e-30f;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
+    if (q < 0.f) ++cnt;
   }
   return cnt;
 }
@@ -373,34 +399,25 @@ __device__ double hash_unit(unsigned a, unsigned b) {
 }
 
 // Solve (T - lam I) x = b in place (b -> x), tridiagonal LU with partial pivoting.
-// Work arrays l, u0, u1, u2, piv of length n.
 __device__ void tri_solve(int n, const double* d, const double* e, double lam, double* b,
-                          double* u0, double* u1, double* u2, int* piv, double tiny) {
-  // rows: main diag a_i = d_i - lam, sub/super e_i
+                          double* u0, double* u1, double* u2, double tiny) {
   for (int i = 0; i < n; ++i) {
     u0[i] = d[i] - lam;
     u1[i] = (i < n - 1) ? e[i] : 0.0;
     u2[i] = 0.0;
   }
-  // forward elimination with row swaps (u0 diag, u1 first super, u2 second super)
   for (int i = 0; i < n - 1; ++i) {
     const double sub = e[i];  // element (i+1, i)
     if (fabs(u0[i]) >= fabs(sub)) {
-      piv[i] = 0;
       if (u0[i] == 0.0) u0[i] = tiny;
       const double f = sub / u0[i];
       u0[i + 1] -= f * u1[i];
-      // u2[i] stays 0
       b[i + 1] -= f * b[i];
-      u2[i] = 0.0;
-      // store multiplier implicitly (not needed: b updated on the fly)
     } else {
-      piv[i] = 1;
       const double f = u0[i] / sub;
-      // swap rows i and i+1
-      const double r0 = sub, r1 = u0[i + 1], r2 = (i + 1 < n - 1) ? e[i + 1] : 0.0;
+      const double r1 = u0[i + 1], r2 = (i + 1 < n - 1) ? e[i + 1] : 0.0;
       const double o1 = u1[i];
-      u0[i] = r0;
+      u0[i] = sub;
       u1[i] = r1;
       u2[i] = r2;
       u0[i + 1] = o1 - f * r1;
@@ -411,7 +428,6 @@ __device__ void tri_solve(int n, const double* d, const double* e, double lam, d
     }
   }
   if (u0[n - 1] == 0.0) u0[n - 1] = tiny;
-  // back substitution
   b[n - 1] /= u0[n - 1];
   if (n >= 2) {
     b[n - 2] = (b[n - 2] - u1[n - 2] * b[n - 1]) / u0[n - 2];
@@ -419,143 +435,148 @@ __device__ void tri_solve(int n, const double* d, const double* e, double lam, d
   }
 }
 
-__global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __restrict__ GA, int lda,
-                                               const double* __restrict__ GB, int ldb, double* work,
-                                               double* __restrict__ lam, double* __restrict__ C,
-                                               int ldc, int* status) {
-  __shared__ double red[40];
-  __shared__ int s_fail;
-  __shared__ double s_lo, s_hi;
+// 1. scaling + Cholesky with dropping (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) k_sygv_chol(int n, int k, const double* __restrict__ GA, int lda,
+                                                    const double* __restrict__ GB, int ldb, double* work,
+                                                    int* status) {
+  __shared__ int s_fail, s_drop;
+  extern __shared__ double colj[];  // n
+  SygvWork W = sygv_work(work, n, k);
   const int tid = threadIdx.x, nt = blockDim.x;
-  double* K = work;                // n*n  (becomes tridiagonal + Householder vectors)
-  double* L = K + (int64_t)n * n;  // n*n
-  double* Z = L + (int64_t)n * n;  // n*k
-  double* d = Z + (int64_t)n * k;  // n
-  double* e = d + n;               // n
-  double* tau = e + n;             // n
-  double* sc = tau + n;            // n
-  double* v = sc + n;              // n
-  double* p = v + n;               // n
-  double* iw = p + n;              // 4 n k  (inverse iteration scratch)
-  int* ipiv = reinterpret_cast<int*>(iw + (int64_t)4 * n * k);  // n k
-  if (tid == 0) s_fail = 0;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  if (tid == 0) {
+    s_fail = 0;
+    s_drop = 0;
+  }
   __syncthreads();
-  // 1. scaling; a zero column (a locked search direction) gets scale 0 and is dropped
   for (int i = tid; i < n; i += nt) {
     const double g = GB[(int64_t)i * ldb + i];
     if (!(g >= 0.0) || !isfinite(g)) s_fail = 1;
-    sc[i] = (g > 0.0) ? rsqrt(g) : 0.0;
+    W.sc[i] = (g > 0.0) ? rsqrt(g) : 0.0;
   }
   __syncthreads();
   if (s_fail) {
     if (tid == 0) status[0] = 1;
     return;
   }
-  for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
-    const int i = (int)(idx / n), j = (int)(idx % n);
-    const double s = sc[i] * sc[j];
-    K[idx] = s * 0.5 * (GA[(int64_t)i * lda + j] + GA[(int64_t)j * lda + i]);
-    L[idx] = s * 0.5 * (GB[(int64_t)i * ldb + j] + GB[(int64_t)j * ldb + i]);
-  }
-  __syncthreads();
-  // 2. Cholesky (lower, in place in L) with dropping: a pivot below kPivTol (relative to
-  //    the unit diagonal after scaling) marks a direction numerically dependent on the
-  //    earlier ones; its column is zeroed, L[j][j] = 1, and the direction is later given an
-  //    eigenvalue above the whole spectrum so that no returned vector uses it.
-  __shared__ int s_drop;
-  if (tid == 0) s_drop = 0;
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = lane; j < n; j += 32) {
+      const double s = W.sc[i] * W.sc[j];
+      W.K[(int64_t)i * n + j] = s * 0.5 * (GA[(int64_t)i * lda + j] + GA[(int64_t)j * lda + i]);
+      W.L[(int64_t)i * n + j] = s * 0.5 * (GB[(int64_t)i * ldb + j] + GB[(int64_t)j * ldb + i]);
+    }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    const double dj = L[(int64_t)j * n + j];
+    const double dj = W.L[(int64_t)j * n + j];
     const bool drop = !(dj > kPivTol) || !isfinite(dj);
+    const double ljj = drop ? 1.0 : sqrt(dj);
+    const int len = n - j - 1;
+    for (int r = tid; r < len; r += nt) colj[r] = drop ? 0.0 : W.L[(int64_t)(j + 1 + r) * n + j] / ljj;
     __syncthreads();
     if (tid == 0) {
-      L[(int64_t)j * n + j] = drop ? 1.0 : sqrt(dj);
-      if (drop) {
-        ++s_drop;
-        tau[j] = 1.0;  // tau doubles as the drop mask until step 4
-      } else {
-        tau[j] = 0.0;
+      W.L[(int64_t)j * n + j] = ljj;
+      W.tau[j] = drop ? 1.0 : 0.0;
+      if (drop) ++s_drop;
+    }
+    for (int r = tid; r < len; r += nt) W.L[(int64_t)(j + 1 + r) * n + j] = colj[r];
+    if (!drop)
+      for (int r = warp; r < len; r += nwarps) {
+        double* Lr = W.L + (int64_t)(j + 1 + r) * n + (j + 1);
+        const double cr = colj[r];
+        for (int c = lane; c <= r; c += 32) Lr[c] -= cr * colj[c];
       }
-    }
-    __syncthreads();
-    const double ljj = L[(int64_t)j * n + j];
-    for (int i = j + 1 + tid; i < n; i += nt) L[(int64_t)i * n + j] = drop ? 0.0 : L[(int64_t)i * n + j] / ljj;
-    __syncthreads();
-    if (!drop) {
-      const int len = n - j - 1;
-      for (int idx = tid; idx < len * len; idx += nt) {
-        const int i = j + 1 + idx / len, l = j + 1 + idx % len;
-        if (l <= i) L[(int64_t)i * n + l] -= L[(int64_t)i * n + j] * L[(int64_t)l * n + j];
-      }
-    }
     __syncthreads();
   }
-  if (n - s_drop < k) {
-    if (tid == 0) status[0] = 1;
-    return;
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = i + 1 + lane; j < n; j += 32) W.L[(int64_t)i * n + j] = 0.0;
+  if (tid == 0) {
+    W.info[0] = s_drop;
+    status[0] = (n - s_drop < k) ? 1 : 0;
   }
-  // 3. K <- L^-1 K  (row i after rows < i; parallel over columns)
+}
+
+// 2. out[c-th vector] = L^-1 in[c-th vector], one CTA per vector.  pass 0: input row c of
+//    K (= column c, K symmetric), output column c of Y; pass 1: input row c of Y, output
+//    row c of K (K <- L^-1 K L^-T since K' = (L^-1 Y^T)^T and K' is symmetric).
+__global__ void __launch_bounds__(128) k_sygv_trsm(int n, int k, double* work, int pass, const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double sy[];  // n solution entries + 4 warp partials
+  double* red = sy + n;
+  SygvWork W = sygv_work(work, n, k);
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* in = (pass == 0) ? W.K + (int64_t)c * n : W.Y + (int64_t)c * n;
   for (int i = 0; i < n; ++i) {
-    const double lii = L[(int64_t)i * n + i];
-    for (int c = tid; c < n; c += nt) {
-      double s = K[(int64_t)i * n + c];
-      for (int l = 0; l < i; ++l) s -= L[(int64_t)i * n + l] * K[(int64_t)l * n + c];
-      K[(int64_t)i * n + c] = s / lii;
+    const double* Li = W.L + (int64_t)i * n;
+    double acc = 0.0;
+    for (int l = tid; l < i; l += blockDim.x) acc = fma(Li[l], sy[l], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      sy[i] = (in[i] - t) / Li[i];
     }
     __syncthreads();
   }
-  //    K <- K L^-T  (column i after columns < i; parallel over rows)
-  for (int i = 0; i < n; ++i) {
-    const double lii = L[(int64_t)i * n + i];
-    for (int r = tid; r < n; r += nt) {
-      double s = K[(int64_t)r * n + i];
-      for (int l = 0; l < i; ++l) s -= K[(int64_t)r * n + l] * L[(int64_t)i * n + l];
-      K[(int64_t)r * n + i] = s / lii;
-    }
-    __syncthreads();
-  }
-  for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
-    const int i = (int)(idx / n), j = (int)(idx % n);
-    if (i < j) {
+  if (pass == 0)
+    for (int i = tid; i < n; i += blockDim.x) W.Y[(int64_t)i * n + c] = sy[i];
+  else
+    for (int i = tid; i < n; i += blockDim.x) W.K[(int64_t)c * n + i] = sy[i];
+}
+
+// 3. Householder tridiagonalisation and FP32 multisection (one CTA of 1024 threads).
+//    Reflector j acts on rows/cols j+1..n-1; its vector (v[0] = 1 implicit) is kept in
+//    row j, K[j][j+2..n-1], and tau[j].
+__global__ void __launch_bounds__(1024) k_sygv_tridiag(int n, int k, double* work, const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double shm[];
+  __shared__ double red[40];
+  __shared__ double s_lo, s_hi;
+  SygvWork W = sygv_work(work, n, k);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  double* v = shm;        // n
+  double* p = v + n;      // n
+  double* part = p + n;   // nt
+  int* icnt = reinterpret_cast<int*>(part + nt);  // nt
+  float* df = reinterpret_cast<float*>(icnt + nt);
+  float* e2f = df + n;
+  float* flo = e2f + n;
+  float* fhi = flo + k;
+  double* K = W.K;
+  // symmetrise; dropped directions get an eigenvalue just above the kept spectrum
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = i + 1 + lane; j < n; j += 32) {
       const double a = 0.5 * (K[(int64_t)i * n + j] + K[(int64_t)j * n + i]);
       K[(int64_t)i * n + j] = a;
       K[(int64_t)j * n + i] = a;
     }
-  }
   __syncthreads();
-  if (s_drop > 0) {
-    // dropped directions get an eigenvalue just above the kept spectrum (Gershgorin
-    // bound of the kept rows), so they are never among the k smallest and do not
-    // inflate the norm that scales the inverse-iteration tolerances
-    double part = 0.0;
+  if (W.info[0] > 0) {
+    double rmax = 0.0;
     for (int i = tid; i < n; i += nt) {
-      if (tau[i] != 0.0) continue;
+      if (W.tau[i] != 0.0) continue;
       double r = 0.0;
       for (int j = 0; j < n; ++j)
-        if (tau[j] == 0.0) r += fabs(K[(int64_t)i * n + j]);
-      part = fmax(part, r);
+        if (W.tau[j] == 0.0) r += fabs(K[(int64_t)i * n + j]);
+      rmax = fmax(rmax, r);
     }
-    const double big = 2.0 * block_max(part, red) + 1.0;
-    for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
-      const int i = (int)(idx / n), j = (int)(idx % n);
-      if (tau[i] != 0.0 || tau[j] != 0.0) K[idx] = (i == j) ? big : 0.0;
-    }
+    const double big = 2.0 * block_max(rmax, red) + 1.0;
+    for (int i = warp; i < n; i += nwarps)
+      for (int j = lane; j < n; j += 32)
+        if (W.tau[i] != 0.0 || W.tau[j] != 0.0) K[(int64_t)i * n + j] = (i == j) ? big : 0.0;
     __syncthreads();
   }
-  // 4. Householder tridiagonalisation; reflector j acts on rows/cols j+1..n-1 and its
-  //    vector (v[0] = 1 implicit) is kept in K[(j+1..n-1)*n + j], tau[j].
   for (int j = 0; j + 2 < n; ++j) {
     const int len = n - j - 1;
+    const double* xr = K + (int64_t)j * n + (j + 1);  // row j = column j (symmetric)
     double* A22 = K + (int64_t)(j + 1) * n + (j + 1);
-    // norm of x = K[j+1.., j]
-    double part = 0.0;
-    for (int r = 1 + tid; r < len; r += nt) {
-      const double x = K[(int64_t)(j + 1 + r) * n + j];
-      part += x * x;
-    }
-    const double sig = block_sum(part, red);
-    const double x0 = K[(int64_t)(j + 1) * n + j];
+    double part_s = 0.0;
+    for (int r = 1 + tid; r < len; r += nt) part_s += xr[r] * xr[r];
+    const double sig = block_sum(part_s, red);
+    const double x0 = xr[0];
     double beta, t;
     if (sig == 0.0) {
       t = 0.0;
@@ -566,15 +587,16 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
       t = (beta - x0) / beta;
     }
     const double scal = (sig == 0.0) ? 0.0 : 1.0 / (x0 - beta);
-    for (int r = tid; r < len; r += nt) v[r] = (r == 0) ? 1.0 : K[(int64_t)(j + 1 + r) * n + j] * scal;
+    for (int r = tid; r < len; r += nt) v[r] = (r == 0) ? 1.0 : xr[r] * scal;
     __syncthreads();
     if (t != 0.0) {
-      // p = t A22 v
-      for (int r = tid; r < len; r += nt) {
-        double s = 0.0;
+      for (int r = warp; r < len; r += nwarps) {  // p = t A22 v, one warp per row
         const double* row = A22 + (int64_t)r * n;
-        for (int c = 0; c < len; ++c) s = fma(row[c], v[c], s);
-        p[r] = t * s;
+        double acc = 0.0;
+        for (int c = lane; c < len; c += 32) acc = fma(row[c], v[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) p[r] = t * acc;
       }
       __syncthreads();
       double pv = 0.0;
@@ -582,191 +604,289 @@ __global__ void __launch_bounds__(1024) k_sygv(int n, int k, const double* __res
       const double Kc = 0.5 * t * block_sum(pv, red);
       for (int r = tid; r < len; r += nt) p[r] -= Kc * v[r];
       __syncthreads();
-      for (int64_t idx = tid; idx < (int64_t)len * len; idx += nt) {
-        const int r = (int)(idx / len), c = (int)(idx % len);
-        A22[(int64_t)r * n + c] -= v[r] * p[c] + p[r] * v[c];
+      for (int r = warp; r < len; r += nwarps) {
+        double* row = A22 + (int64_t)r * n;
+        const double vr = v[r], pr = p[r];
+        for (int c = lane; c < len; c += 32) row[c] -= vr * p[c] + pr * v[c];
       }
     }
     __syncthreads();
     if (tid == 0) {
-      d[j] = K[(int64_t)j * n + j];
-      e[j] = beta;
-      tau[j] = t;
+      W.d[j] = K[(int64_t)j * n + j];
+      W.e[j] = beta;
+      W.tau[j] = t;
     }
-    for (int r = 1 + tid; r < len; r += nt) K[(int64_t)(j + 1 + r) * n + j] = v[r];
+    for (int r = 1 + tid; r < len; r += nt) K[(int64_t)j * n + (j + 1 + r)] = v[r];
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
-      d[n - 2] = K[(int64_t)(n - 2) * n + (n - 2)];
-      e[n - 2] = K[(int64_t)(n - 1) * n + (n - 2)];
-      tau[n - 2] = 0.0;
+      W.d[n - 2] = K[(int64_t)(n - 2) * n + (n - 2)];
+      W.e[n - 2] = K[(int64_t)(n - 1) * n + (n - 2)];
+      W.tau[n - 2] = 0.0;
     }
-    d[n - 1] = K[(int64_t)(n - 1) * n + (n - 1)];
-    e[n - 1] = 0.0;
-    // Gershgorin interval
+    W.d[n - 1] = K[(int64_t)(n - 1) * n + (n - 1)];
+    W.e[n - 1] = 0.0;
+    W.tau[n - 1] = 0.0;
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < n; ++i) {
-      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, d[i] - r);
-      hi = fmax(hi, d[i] + r);
+      const double r = (i > 0 ? fabs(W.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(W.e[i]) : 0.0);
+      lo = fmin(lo, W.d[i] - r);
+      hi = fmax(hi, W.d[i] + r);
     }
-    const double pad = 1e-14 * fmax(fabs(lo), fabs(hi)) + DBL_MIN;
-    s_lo = lo - pad;
-    s_hi = hi + pad;
+    s_lo = lo;
+    s_hi = hi;
   }
   __syncthreads();
-  const double tnorm = fmax(fabs(s_lo), fabs(s_hi));
-  // 5. bisection: lam[i] = i-th smallest (0-based)
+  for (int i = tid; i < n; i += nt) {
+    df[i] = (float)W.d[i];
+    e2f[i] = (float)(W.e[i] * W.e[i]);
+  }
   for (int i = tid; i < k; i += nt) {
-    double a = s_lo, b = s_hi;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (mid <= a || mid >= b) break;
-      if (b - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b))) break;
-      if (sturm_count(n, d, e, mid) > i) b = mid;
-      else a = mid;
-    }
-    lam[i] = 0.5 * (a + b);
+    flo[i] = (float)s_lo - 1e-6f * (float)fabs(s_lo) - 1e-30f;
+    fhi[i] = (float)s_hi + 1e-6f * (float)fabs(s_hi) + 1e-30f;
   }
   __syncthreads();
-  // 6. inverse iteration.  Eigenvalues closer than ctol = 1e-6 |T| form a cluster, owned by
-  //    the thread of its first member: its vectors are re-orthogonalised against each
-  //    other (vectors of close eigenvalues computed independently lose orthogonality by
-  //    ~eps |T| / gap) and then rotated by a Rayleigh-Ritz step inside the cluster, so
-  //    that every returned pair has value = Rayleigh quotient of its vector.
-  const double ctol = 1e-6 * tnorm;
-  const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
-  for (int i = tid; i < k; i += nt) {
-    if (i > 0 && lam[i] - lam[i - 1] <= ctol) continue;  // not a cluster head
-    int last = i;
-    while (last + 1 < k && lam[last + 1] - lam[last] <= ctol) ++last;
-    double* u0 = iw + (int64_t)4 * n * i;
-    double* u1 = u0 + n;
-    double* u2 = u1 + n;
-    double* bb = u2 + n;
-    int* pv_ = ipiv + (int64_t)n * i;
-    for (int q = i; q <= last; ++q) {
-      double* z = Z + q;  // column q, stride k
-      for (int r = 0; r < n; ++r) bb[r] = hash_unit((unsigned)q, (unsigned)r) + 1e-3;
-      for (int it = 0; it < 3; ++it) {
-        tri_solve(n, d, e, lam[q], bb, u0, u1, u2, pv_, tiny);
-        for (int pass = 0; pass < 2; ++pass)
-          for (int o = i; o < q; ++o) {
-            double dot = 0.0;
-            for (int r = 0; r < n; ++r) dot += bb[r] * Z[(int64_t)r * k + o];
-            for (int r = 0; r < n; ++r) bb[r] -= dot * Z[(int64_t)r * k + o];
-          }
-        double nrm = 0.0;
-        for (int r = 0; r < n; ++r) nrm += bb[r] * bb[r];
-        nrm = sqrt(nrm);
-        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        for (int r = 0; r < n; ++r) bb[r] *= inv;
-      }
-      for (int r = 0; r < n; ++r) z[(int64_t)r * k] = bb[r];
-    }
-    const int s = last - i + 1;
-    if (s >= 2 && s <= kClusterRR) {
-      // H = Q^T T Q for the cluster block Q = Z[:, i..last], then cyclic Jacobi on H
-      double H[kClusterRR * kClusterRR];
-      for (int a = 0; a < s; ++a)
-        for (int b = a; b < s; ++b) {
-          double acc = 0.0;
-          for (int r = 0; r < n; ++r) {
-            double tq = d[r] * Z[(int64_t)r * k + i + b];
-            if (r > 0) tq += e[r - 1] * Z[(int64_t)(r - 1) * k + i + b];
-            if (r < n - 1) tq += e[r] * Z[(int64_t)(r + 1) * k + i + b];
-            acc += Z[(int64_t)r * k + i + a] * tq;
-          }
-          H[a * s + b] = acc;
-          H[b * s + a] = acc;
-        }
-      for (int sweep = 0; sweep < 12; ++sweep) {
-        double off = 0.0;
-        for (int a = 0; a < s; ++a)
-          for (int b = a + 1; b < s; ++b) off += H[a * s + b] * H[a * s + b];
-        if (off <= 1e-32 * (tnorm * tnorm)) break;
-        for (int a = 0; a < s; ++a)
-          for (int b = a + 1; b < s; ++b) {
-            const double hab = H[a * s + b];
-            if (hab == 0.0) continue;
-            const double th = 0.5 * (H[b * s + b] - H[a * s + a]) / hab;
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-            for (int l = 0; l < s; ++l) {  // columns a, b of H
-              const double ha = H[l * s + a], hb = H[l * s + b];
-              H[l * s + a] = c * ha - sn * hb;
-              H[l * s + b] = sn * ha + c * hb;
-            }
-            for (int l = 0; l < s; ++l) {  // rows a, b
-              const double ha = H[a * s + l], hb = H[b * s + l];
-              H[a * s + l] = c * ha - sn * hb;
-              H[b * s + l] = sn * ha + c * hb;
-            }
-            for (int r = 0; r < n; ++r) {  // vectors
-              const double za = Z[(int64_t)r * k + i + a], zb = Z[(int64_t)r * k + i + b];
-              Z[(int64_t)r * k + i + a] = c * za - sn * zb;
-              Z[(int64_t)r * k + i + b] = sn * za + c * zb;
-            }
-          }
-      }
-      // sort the cluster ascending by its Rayleigh quotients
-      for (int a = 0; a < s; ++a) {
-        int best = a;
-        for (int b = a + 1; b < s; ++b)
-          if (H[b * s + b] < H[best * s + best]) best = b;
-        if (best != a) {
-          const double t = H[a * s + a];
-          H[a * s + a] = H[best * s + best];
-          H[best * s + best] = t;
-          for (int r = 0; r < n; ++r) {
-            const double za = Z[(int64_t)r * k + i + a];
-            Z[(int64_t)r * k + i + a] = Z[(int64_t)r * k + i + best];
-            Z[(int64_t)r * k + i + best] = za;
-          }
-        }
-        lam[i + a] = H[a * s + a];
-      }
-    }
-  }
-  __syncthreads();
-  // 7. back-transform z <- H_0 ... H_{n-3} z, reflector j acting on rows j+1..
-  for (int j = n - 3; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;
-    const int len = n - j - 1;
-    for (int c = tid; c < k; c += nt) {
-      double s = Z[(int64_t)(j + 1) * k + c];
-      for (int r = 1; r < len; ++r) s = fma(K[(int64_t)(j + 1 + r) * n + j], Z[(int64_t)(j + 1 + r) * k + c], s);
-      s *= t;
-      Z[(int64_t)(j + 1) * k + c] -= s;
-      for (int r = 1; r < len; ++r) Z[(int64_t)(j + 1 + r) * k + c] -= s * K[(int64_t)(j + 1 + r) * n + j];
+  const int G = max(1, min(32, nt / k));
+  for (int round = 0; round < 40; ++round) {
+    const int i = tid / G, g = tid % G;
+    if (i < k) {
+      const float a = flo[i], b = fhi[i];
+      const float x = a + (b - a) * (float)(g + 1) / (float)(G + 1);
+      icnt[tid] = (b - a > 4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) ? sturm_count_f32(n, df, e2f, x) : -1;
     }
     __syncthreads();
-  }
-  //    c = D L^-T z  (back substitution, parallel over columns)
-  for (int c = tid; c < k; c += nt) {
-    for (int i = n - 1; i >= 0; --i) {
-      double s = Z[(int64_t)i * k + c];
-      for (int l = i + 1; l < n; ++l) s -= L[(int64_t)l * n + i] * Z[(int64_t)l * k + c];
-      Z[(int64_t)i * k + c] = s / L[(int64_t)i * n + i];
+    int moved = 0;
+    if (i < k && g == 0 && icnt[tid] >= 0) {
+      const float a = flo[i], b = fhi[i];
+      float na = a, nb = b;
+      for (int q = 0; q < G; ++q) {
+        const float x = a + (b - a) * (float)(q + 1) / (float)(G + 1);
+        if (icnt[i * G + q] > i) {
+          nb = x;
+          break;
+        }
+        na = x;
+      }
+      flo[i] = na;
+      fhi[i] = nb;
+      moved = 1;
     }
-    for (int i = 0; i < n; ++i) C[(int64_t)i * ldc + c] = sc[i] * Z[(int64_t)i * k + c];
+    if (block_sum((double)moved, red) == 0.0) break;
   }
-  if (tid == 0) status[0] = 0;
+  for (int i = tid; i < k; i += nt) W.lamx[i] = 0.5 * ((double)flo[i] + (double)fhi[i]);
+  if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));  // |T| bound
+}
+
+// 4. inverse iteration, one CTA per eigenvalue (only cluster heads work; lane 0 runs the
+//    sequential recurrences on shared-memory scratch).  Eigenvalues closer than
+//    ctol = 1e-5 |T| form a cluster: its vectors are re-orthogonalised against each other
+//    (vectors of close eigenvalues computed independently lose orthogonality by
+//    ~eps |T| / gap) and rotated by a Rayleigh-Ritz step inside the cluster.
+__global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work, double* __restrict__ lam,
+                                                     const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double sw[];  // 4n
+  SygvWork W = sygv_work(work, n, k);
+  const int i = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const double tnorm = W.lamx[k];
+  const double ctol = 1e-5 * tnorm;
+  const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
+  const double* lx = W.lamx;
+  if (i > 0 && lx[i] - lx[i - 1] <= ctol) return;  // not a cluster head
+  int last = i;
+  while (last + 1 < k && lx[last + 1] - lx[last] <= ctol) ++last;
+  const double* d = W.d;
+  const double* e = W.e;
+  double* Z = W.Z;
+  double* u0 = sw;
+  double* u1 = u0 + n;
+  double* u2 = u1 + n;
+  double* bb = u2 + n;
+  for (int q = i; q <= last; ++q) {
+    for (int r = 0; r < n; ++r) bb[r] = hash_unit((unsigned)q, (unsigned)r) + 1e-3;
+    double shift = lx[q];
+    const int iters = (i == last) ? 3 : 4;
+    for (int it = 0; it < iters; ++it) {
+      tri_solve(n, d, e, shift, bb, u0, u1, u2, tiny);
+      for (int pass = 0; pass < 2; ++pass)
+        for (int o = i; o < q; ++o) {
+          double dot = 0.0;
+          for (int r = 0; r < n; ++r) dot += bb[r] * Z[(int64_t)r * k + o];
+          for (int r = 0; r < n; ++r) bb[r] -= dot * Z[(int64_t)r * k + o];
+        }
+      double nrm = 0.0;
+      for (int r = 0; r < n; ++r) nrm += bb[r] * bb[r];
+      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+      for (int r = 0; r < n; ++r) bb[r] *= inv;
+      if (it >= 1) {  // Rayleigh-quotient shift
+        double rq = 0.0;
+        for (int r = 0; r < n; ++r) {
+          double tq = d[r] * bb[r];
+          if (r > 0) tq += e[r - 1] * bb[r - 1];
+          if (r < n - 1) tq += e[r] * bb[r + 1];
+          rq += bb[r] * tq;
+        }
+        shift = rq;
+      }
+    }
+    lam[q] = shift;
+    for (int r = 0; r < n; ++r) Z[(int64_t)r * k + q] = bb[r];
+  }
+  const int s = last - i + 1;
+  if (s >= 2 && s <= kClusterRR) {
+    double H[kClusterRR * kClusterRR], R[kClusterRR * kClusterRR];
+    for (int a = 0; a < s; ++a)
+      for (int b = a; b < s; ++b) {
+        double acc = 0.0;
+        for (int r = 0; r < n; ++r) {
+          double tq = d[r] * Z[(int64_t)r * k + i + b];
+          if (r > 0) tq += e[r - 1] * Z[(int64_t)(r - 1) * k + i + b];
+          if (r < n - 1) tq += e[r] * Z[(int64_t)(r + 1) * k + i + b];
+          acc += Z[(int64_t)r * k + i + a] * tq;
+        }
+        H[a * s + b] = acc;
+        H[b * s + a] = acc;
+      }
+    for (int a = 0; a < s; ++a)
+      for (int b = 0; b < s; ++b) R[a * s + b] = (a == b) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      double off = 0.0, diag = 0.0;
+      for (int a = 0; a < s; ++a) {
+        diag += H[a * s + a] * H[a * s + a];
+        for (int b = a + 1; b < s; ++b) off += H[a * s + b] * H[a * s + b];
+      }
+      if (off <= 1e-30 * (diag + DBL_MIN)) break;
+      for (int a = 0; a < s; ++a)
+        for (int b = a + 1; b < s; ++b) {
+          const double hab = H[a * s + b];
+          if (hab == 0.0) continue;
+          const double th = 0.5 * (H[b * s + b] - H[a * s + a]) / hab;
+          const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+          const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+          for (int l = 0; l < s; ++l) {
+            const double ha = H[l * s + a], hb = H[l * s + b];
+            H[l * s + a] = c * ha - sn * hb;
+            H[l * s + b] = sn * ha + c * hb;
+          }
+          for (int l = 0; l < s; ++l) {
+            const double ha = H[a * s + l], hb = H[b * s + l];
+            H[a * s + l] = c * ha - sn * hb;
+            H[b * s + l] = sn * ha + c * hb;
+          }
+          for (int l = 0; l < s; ++l) {
+            const double ra = R[l * s + a], rb = R[l * s + b];
+            R[l * s + a] = c * ra - sn * rb;
+            R[l * s + b] = sn * ra + c * rb;
+          }
+        }
+    }
+    int perm[kClusterRR];
+    for (int a = 0; a < s; ++a) perm[a] = a;
+    for (int a = 0; a < s; ++a)
+      for (int b = a + 1; b < s; ++b)
+        if (H[perm[b] * s + perm[b]] < H[perm[a] * s + perm[a]]) {
+          const int t2 = perm[a];
+          perm[a] = perm[b];
+          perm[b] = t2;
+        }
+    double row[kClusterRR];
+    for (int r = 0; r < n; ++r) {
+      for (int a = 0; a < s; ++a) {
+        double acc = 0.0;
+        for (int b = 0; b < s; ++b) acc += Z[(int64_t)r * k + i + b] * R[b * s + perm[a]];
+        row[a] = acc;
+      }
+      for (int a = 0; a < s; ++a) Z[(int64_t)r * k + i + a] = row[a];
+    }
+    for (int a = 0; a < s; ++a) lam[i + a] = H[perm[a] * s + perm[a]];
+  }
+}
+
+// 5. back-transform: each CTA takes kBtCols columns of Z through z <- H_0 ... H_{n-3} z,
+//    then c = D L^-T z.
+constexpr int kBtCols = 4;
+__global__ void __launch_bounds__(128) k_sygv_back(int n, int k, double* work, double* __restrict__ C, int ldc,
+                                                   const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double zc[];  // kBtCols * n, column-major per column
+  __shared__ double red[4 * kBtCols];
+  __shared__ double coef[kBtCols];
+  SygvWork W = sygv_work(work, n, k);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.x * kBtCols;
+  const int nc = min(kBtCols, k - c0);
+  for (int q = 0; q < nc; ++q)
+    for (int r = tid; r < n; r += blockDim.x) zc[q * n + r] = W.Z[(int64_t)r * k + c0 + q];
+  __syncthreads();
+  for (int j = n - 3; j >= 0; --j) {
+    const double t = W.tau[j];
+    if (t == 0.0) continue;
+    const int len = n - j - 1;
+    const double* vr = W.K + (int64_t)j * n + (j + 1);
+    for (int q = 0; q < nc; ++q) {
+      double acc = 0.0;
+      for (int r = tid; r < len; r += blockDim.x) acc = fma(r == 0 ? 1.0 : vr[r], zc[q * n + j + 1 + r], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) red[q * 4 + warp] = acc;
+    }
+    __syncthreads();
+    if (tid < nc) coef[tid] = t * (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3]);
+    __syncthreads();
+    for (int q = 0; q < nc; ++q)
+      for (int r = tid; r < len; r += blockDim.x) zc[q * n + j + 1 + r] -= coef[q] * (r == 0 ? 1.0 : vr[r]);
+    __syncthreads();
+  }
+  // L^T x = z, rows from the bottom (L lower, column i of L = L[l][i], l > i)
+  for (int i = n - 1; i >= 0; --i) {
+    for (int q = 0; q < nc; ++q) {
+      double acc = 0.0;
+      for (int l = i + 1 + tid; l < n; l += blockDim.x) acc = fma(W.L[(int64_t)l * n + i], zc[q * n + l], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) red[q * 4 + warp] = acc;
+    }
+    __syncthreads();
+    if (tid < nc)
+      zc[tid * n + i] = (zc[tid * n + i] - (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3])) /
+                        W.L[(int64_t)i * n + i];
+    __syncthreads();
+  }
+  for (int q = 0; q < nc; ++q)
+    for (int r = tid; r < n; r += blockDim.x) C[(int64_t)r * ldc + c0 + q] = W.sc[r] * zc[q * n + r];
 }
 
 size_t small_sygv_work_doubles(int n, int k) {
-  return (size_t)2 * n * n + (size_t)n * k + 6 * (size_t)n + (size_t)4 * n * k + (size_t)n * k;  // ints fit
+  return (size_t)3 * n * n + (size_t)n * k + 4 * (size_t)n + k + 8;
 }
 
 int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,
                double* lam, double* C, int ldc, int* status_dev) {
-  if (n <= 0 || k <= 0 || k > n) return fail(PASE_ERR_INVALID_ARG, "small_sygv: bad size");
+  if (n <= 0 || k <= 0 || k > n || k > 1024) return fail(PASE_ERR_INVALID_ARG, "small_sygv: bad size");
   if (small_sygv_work_doubles(n, k) > h->w.eigwork_doubles)
     return fail(PASE_ERR_INVALID_ARG, "small_sygv: workspace too small");
-  k_sygv<<<1, 1024, 0, h->stream>>>(n, k, GA, lda, GB, ldb, h->w.eigwork, lam, C, ldc, status_dev);
-  h->launches++;
+  const size_t smem_tri = (size_t)(2 * n + 1024) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
+  if (smem_tri > 200 * 1024 || (size_t)4 * n * sizeof(double) > 200 * 1024)
+    return fail(PASE_ERR_INVALID_ARG, "small_sygv: problem too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_back, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  double* w = h->w.eigwork;
+  auto s = h->stream;
+  k_sygv_chol<<<1, 1024, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
+  k_sygv_trsm<<<n, 128, (size_t)(n + 8) * sizeof(double), s>>>(n, k, w, 0, status_dev);
+  k_sygv_trsm<<<n, 128, (size_t)(n + 8) * sizeof(double), s>>>(n, k, w, 1, status_dev);
+  k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
+  k_sygv_inviter<<<k, 32, (size_t)4 * n * sizeof(double), s>>>(n, k, w, lam, status_dev);
+  k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, (size_t)kBtCols * n * sizeof(double), s>>>(n, k, w, C, ldc,
+                                                                                           status_dev);
+  h->launches += 6;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
 }

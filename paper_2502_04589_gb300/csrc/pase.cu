@@ -947,7 +947,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
   if (kernel == PASE_KERNEL_JACOBI_FP32 && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_SYGV) return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
+  if (kernel < 0 || kernel > PASE_KERNEL_SYGV3) return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   // deterministic operands
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 8u, w.R));
@@ -960,6 +960,13 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   if (kernel == PASE_KERNEL_SYGV) {  // a generic symmetric-definite pair (distinct eigenvalues)
     PASE_TRY(ts_gram(h, h->N, m, m, w.R, m, w.R, m, w.Gq, m3, true));
     PASE_TRY(ts_gram(h, h->N, m, m, w.W, m, w.W, m, w.Gb, m3, true));
+  }
+  if (kernel == PASE_KERNEL_SYGV3) {  // the Rayleigh-Ritz size of the step-(c) solver
+    const int64_t nc = h->NH + m;
+    PASE_TRY(launch_hash_fill(h, nc, m3, m3, 10u, w.S));
+    PASE_TRY(launch_hash_fill(h, nc, m3, m3, 11u, w.AS));
+    PASE_TRY(ts_gram(h, nc, m3, m3, w.AS, m3, w.AS, m3, w.Gq, m3, true));
+    PASE_TRY(ts_gram(h, nc, m3, m3, w.S, m3, w.S, m3, w.Gb, m3, true));
   }
   const Level& L0 = h->lv[0];
   auto once = [&]() -> int {
@@ -979,6 +986,8 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
         return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
       case PASE_KERNEL_SYGV:
         return small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
+      case PASE_KERNEL_SYGV3:
+        return small_sygv(h, m3, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
     }
     return PASE_OK;
   };

@@ -322,3 +322,25 @@ def test_errors_are_reported_not_raised_on_device(p2d):
         assert e.value.code == -1
     finally:
         c.close()
+
+
+@pytest.fixture(scope="module")
+def p3d_128():
+    """The benchmark workload: 3D Q1 Laplace 128^3, coarse 16^3, multigrid down to 4^3."""
+    return pin.build_problem(3, 128, 16, mg_min=4)
+
+
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_full_size_laplace_3d_128_nev50(p3d_128, precision):
+    """Full-size parity at the benchmark configuration (same options as bench.py):
+    eigenvalues vs the closed form, residuals and M-orthonormality recomputed on the CPU."""
+    pb = p3d_128
+    nev, m = 50, pin.guard_columns(50)
+    rc, st, lam, U = _solve(pb, nev, 1e-8, precision, m=m, seed=0)
+    assert rc == P.PASE_OK, st
+    ref = spectrum.q1_laplace_eigenvalues(3, 128, nev)
+    np.testing.assert_allclose(lam[:nev], ref, rtol=1e-10)
+    res = opase.relative_residuals(pb.A, pb.M, U[:, :nev], lam[:nev])
+    assert np.all(res <= 1e-8), res.max()
+    MU = pb.M @ U
+    np.testing.assert_allclose(U.T @ MU, np.eye(m), atol=1e-10)
