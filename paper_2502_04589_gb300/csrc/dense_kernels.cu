@@ -254,17 +254,19 @@ int small_gemm(pase_ctx* h, int m, int n, int k, double alpha, const double* A, 
 
 // ------------------------------------------------------------------ block reductions
 __device__ double block_sum(double v, double* red) {
-  // red: >= 32 doubles of shared memory
+  // red: >= 33 doubles of shared memory; warp partials, then a shuffle tree in warp 0
+  // (a serial FP64 sum would be a long dependent chain on this part)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < nw; ++w) s += red[w];
-    red[32] = s;
+  if (wid == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[32] = s;
   }
   __syncthreads();
   return red[32];
@@ -277,10 +279,11 @@ __device__ double block_max(double v, double* red) {
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
-    red[32] = s;
+  if (wid == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+    if (lane == 0) red[32] = s;
   }
   __syncthreads();
   return red[32];
@@ -398,6 +401,17 @@ __device__ double hash_unit(unsigned a, unsigned b) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
 }
 
+// 1/x: FP32 seed refined by two FP64 Newton steps (a much shorter dependent chain than
+// FP64 division on this part; accurate to about one ulp), true division outside FP32 range.
+__device__ __forceinline__ double fast_rcp(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)(1.0f / (float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
+
 // Solve (T - lam I) x = b in place (b -> x), tridiagonal LU with partial pivoting.
 __device__ void tri_solve(int n, const double* d, const double* e, double lam, double* b,
                           double* u0, double* u1, double* u2, double tiny) {
@@ -410,11 +424,11 @@ __device__ void tri_solve(int n, const double* d, const double* e, double lam, d
     const double sub = e[i];  // element (i+1, i)
     if (fabs(u0[i]) >= fabs(sub)) {
       if (u0[i] == 0.0) u0[i] = tiny;
-      const double f = sub / u0[i];
+      const double f = sub * fast_rcp(u0[i]);
       u0[i + 1] -= f * u1[i];
       b[i + 1] -= f * b[i];
     } else {
-      const double f = u0[i] / sub;
+      const double f = u0[i] * fast_rcp(sub);
       const double r1 = u0[i + 1], r2 = (i + 1 < n - 1) ? e[i + 1] : 0.0;
       const double o1 = u1[i];
       u0[i] = sub;
@@ -428,10 +442,10 @@ __device__ void tri_solve(int n, const double* d, const double* e, double lam, d
     }
   }
   if (u0[n - 1] == 0.0) u0[n - 1] = tiny;
-  b[n - 1] /= u0[n - 1];
+  b[n - 1] *= fast_rcp(u0[n - 1]);
   if (n >= 2) {
-    b[n - 2] = (b[n - 2] - u1[n - 2] * b[n - 1]) / u0[n - 2];
-    for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - u1[i] * b[i + 1] - u2[i] * b[i + 2]) / u0[i];
+    b[n - 2] = (b[n - 2] - u1[n - 2] * b[n - 1]) * fast_rcp(u0[n - 2]);
+    for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - u1[i] * b[i + 1] - u2[i] * b[i + 2]) * fast_rcp(u0[i]);
   }
 }
 
@@ -466,18 +480,25 @@ __global__ void __launch_bounds__(1024) k_sygv_chol(int n, int k, const double* 
       W.L[(int64_t)i * n + j] = s * 0.5 * (GB[(int64_t)i * ldb + j] + GB[(int64_t)j * ldb + i]);
     }
   __syncthreads();
+  __shared__ double s_inv;
+  __shared__ int s_dropj;
   for (int j = 0; j < n; ++j) {
-    const double dj = W.L[(int64_t)j * n + j];
-    const bool drop = !(dj > kPivTol) || !isfinite(dj);
-    const double ljj = drop ? 1.0 : sqrt(dj);
-    const int len = n - j - 1;
-    for (int r = tid; r < len; r += nt) colj[r] = drop ? 0.0 : W.L[(int64_t)(j + 1 + r) * n + j] / ljj;
-    __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // pivot, its square root and reciprocal once (FP64 sqrt/div are costly)
+      const double dj = W.L[(int64_t)j * n + j];
+      const bool drop = !(dj > kPivTol) || !isfinite(dj);
+      const double ljj = drop ? 1.0 : sqrt(dj);
+      s_inv = drop ? 0.0 : 1.0 / ljj;
+      s_dropj = drop ? 1 : 0;
       W.L[(int64_t)j * n + j] = ljj;
       W.tau[j] = drop ? 1.0 : 0.0;
       if (drop) ++s_drop;
     }
+    __syncthreads();
+    const bool drop = s_dropj != 0;
+    const double inv = s_inv;
+    const int len = n - j - 1;
+    for (int r = tid; r < len; r += nt) colj[r] = W.L[(int64_t)(j + 1 + r) * n + j] * inv;
+    __syncthreads();
     for (int r = tid; r < len; r += nt) W.L[(int64_t)(j + 1 + r) * n + j] = colj[r];
     if (!drop)
       for (int r = warp; r < len; r += nwarps) {
@@ -498,15 +519,22 @@ __global__ void __launch_bounds__(1024) k_sygv_chol(int n, int k, const double* 
 // 2. out[c-th vector] = L^-1 in[c-th vector], one CTA per vector.  pass 0: input row c of
 //    K (= column c, K symmetric), output column c of Y; pass 1: input row c of Y, output
 //    row c of K (K <- L^-1 K L^-T since K' = (L^-1 Y^T)^T and K' is symmetric).
-__global__ void __launch_bounds__(128) k_sygv_trsm(int n, int k, double* work, int pass, const int* status) {
+__global__ void __launch_bounds__(128) k_sygv_trsm(int n, int k, double* work, int pass, int stage_l,
+                                                   const int* status) {
   if (status[0] != 0) return;
-  extern __shared__ double sy[];  // n solution entries + 4 warp partials
+  extern __shared__ double sy[];  // n solution entries, 4 warp partials, [packed L]
   double* red = sy + n;
+  double* Lp = red + 8;           // row i of L at Lp + i(i+1)/2 when staged
   SygvWork W = sygv_work(work, n, k);
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* in = (pass == 0) ? W.K + (int64_t)c * n : W.Y + (int64_t)c * n;
+  if (stage_l) {
+    for (int i = warp; i < n; i += (int)(blockDim.x >> 5))
+      for (int l = lane; l <= i; l += 32) Lp[i * (i + 1) / 2 + l] = W.L[(int64_t)i * n + l];
+    __syncthreads();
+  }
   for (int i = 0; i < n; ++i) {
-    const double* Li = W.L + (int64_t)i * n;
+    const double* Li = stage_l ? Lp + i * (i + 1) / 2 : W.L + (int64_t)i * n;
     double acc = 0.0;
     for (int l = tid; l < i; l += blockDim.x) acc = fma(Li[l], sy[l], acc);
 #pragma unroll
@@ -533,7 +561,7 @@ __global__ void __launch_bounds__(1024) k_sygv_tridiag(int n, int k, double* wor
   if (status[0] != 0) return;
   extern __shared__ double shm[];
   __shared__ double red[40];
-  __shared__ double s_lo, s_hi;
+  __shared__ double s_lo, s_hi, s_hh[3];
   SygvWork W = sygv_work(work, n, k);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
@@ -576,17 +604,21 @@ __global__ void __launch_bounds__(1024) k_sygv_tridiag(int n, int k, double* wor
     double part_s = 0.0;
     for (int r = 1 + tid; r < len; r += nt) part_s += xr[r] * xr[r];
     const double sig = block_sum(part_s, red);
-    const double x0 = xr[0];
-    double beta, t;
-    if (sig == 0.0) {
-      t = 0.0;
-      beta = x0;
-    } else {
-      const double nrm = sqrt(x0 * x0 + sig);
-      beta = (x0 >= 0.0) ? -nrm : nrm;
-      t = (beta - x0) / beta;
+    if (tid == 0) {  // reflector scalars once (FP64 sqrt/div are costly), broadcast below
+      const double x0 = xr[0];
+      double beta = x0, t = 0.0, scal = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(x0 * x0 + sig);
+        beta = (x0 >= 0.0) ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        scal = 1.0 / (x0 - beta);
+      }
+      s_hh[0] = beta;
+      s_hh[1] = t;
+      s_hh[2] = scal;
     }
-    const double scal = (sig == 0.0) ? 0.0 : 1.0 / (x0 - beta);
+    __syncthreads();
+    const double beta = s_hh[0], t = s_hh[1], scal = s_hh[2];
     for (int r = tid; r < len; r += nt) v[r] = (r == 0) ? 1.0 : xr[r] * scal;
     __syncthreads();
     if (t != 0.0) {
@@ -676,6 +708,233 @@ __global__ void __launch_bounds__(1024) k_sygv_tridiag(int n, int k, double* wor
   }
   for (int i = tid; i < k; i += nt) W.lamx[i] = 0.5 * ((double)flo[i] + (double)fhi[i]);
   if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));  // |T| bound
+}
+
+// Shared-memory variants of kernels 1 and 3 for n(n+1)/2 doubles that fit in shared memory:
+// the lower triangle is kept packed (row r at r(r+1)/2), so every access in the long
+// sequential loops is a shared-memory access and the rank-2 update touches half the matrix.
+__device__ __forceinline__ int tri_idx(int r, int c) { return r * (r + 1) / 2 + c; }  // c <= r
+
+__global__ void __launch_bounds__(1024) k_sygv_chol_s(int n, int k, const double* __restrict__ GA, int lda,
+                                                      const double* __restrict__ GB, int ldb, double* work,
+                                                      int* status) {
+  __shared__ int s_fail, s_drop, s_dropj;
+  __shared__ double s_inv;
+  extern __shared__ double sm_c[];
+  double* Lp = sm_c;                   // n(n+1)/2
+  double* colj = Lp + n * (n + 1) / 2; // n
+  SygvWork W = sygv_work(work, n, k);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  if (tid == 0) {
+    s_fail = 0;
+    s_drop = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const double g = GB[(int64_t)i * ldb + i];
+    if (!(g >= 0.0) || !isfinite(g)) s_fail = 1;
+    W.sc[i] = (g > 0.0) ? rsqrt(g) : 0.0;
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) status[0] = 1;
+    return;
+  }
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = lane; j < n; j += 32) {
+      const double s = W.sc[i] * W.sc[j];
+      W.K[(int64_t)i * n + j] = s * 0.5 * (GA[(int64_t)i * lda + j] + GA[(int64_t)j * lda + i]);
+      if (j <= i) Lp[tri_idx(i, j)] = s * 0.5 * (GB[(int64_t)i * ldb + j] + GB[(int64_t)j * ldb + i]);
+    }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double dj = Lp[tri_idx(j, j)];
+      const bool drop = !(dj > kPivTol) || !isfinite(dj);
+      const double ljj = drop ? 1.0 : sqrt(dj);
+      s_inv = drop ? 0.0 : 1.0 / ljj;
+      s_dropj = drop ? 1 : 0;
+      Lp[tri_idx(j, j)] = ljj;
+      W.tau[j] = drop ? 1.0 : 0.0;
+      if (drop) ++s_drop;
+    }
+    __syncthreads();
+    const bool drop = s_dropj != 0;
+    const double inv = s_inv;
+    const int len = n - j - 1;
+    for (int r = tid; r < len; r += nt) {
+      const double x = Lp[tri_idx(j + 1 + r, j)] * inv;
+      Lp[tri_idx(j + 1 + r, j)] = x;
+      colj[r] = x;
+    }
+    __syncthreads();
+    if (!drop)
+      for (int r = warp; r < len; r += nwarps) {
+        double* Lr = Lp + tri_idx(j + 1 + r, j + 1);
+        const double cr = colj[r];
+        for (int c = lane; c <= r; c += 32) Lr[c] -= cr * colj[c];
+      }
+    __syncthreads();
+  }
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = lane; j < n; j += 32) W.L[(int64_t)i * n + j] = (j <= i) ? Lp[tri_idx(i, j)] : 0.0;
+  if (tid == 0) {
+    W.info[0] = s_drop;
+    status[0] = (n - s_drop < k) ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sygv_tridiag_s(int n, int k, double* work, const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double sm_t[];
+  __shared__ double red[40];
+  __shared__ double s_lo, s_hi, s_hh[3];
+  SygvWork W = sygv_work(work, n, k);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  double* Ap = sm_t;                     // n(n+1)/2, packed lower triangle
+  double* v = Ap + n * (n + 1) / 2;      // n
+  double* p = v + n;                     // n
+  int* icnt = reinterpret_cast<int*>(p + n);  // nt
+  float* df = reinterpret_cast<float*>(icnt + nt);
+  float* e2f = df + n;
+  float* flo = e2f + n;
+  float* fhi = flo + k;
+  const double* K = W.K;
+  for (int i = warp; i < n; i += nwarps)
+    for (int j = lane; j <= i; j += 32) Ap[tri_idx(i, j)] = 0.5 * (K[(int64_t)i * n + j] + K[(int64_t)j * n + i]);
+  __syncthreads();
+  if (W.info[0] > 0) {
+    double rmax = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      if (W.tau[i] != 0.0) continue;
+      double r = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (W.tau[j] == 0.0) r += fabs(j <= i ? Ap[tri_idx(i, j)] : Ap[tri_idx(j, i)]);
+      rmax = fmax(rmax, r);
+    }
+    const double big = 2.0 * block_max(rmax, red) + 1.0;
+    for (int i = warp; i < n; i += nwarps)
+      for (int j = lane; j <= i; j += 32)
+        if (W.tau[i] != 0.0 || W.tau[j] != 0.0) Ap[tri_idx(i, j)] = (i == j) ? big : 0.0;
+    __syncthreads();
+  }
+  for (int j = 0; j + 2 < n; ++j) {
+    const int len = n - j - 1, j1 = j + 1;
+    double part_s = 0.0;
+    for (int r = 1 + tid; r < len; r += nt) {
+      const double x = Ap[tri_idx(j1 + r, j)];
+      part_s += x * x;
+    }
+    const double sig = block_sum(part_s, red);
+    if (tid == 0) {
+      const double x0 = Ap[tri_idx(j1, j)];
+      double beta = x0, t = 0.0, scal = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(x0 * x0 + sig);
+        beta = (x0 >= 0.0) ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        scal = 1.0 / (x0 - beta);
+      }
+      s_hh[0] = beta;
+      s_hh[1] = t;
+      s_hh[2] = scal;
+    }
+    __syncthreads();
+    const double beta = s_hh[0], t = s_hh[1], scal = s_hh[2];
+    for (int r = tid; r < len; r += nt) v[r] = (r == 0) ? 1.0 : Ap[tri_idx(j1 + r, j)] * scal;
+    __syncthreads();
+    if (t != 0.0) {
+      for (int r = warp; r < len; r += nwarps) {  // p = t A22 v, A22 symmetric from the packed triangle
+        const int R = j1 + r;
+        double acc = 0.0;
+        for (int c = lane; c < len; c += 32) {
+          const int C = j1 + c;
+          acc = fma(c <= r ? Ap[tri_idx(R, C)] : Ap[tri_idx(C, R)], v[c], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) p[r] = t * acc;
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int r = tid; r < len; r += nt) pv += p[r] * v[r];
+      const double Kc = 0.5 * t * block_sum(pv, red);
+      for (int r = tid; r < len; r += nt) p[r] -= Kc * v[r];
+      __syncthreads();
+      for (int r = warp; r < len; r += nwarps) {  // lower triangle only
+        double* row = Ap + tri_idx(j1 + r, j1);
+        const double vr = v[r], pr = p[r];
+        for (int c = lane; c <= r; c += 32) row[c] -= vr * p[c] + pr * v[c];
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      W.d[j] = Ap[tri_idx(j, j)];
+      W.e[j] = beta;
+      W.tau[j] = t;
+    }
+    for (int r = 1 + tid; r < len; r += nt) W.K[(int64_t)j * n + (j1 + r)] = v[r];  // reflector store
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      W.d[n - 2] = Ap[tri_idx(n - 2, n - 2)];
+      W.e[n - 2] = Ap[tri_idx(n - 1, n - 2)];
+      W.tau[n - 2] = 0.0;
+    }
+    W.d[n - 1] = Ap[tri_idx(n - 1, n - 1)];
+    W.e[n - 1] = 0.0;
+    W.tau[n - 1] = 0.0;
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(W.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(W.e[i]) : 0.0);
+      lo = fmin(lo, W.d[i] - r);
+      hi = fmax(hi, W.d[i] + r);
+    }
+    s_lo = lo;
+    s_hi = hi;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    df[i] = (float)W.d[i];
+    e2f[i] = (float)(W.e[i] * W.e[i]);
+  }
+  for (int i = tid; i < k; i += nt) {
+    flo[i] = (float)s_lo - 1e-6f * (float)fabs(s_lo) - 1e-30f;
+    fhi[i] = (float)s_hi + 1e-6f * (float)fabs(s_hi) + 1e-30f;
+  }
+  __syncthreads();
+  const int G = max(1, min(32, nt / k));
+  for (int round = 0; round < 40; ++round) {
+    const int i = tid / G, g = tid % G;
+    if (i < k) {
+      const float a = flo[i], b = fhi[i];
+      const float x = a + (b - a) * (float)(g + 1) / (float)(G + 1);
+      icnt[tid] = (b - a > 4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) ? sturm_count_f32(n, df, e2f, x) : -1;
+    }
+    __syncthreads();
+    int moved = 0;
+    if (i < k && g == 0 && icnt[tid] >= 0) {
+      const float a = flo[i], b = fhi[i];
+      float na = a, nb = b;
+      for (int q = 0; q < G; ++q) {
+        const float x = a + (b - a) * (float)(q + 1) / (float)(G + 1);
+        if (icnt[i * G + q] > i) {
+          nb = x;
+          break;
+        }
+        na = x;
+      }
+      flo[i] = na;
+      fhi[i] = nb;
+      moved = 1;
+    }
+    if (block_sum((double)moved, red) == 0.0) break;
+  }
+  for (int i = tid; i < k; i += nt) W.lamx[i] = 0.5 * ((double)flo[i] + (double)fhi[i]);
+  if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));
 }
 
 // 4. inverse iteration, one CTA per eigenvalue (only cluster heads work; lane 0 runs the
@@ -808,23 +1067,32 @@ __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work,
 //    then c = D L^-T z.
 constexpr int kBtCols = 4;
 __global__ void __launch_bounds__(128) k_sygv_back(int n, int k, double* work, double* __restrict__ C, int ldc,
-                                                   const int* status) {
+                                                   int stage, const int* status) {
   if (status[0] != 0) return;
-  extern __shared__ double zc[];  // kBtCols * n, column-major per column
+  extern __shared__ double zc[];  // kBtCols * n, then [packed reflectors | packed L]
   __shared__ double red[4 * kBtCols];
   __shared__ double coef[kBtCols];
   SygvWork W = sygv_work(work, n, k);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+  double* pk = zc + kBtCols * n;
   const int c0 = blockIdx.x * kBtCols;
   const int nc = min(kBtCols, k - c0);
   for (int q = 0; q < nc; ++q)
     for (int r = tid; r < n; r += blockDim.x) zc[q * n + r] = W.Z[(int64_t)r * k + c0 + q];
+  // reflector j (rows j+1..n-1): v[0] = 1, v[r] = K[j][j+1+r] for r >= 1, packed at
+  // pk + off(j), off(j) = j(n-2) - j(j-1)/2, n-j-2 entries
+  if (stage) {
+    for (int j = warp; j + 2 < n; j += nw) {
+      const int off = j * (n - 2) - j * (j - 1) / 2;
+      for (int r = lane; r < n - j - 2; r += 32) pk[off + r] = W.K[(int64_t)j * n + (j + 2 + r)];
+    }
+  }
   __syncthreads();
   for (int j = n - 3; j >= 0; --j) {
     const double t = W.tau[j];
     if (t == 0.0) continue;
     const int len = n - j - 1;
-    const double* vr = W.K + (int64_t)j * n + (j + 1);
+    const double* vr = stage ? pk + (j * (n - 2) - j * (j - 1) / 2) - 1 : W.K + (int64_t)j * n + (j + 1);
     for (int q = 0; q < nc; ++q) {
       double acc = 0.0;
       for (int r = tid; r < len; r += blockDim.x) acc = fma(r == 0 ? 1.0 : vr[r], zc[q * n + j + 1 + r], acc);
@@ -839,19 +1107,27 @@ __global__ void __launch_bounds__(128) k_sygv_back(int n, int k, double* work, d
       for (int r = tid; r < len; r += blockDim.x) zc[q * n + j + 1 + r] -= coef[q] * (r == 0 ? 1.0 : vr[r]);
     __syncthreads();
   }
-  // L^T x = z, rows from the bottom (L lower, column i of L = L[l][i], l > i)
+  // L^T x = z, rows from the bottom (column i of L = L[l][i], l > i); L packed by rows,
+  // row l at off(l) = l(l+1)/2, when staged
+  if (stage) {
+    for (int l = warp; l < n; l += nw)
+      for (int c = lane; c <= l; c += 32) pk[l * (l + 1) / 2 + c] = W.L[(int64_t)l * n + c];
+    __syncthreads();
+  }
   for (int i = n - 1; i >= 0; --i) {
     for (int q = 0; q < nc; ++q) {
       double acc = 0.0;
-      for (int l = i + 1 + tid; l < n; l += blockDim.x) acc = fma(W.L[(int64_t)l * n + i], zc[q * n + l], acc);
+      for (int l = i + 1 + tid; l < n; l += blockDim.x)
+        acc = fma(stage ? pk[l * (l + 1) / 2 + i] : W.L[(int64_t)l * n + i], zc[q * n + l], acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) red[q * 4 + warp] = acc;
     }
     __syncthreads();
-    if (tid < nc)
-      zc[tid * n + i] = (zc[tid * n + i] - (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3])) /
-                        W.L[(int64_t)i * n + i];
+    if (tid < nc) {
+      const double lii = stage ? pk[i * (i + 1) / 2 + i] : W.L[(int64_t)i * n + i];
+      zc[tid * n + i] = (zc[tid * n + i] - (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3])) / lii;
+    }
     __syncthreads();
   }
   for (int q = 0; q < nc; ++q)
@@ -875,17 +1151,35 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     PASE_CUDA(cudaFuncSetAttribute(k_sygv_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     PASE_CUDA(cudaFuncSetAttribute(k_sygv_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     PASE_CUDA(cudaFuncSetAttribute(k_sygv_back, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_chol_s, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PASE_CUDA(cudaFuncSetAttribute(k_sygv_tridiag_s, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   double* w = h->w.eigwork;
   auto s = h->stream;
-  k_sygv_chol<<<1, 1024, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
-  k_sygv_trsm<<<n, 128, (size_t)(n + 8) * sizeof(double), s>>>(n, k, w, 0, status_dev);
-  k_sygv_trsm<<<n, 128, (size_t)(n + 8) * sizeof(double), s>>>(n, k, w, 1, status_dev);
-  k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
+  const size_t tri = (size_t)n * (n + 1) / 2;
+  const size_t smem_trsm_st = (size_t)(n + 8 + tri) * sizeof(double);
+  const int stage_l = smem_trsm_st <= 200 * 1024 ? 1 : 0;
+  const size_t smem_trsm = stage_l ? smem_trsm_st : (size_t)(n + 8) * sizeof(double);
+  const size_t smem_back_st = (size_t)(kBtCols * n + tri) * sizeof(double);
+  const int stage_b = smem_back_st <= 200 * 1024 ? 1 : 0;
+  const size_t smem_back = stage_b ? smem_back_st : (size_t)kBtCols * n * sizeof(double);
+  const size_t smem_chol_s = (tri + n) * sizeof(double);
+  const size_t smem_tri_s = (tri + 2 * n) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
+  const bool packed = smem_tri_s <= 200 * 1024 && smem_chol_s <= 200 * 1024;
+  if (packed)
+    k_sygv_chol_s<<<1, 1024, smem_chol_s, s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
+  else
+    k_sygv_chol<<<1, 1024, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
+  k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, status_dev);
+  k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, status_dev);
+  if (packed)
+    k_sygv_tridiag_s<<<1, 1024, smem_tri_s, s>>>(n, k, w, status_dev);
+  else
+    k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
   k_sygv_inviter<<<k, 32, (size_t)4 * n * sizeof(double), s>>>(n, k, w, lam, status_dev);
-  k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, (size_t)kBtCols * n * sizeof(double), s>>>(n, k, w, C, ldc,
-                                                                                           status_dev);
+  k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
