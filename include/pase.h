@@ -74,6 +74,10 @@ typedef struct {
   int aug_adaptive;    /* 1 (default): inner target max(aug_tol, 1e-3 x current outer residual);
                           0: always aug_tol                                                     */
   int verbose;         /* 0 silent, 1 per-iteration line on stderr, 2 also inner iterations    */
+  int use_graphs;      /* 1 (default): inside pase_solve the step-(a) linear solve is captured
+                          once into a CUDA graph and replayed (needs a non-NULL stream)        */
+  int autotune;        /* 1 (default): pase_reserve times the sparse kernel at a few block
+                          sizes for every multigrid matrix and keeps the fastest            */
 } pase_options;
 
 /* Per-solve statistics (all times in milliseconds, device-event timed). */
@@ -130,6 +134,20 @@ int pase_reserve(pase_handle h, int m);
  * Returns PASE_ERR_NOT_CONVERGED (outputs written) if max_iter is reached. */
 int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, double* lambda,
                double* U, pase_stats* st);
+
+/* Many independent problems at once.  The method treats one pencil per call (Alg. 3);
+ * solving unrelated pencils side by side has no counterpart in the paper.  count handles,
+ * each set up and best created on its own CUDA stream, are solved concurrently by a pool
+ * of host threads so that their kernels overlap on the GPU (handles that share a stream
+ * run one after another, largest groups first).  Problem i runs exactly as pase_solve with
+ * nev[i], tol[i], m[i] (m NULL or m[i] = 0: the default block width), U0[i] (U0 or U0[i]
+ * NULL: coarse start), lambda[i] and U[i]; host or device pointers as in pase_solve.
+ * st (may be NULL) receives count stats.  Returns PASE_OK if all converged,
+ * PASE_ERR_NOT_CONVERGED if some reached max_iter, else the first other error (the
+ * message names the problem); every problem is attempted. */
+int pase_solve_batched(pase_handle* hs, int count, const int* nev, const double* tol,
+                       const int* m, const double* const* U0, double* const* lambda,
+                       double* const* U, pase_stats* st);
 
 /* ---- the steps of one iteration, for callers that drive the loop themselves ---------- */
 

@@ -132,11 +132,7 @@ int ts_gram(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int ldx, co
   gx = (n + rpb - 1) / rpb;
   if (gx < 1) gx = 1;
   const size_t smem = (size_t)kGramRC * (((k1 + 3) & ~3) + ((k2 + 3) & ~3)) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    PASE_CUDA(cudaFuncSetAttribute(k_ts_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  PASE_TRY(ensure_max_smem((const void*)k_ts_gram, 200 * 1024));
   dim3 grid((unsigned)gx, (unsigned)gy);
   k_ts_gram<<<grid, 256, smem, h->stream>>>(n, k1, k2, X, ldx, Y, ldy, sym ? 1 : 0, ntiles, tiles_j,
                                             rpb, h->w.partial);
@@ -199,11 +195,7 @@ static int ts_gemm_t(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const
   const int rpb = 256 / tpr;
   const int64_t grid = (n + rpb - 1) / rpb;
   const size_t smem = (size_t)32 * tpr * 2 * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    PASE_CUDA(cudaFuncSetAttribute(k_ts_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  PASE_TRY(ensure_max_smem((const void*)k_ts_gemm<T>, 200 * 1024));
   k_ts_gemm<T><<<(unsigned)grid, 256, smem, h->stream>>>(n, k1, k2, (T)alpha, X, ldx, C, ldc, (T)beta,
                                                          Y, ldy, tpr, rpb);
   h->launches++;
@@ -1146,16 +1138,9 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   const size_t smem_tri = (size_t)(2 * n + 1024) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   if (smem_tri > 200 * 1024 || (size_t)4 * n * sizeof(double) > 200 * 1024)
     return fail(PASE_ERR_INVALID_ARG, "small_sygv: problem too large");
-  static bool attr_set = false;
-  if (!attr_set) {
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_back, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_chol_s, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PASE_CUDA(cudaFuncSetAttribute(k_sygv_tridiag_s, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  for (const void* f : {(const void*)k_sygv_tridiag, (const void*)k_sygv_inviter, (const void*)k_sygv_back,
+                        (const void*)k_sygv_trsm, (const void*)k_sygv_chol_s, (const void*)k_sygv_tridiag_s})
+    PASE_TRY(ensure_max_smem(f, 200 * 1024));
   double* w = h->w.eigwork;
   auto s = h->stream;
   const size_t tri = (size_t)n * (n + 1) / 2;

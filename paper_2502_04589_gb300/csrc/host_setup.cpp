@@ -7,6 +7,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "pase_internal.h"
 
@@ -20,6 +23,20 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 const char* last_error_cstr() { return g_last_error.c_str(); }
+
+// The dynamic shared-memory limit is a per-device property of a kernel: raise it once
+// per (device, kernel), safely from several host threads.
+int ensure_max_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  PASE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, func})) return PASE_OK;
+  PASE_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({dev, func});
+  return PASE_OK;
+}
 
 int csr_from_abi(const pase_csr* in, HostCSR& out, const char* name) {
   if (!in) return fail(PASE_ERR_INVALID_ARG, std::string(name) + ": null matrix");

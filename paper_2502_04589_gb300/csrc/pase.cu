@@ -17,7 +17,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 
 #include "pase_internal.h"
 
@@ -133,6 +135,65 @@ struct Stage {
   }
 };
 
+// ------------------------------------------------------------------ autotuner
+// For every multigrid matrix, time the damped-Jacobi sweep (the precision the linear solve
+// runs in) at 128, 256 and 512 threads per block and keep the fastest.  Deterministic
+// operands; a few launches each, once per handle and block width.
+static int autotune(pase_ctx* h) {
+  Work& w = h->w;
+  const int m = w.m;
+  const bool mixed = h->opt.precision == PASE_PREC_MIXED;
+  cudaEvent_t e0, e1;
+  PASE_CUDA(cudaEventCreate(&e0));
+  PASE_CUDA(cudaEventCreate(&e1));
+  const int cand[3] = {128, 256, 512};
+  for (int l = 0; l + 1 < h->L; ++l) {
+    Level& L = h->lv[l];
+    const int64_t nl = L.A.nrows;
+    double *x = (l == 0) ? w.W : w.lx[l], *b = (l == 0) ? w.R : w.lb[l], *y = (l == 0) ? w.T1 : w.lt1[l];
+    PASE_TRY(launch_hash_fill(h, nl, m, m, 3u, x));
+    PASE_TRY(launch_hash_fill(h, nl, m, m, 4u, b));
+    float *xf = nullptr, *bf = nullptr, *yf = nullptr;
+    if (mixed) {
+      xf = w.fx[l];
+      bf = w.fb[l];
+      yf = w.ft1[l];
+      PASE_TRY(launch_f64_to_f32(h, nl * m, x, xf));
+      PASE_TRY(launch_f64_to_f32(h, nl * m, b, bf));
+    }
+    float best = 1e30f;
+    int best_bs = 256;
+    for (int c : cand) {
+      L.A.block = c;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1) PASE_CUDA(cudaEventRecord(e0, h->stream));
+        for (int it = 0; it < 3; ++it) {
+          if (mixed)
+            PASE_TRY(launch_csr<float>(h, CSR_JACOBI, m, L.A, L.A.val32, nullptr, xf, nullptr, bf, L.dinv32, nullptr,
+                                       h->opt.omega, yf, nullptr, nullptr, nullptr));
+          else
+            PASE_TRY(launch_csr<double>(h, CSR_JACOBI, m, L.A, L.A.val, nullptr, x, nullptr, b, L.dinv, nullptr,
+                                        h->opt.omega, y, nullptr, nullptr, nullptr));
+        }
+      }
+      PASE_CUDA(cudaEventRecord(e1, h->stream));
+      PASE_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      PASE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_bs = c;
+      }
+    }
+    L.A.block = best_bs;
+    if (h->opt.verbose) fprintf(stderr, "[pase] autotune level %d: %d threads/block (%.3f ms for 3 sweeps)\n", l, best_bs, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned_m = m;
+  return PASE_OK;
+}
+
 // ------------------------------------------------------------------ workspace
 static int reserve(pase_ctx* h, int m) {
   if (!h->ready) return fail(PASE_ERR_STATE, "pase_setup has not completed");
@@ -211,6 +272,7 @@ static int reserve(pase_ctx* h, int m) {
   PASE_TRY(dev_alloc_t(h, &w.status, 8));
   PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
   PASE_CUDA(cudaMallocHost(&w.h_status, sizeof(int) * 8));
+  if (h->opt.autotune) PASE_TRY(autotune(h));
   return PASE_OK;
 }
 
@@ -368,6 +430,55 @@ static int step_linear_solve(pase_ctx* h, const double* U, double* W) {
     for (int c = 0; c < s; ++c) PASE_TRY(vcycle<double>(h, B, 0, m, c == 0));
     PASE_TRY(launch_axpy(h, nm, 1.0, w.E, U, W));
   }
+  return PASE_OK;
+}
+
+// Step (a) through a CUDA graph.  The graph bakes in the addresses of U and W, so it is
+// captured only once the same (U, W) pair has been seen on two calls in a row (the first
+// of them runs eagerly and also sets up kernel attributes); later calls with that pair
+// replay it, calls with other buffers run eagerly.
+static int step_linear_solve_graphed(pase_ctx* h, const double* U, double* W) {
+  if (!h->opt.use_graphs || !h->graphs_ok || h->stream == nullptr) return step_linear_solve(h, U, W);
+  if (h->ls_graph && h->ls_graph_U == U && h->ls_graph_W == W) {
+    PASE_CUDA(cudaGraphLaunch(h->ls_graph, h->stream));
+    h->launches += h->ls_graph_kernels;
+    return PASE_OK;
+  }
+  const bool stable = (h->ls_last_U == U && h->ls_last_W == W);
+  h->ls_last_U = U;
+  h->ls_last_W = W;
+  if (!stable) return step_linear_solve(h, U, W);
+  if (h->ls_graph) {
+    cudaGraphExecDestroy(h->ls_graph);
+    h->ls_graph = nullptr;
+  }
+  const int64_t l0 = h->launches;
+  PASE_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = step_linear_solve(h, U, W);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  const int64_t captured = h->launches - l0;
+  h->launches = l0;
+  if (rc != PASE_OK || e != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    h->graphs_ok = false;  // fall back to eager launches for this handle
+    return step_linear_solve(h, U, W);
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    h->graphs_ok = false;
+    return step_linear_solve(h, U, W);
+  }
+  h->ls_graph = ex;
+  h->ls_graph_U = U;
+  h->ls_graph_W = W;
+  h->ls_graph_kernels = captured;
+  PASE_CUDA(cudaGraphLaunch(ex, h->stream));
+  h->launches += captured;
   return PASE_OK;
 }
 
@@ -614,11 +725,11 @@ static int coarse_start(pase_ctx* h, double* U, double* lam, int* iters) {
 // One outer iteration after the residual has been formed in w.R (or with W = U when
 // do_solve is false): (a) (b) (c) (d); U and lam are overwritten.
 static int iterate_body(pase_ctx* h, double* U, double* lam, bool do_solve, pase_stats* st,
-                        cudaEvent_t* ev) {
+                        cudaEvent_t* ev, bool graphed = false) {
   Work& w = h->w;
   const size_t nm = (size_t)h->N * w.m;
   if (ev) PASE_CUDA(cudaEventRecord(ev[0], h->stream));
-  if (do_solve) PASE_TRY(step_linear_solve(h, U, w.W));
+  if (do_solve) PASE_TRY(graphed ? step_linear_solve_graphed(h, U, w.W) : step_linear_solve(h, U, w.W));
   else PASE_CUDA(cudaMemcpyAsync(w.W, U, sizeof(double) * nm, cudaMemcpyDeviceToDevice, h->stream));
   if (ev) PASE_CUDA(cudaEventRecord(ev[1], h->stream));
   PASE_TRY(step_project(h, w.W, w.aH, w.bH, w.GA, w.GM));
@@ -654,6 +765,8 @@ void pase_default_options(pase_options* o) {
   o->aug_tol = 1e-12;
   o->aug_adaptive = 1;
   o->verbose = 0;
+  o->use_graphs = 1;
+  o->autotune = 1;
 }
 
 const char* pase_status_string(int code) {
@@ -704,6 +817,7 @@ int pase_destroy(pase_handle h) {
   if (!h) return PASE_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->ls_graph) cudaGraphExecDestroy(h->ls_graph);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_small) cudaFreeHost(h->w.h_small);
   if (h->w.h_status) cudaFreeHost(h->w.h_status);
@@ -920,7 +1034,7 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
   } else if (h->opt.aug_adaptive) {
     h->aug_tol_now = std::max(h->opt.aug_tol, 1e-6);
   }
-  const int rc = iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr);
+  const int rc = iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr, true);
   h->aug_tol_now = 0;
   h->aug_nconv = 0;
   PASE_TRY(rc);
@@ -1091,7 +1205,7 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
     } else {
       h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol;
     }
-    PASE_TRY(iterate_body(h, w.U, w.lam, do_solve, &st, ev));
+    PASE_TRY(iterate_body(h, w.U, w.lam, do_solve, &st, ev, true));
     PASE_CUDA(cudaEventSynchronize(ev[4]));
     for (int p = 0; p < 4; ++p) {
       float ms = 0.f;
@@ -1110,6 +1224,69 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_tol_now = 0;
   h->aug_nconv = 0;
   if (stp) *stp = st;
+  return rc;
+}
+
+int pase_solve_batched(pase_handle* hs, int count, const int* nev, const double* tol, const int* m,
+                       const double* const* U0, double* const* lambda, double* const* U, pase_stats* st) {
+  if (count < 0 || (count > 0 && (!hs || !nev || !tol || !lambda || !U)))
+    return fail(PASE_ERR_INVALID_ARG, "pase_solve_batched: bad arguments");
+  if (count == 0) return PASE_OK;
+  std::vector<int> rcs(count, PASE_OK);
+  std::vector<std::string> msgs(count);
+  // Problems whose handles share a CUDA stream run one after another on one thread (a
+  // stream cannot be captured and synchronised at once); distinct streams run concurrently.
+  // Groups start largest first (work ~ rows x block width) to shorten the tail.
+  std::vector<std::vector<int>> groups;
+  {
+    std::vector<std::pair<cudaStream_t, int>> key;  // stream -> group index
+    for (int i = 0; i < count; ++i) {
+      const cudaStream_t s = hs[i] ? hs[i]->stream : nullptr;
+      int g = -1;
+      for (auto& kv : key)
+        if (kv.first == s) g = kv.second;
+      if (g < 0) {
+        g = (int)groups.size();
+        key.push_back({s, g});
+        groups.emplace_back();
+      }
+      groups[g].push_back(i);
+    }
+    auto work = [&](const std::vector<int>& gr) {
+      double w = 0.0;
+      for (int i : gr) w += hs[i] ? (double)hs[i]->N * (m ? m[i] : nev[i]) : 0.0;
+      return w;
+    };
+    std::stable_sort(groups.begin(), groups.end(),
+                     [&](const std::vector<int>& a, const std::vector<int>& b) { return work(a) > work(b); });
+  }
+  std::atomic<int> next(0);
+  const int ngroups = (int)groups.size();
+  const int nthreads = std::max(1, std::min(ngroups, 32));
+  auto worker = [&]() {
+    for (;;) {
+      const int g = next.fetch_add(1);
+      if (g >= ngroups) break;
+      for (int i : groups[g]) {
+        if (hs[i]) cudaSetDevice(hs[i]->device);
+        pase_stats tmp;
+        rcs[i] = pase_solve(hs[i], nev[i], tol[i], m ? m[i] : 0, U0 ? U0[i] : nullptr, lambda[i], U[i],
+                            st ? &st[i] : &tmp);
+        if (rcs[i] != PASE_OK) msgs[i] = pase_last_error();
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  int rc = PASE_OK;
+  for (int i = 0; i < count; ++i)
+    if (rcs[i] != PASE_OK && rcs[i] != PASE_ERR_NOT_CONVERGED) {
+      return fail(rcs[i], "problem " + std::to_string(i) + ": " + msgs[i]);
+    } else if (rcs[i] == PASE_ERR_NOT_CONVERGED) {
+      rc = PASE_ERR_NOT_CONVERGED;
+    }
+  if (rc != PASE_OK) pase::set_error("some problems reached max_iter");
   return rc;
 }
 

@@ -39,6 +39,7 @@ struct HostCSR {
   int64_t nnz() const { return (int64_t)col.size(); }
 };
 
+int ensure_max_smem(const void* func, int bytes);
 int csr_from_abi(const pase_csr* in, HostCSR& out, const char* name);
 HostCSR csr_transpose(const HostCSR& a);
 HostCSR csr_multiply(const HostCSR& a, const HostCSR& b);  // a * b
@@ -54,6 +55,7 @@ struct DevCSR {
   int32_t* col = nullptr;
   double* val = nullptr;   // FP64 values
   float* val32 = nullptr;  // FP32 copy (mixed precision), may be null
+  int block = 0;           // threads per block of the CSR kernel (0 = 256; set by the autotuner)
 };
 
 struct Level {
@@ -121,6 +123,15 @@ struct pase_ctx {
   pase::Work w;
   int64_t launches = 0;
   int aug_nconv = 0;         // columns the step-(c) solver must converge (0 = all)
+  // CUDA graph of the step-(a) linear solve (captured once per handle inside pase_solve)
+  cudaGraphExec_t ls_graph = nullptr;
+  const double* ls_graph_U = nullptr;
+  double* ls_graph_W = nullptr;
+  int64_t ls_graph_kernels = 0;
+  const double* ls_last_U = nullptr;  // buffers of the previous step-(a) call
+  const double* ls_last_W = nullptr;
+  bool graphs_ok = true;
+  int tuned_m = 0;
   double aug_tol_now = 0;    // current inner tolerance
   std::vector<void*> allocations;
 };

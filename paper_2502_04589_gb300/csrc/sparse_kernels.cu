@@ -45,7 +45,7 @@ struct Vec16<float> {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_csr(int64_t n, int m, int64_t ldx, int64_t ldy, int tpr, int rpb,
+__global__ void __launch_bounds__(512) k_csr(int64_t n, int m, int64_t ldx, int64_t ldy, int tpr, int rpb,
                                              const int64_t* __restrict__ rowptr,
                                              const int32_t* __restrict__ col,
                                              const T* __restrict__ va, const T* __restrict__ vm,
@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(256) k_csr(int64_t n, int m, int64_t ldx, int6
     }
   }
   if (MODE == CSR_EIGRES) {
-    // block reduction of the column sums: red[2][rpb][m] with rpb*m <= 256*VW
-    __shared__ double red[2 * 256 * VW];
+    // block reduction of the column sums: red[2][rpb][m] with rpb*m <= 512*VW
+    __shared__ double red[2 * 512 * VW];
     if (active) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
@@ -165,9 +165,12 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   if (ldx <= 0) ldx = m;
   if (ldy <= 0) ldy = m;
   constexpr int VW = 16 / sizeof(T);
-  if (m % 8 != 0 || m <= 0 || m / VW > 256) return fail(PASE_ERR_INVALID_ARG, "launch_csr: bad m");
+  if (m % 8 != 0 || m <= 0 || m / VW > 512) return fail(PASE_ERR_INVALID_ARG, "launch_csr: bad m");
   const int tpr = m / VW;
-  const int rpb = 256 / tpr;
+  int bs = A.block > 0 ? A.block : 256;
+  if (bs < tpr) bs = ((tpr + 31) / 32) * 32;
+  if (bs > 512) bs = 512;
+  const int rpb = bs / tpr;
   const int grid = grid_for(A.nrows, rpb, mode == CSR_EIGRES ? kReduceBlocks : 0);
   if (nblocks_out) *nblocks_out = grid;
   if (A.nrows == 0) return PASE_OK;
@@ -175,7 +178,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   const T om = (T)omega;
 #define PASE_CSR_CASE(MD)                                                                   \
   case MD:                                                                                  \
-    k_csr<T, MD><<<grid, 256, 0, s>>>(A.nrows, m, ldx, ldy, tpr, rpb, A.rowptr, A.col, va, vm, X, X2, \
+    k_csr<T, MD><<<grid, bs, 0, s>>>(A.nrows, m, ldx, ldy, tpr, rpb, A.rowptr, A.col, va, vm, X, X2, \
                                        B, dinv, lam, om, Y1, Y2, partial);                   \
     break;
   switch (mode) {

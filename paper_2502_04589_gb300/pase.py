@@ -32,7 +32,7 @@ class PaseOptions(ctypes.Structure):
                 ("omega", ctypes.c_double), ("coarse_level", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class PaseStats(ctypes.Structure):
@@ -57,6 +57,7 @@ class PaseError(RuntimeError):
 _lib = None
 
 EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
+            "pase_solve_batched",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
             "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_residual_noalloc",
             "pase_time_kernel",
@@ -81,6 +82,9 @@ def load_library(path=LIB_PATH):
                              ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR)]
     L.pase_reserve.argtypes = [vp, i32]
     L.pase_solve.argtypes = [vp, i32, dbl, i32, vp, vp, vp, ctypes.POINTER(PaseStats)]
+    L.pase_solve_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
+                                     ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp), ctypes.POINTER(PaseStats)]
     L.pase_residual.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pase_linear_solve.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pase_project.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -97,7 +101,8 @@ def load_library(path=LIB_PATH):
     L.pase_status_string.restype = ctypes.c_char_p
     L.pase_last_error.argtypes = []
     L.pase_last_error.restype = ctypes.c_char_p
-    for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_residual",
+    for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_solve_batched",
+                 "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
                  "pase_iterate", "pase_spmm_am", "pase_residual_noalloc", "pase_time_kernel",
                  "pase_destroy"]:
@@ -189,6 +194,23 @@ def pase_solve(h, nev, tol, m, U0, lam, U):
     rc = _check(load_library().pase_solve(h, nev, tol, m, _ptr(U0), _ptr(lam), _ptr(U),
                                           ctypes.byref(st)), allow=(PASE_ERR_NOT_CONVERGED,))
     return rc, st.as_dict()
+
+
+def pase_solve_batched(handles, nev, tol, m, U0, lam, U):
+    """Solve independent problems concurrently; lists of per-problem arguments (U0 entries may
+    be None).  Returns (status, list of stats dicts)."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    NEV = (ctypes.c_int * n)(*nev)
+    TOL = (ctypes.c_double * n)(*tol)
+    M = (ctypes.c_int * n)(*m)
+    U0p = (ctypes.c_void_p * n)(*[_ptr(x) for x in U0])
+    Lp = (ctypes.c_void_p * n)(*[_ptr(x) for x in lam])
+    Up = (ctypes.c_void_p * n)(*[_ptr(x) for x in U])
+    st = (PaseStats * n)()
+    rc = _check(load_library().pase_solve_batched(H, n, NEV, TOL, M, U0p, Lp, Up, st),
+                allow=(PASE_ERR_NOT_CONVERGED,))
+    return rc, [s.as_dict() for s in st]
 
 
 def pase_residual(h, m, U, lam, R, relres):

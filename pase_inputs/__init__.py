@@ -270,6 +270,24 @@ WORKLOADS = {
 }
 
 
+def batch_workload(seed: int, count: int, sizes=(64, 128, 256, 512), nev_range=(8, 32),
+                   sigma_range=(0.5, 2.0)):
+    """Independent 2D problems of uneven size for the batched launch: for problem i, draws
+    4i..4i+3 of uniform01(seed) pick the fine mesh from `sizes`, the lognormal spread sigma
+    from `sigma_range`, nev uniformly from the integer range and the kappa field's seed.
+    Returns dicts (d, n, n_coarse = n/8, sigma, nev, kappa_seed)."""
+    u = uniform01(seed, 4 * count)
+    out = []
+    for i in range(count):
+        n = sizes[min(len(sizes) - 1, int(u[4 * i] * len(sizes)))]
+        sigma = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * u[4 * i + 1]
+        lo, hi = nev_range
+        nev = lo + min(hi - lo, int(u[4 * i + 2] * (hi - lo + 1)))
+        kseed = int(u[4 * i + 3] * 2**31)
+        out.append(dict(d=2, n=n, n_coarse=n // 8, sigma=float(sigma), nev=nev, kappa_seed=kseed))
+    return out
+
+
 def build_problem(d, n, n_coarse, kappa_seed=None, sigma=1.0, mg_min=None):
     kappa = None if kappa_seed is None else lognormal_kappa(d, n, kappa_seed, sigma)
     return Problem(d, n, n_coarse, kappa, mg_min=mg_min)
