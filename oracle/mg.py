@@ -10,6 +10,10 @@ the implementation).  Two plain references are given here:
   and a dense Cholesky solve on the coarsest level.
 * `cg`: conjugate gradients run independently on every column (the reading of
   "block CG" used here: one CG per right-hand side, column-wise inner products).
+* `pcg`: the same with a symmetric positive definite preconditioner applied to the
+  residual (here one V-cycle from zero, which is symmetric because pre- and
+  post-smoothing use the same number of damped Jacobi sweeps): textbook preconditioned
+  CG, z = B r, alpha = (r, z) / (p, A p), beta = (r_new, z_new) / (r, z).
 """
 import numpy as np
 import scipy.linalg as sl
@@ -69,4 +73,26 @@ def cg(A, F, X0, steps):
         beta = np.where(rr > 0, rr_new / np.where(rr > 0, rr, 1.0), 0.0)
         Pd = R + Pd * beta
         rr = rr_new
+    return X
+
+
+def pcg(A, F, X0, steps, precond):
+    """`steps` preconditioned CG iterations on A x_j = f_j for every column j, from X0;
+    precond(R) returns the preconditioned residual block Z = B R."""
+    X = X0.copy()
+    R = F - A @ X
+    Z = precond(R)
+    Pd = Z.copy()
+    rz = np.einsum("ij,ij->j", R, Z)
+    for _ in range(steps):
+        AP = A @ Pd
+        pAp = np.einsum("ij,ij->j", Pd, AP)
+        alpha = np.where(pAp > 0, rz / np.where(pAp > 0, pAp, 1.0), 0.0)
+        X += Pd * alpha
+        R -= AP * alpha
+        Z = precond(R)
+        rz_new = np.einsum("ij,ij->j", R, Z)
+        beta = np.where(rz > 0, rz_new / np.where(rz > 0, rz, 1.0), 0.0)
+        Pd = Z + Pd * beta
+        rz = rz_new
     return X

@@ -25,7 +25,7 @@ Readings taken where the paper is silent or garbled:
 import numpy as np
 import scipy.linalg as sl
 
-from .mg import Hierarchy, cg
+from .mg import Hierarchy, cg, pcg
 
 
 def relative_residuals(A, M, U, lam):
@@ -46,12 +46,17 @@ def linear_solve(A, M, U, lam, s, hier=None, solver="vcycle"):
     V-cycle form: correction E from s V-cycles on A E = M U Lambda - A U, E0 = 0, then
     W = U + E (the same iterate as s V-cycles from the initial guess U).
     CG form: s CG steps per column from the initial guess U.
+    MGCG form: s CG steps per column preconditioned by one V-cycle, from U.
     """
     F = (M @ U) * lam
     if solver == "vcycle":
         R = F - A @ U
         E = hier.solve(R, s)
         return U + E
+    if solver == "mgcg":
+        return pcg(A, F, U, s, lambda R: hier.solve(R, 1))
+    if solver != "cg":
+        raise ValueError(solver)
     return cg(A, F, U, s)
 
 
