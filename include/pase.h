@@ -59,11 +59,15 @@ extern "C" {
                              correction (w = u + V32(r64)); (b)-(d) and residuals in FP64  */
 
 #define PASE_SOLVER_VCYCLE 0 /* s V-cycles: damped Jacobi, Galerkin levels, dense coarsest */
-#define PASE_SOLVER_CG 1     /* s CG steps per column                                        */
+#define PASE_SOLVER_CG 1     /* s CG steps per column, column-wise inner products (the block
+                                CG of the paper's numerical section, one CG per column)   */
+#define PASE_SOLVER_MGCG 2   /* s CG steps per column preconditioned by one V-cycle (robust
+                                for rough coefficients); in MIXED precision the V-cycle runs
+                                in FP32, the CG recurrences in FP64                           */
 
 typedef struct {
   int precision;       /* PASE_PREC_FP64 (default) or PASE_PREC_MIXED                          */
-  int linear_solver;   /* PASE_SOLVER_VCYCLE (default) or PASE_SOLVER_CG                       */
+  int linear_solver;   /* PASE_SOLVER_VCYCLE (default), PASE_SOLVER_CG or PASE_SOLVER_MGCG      */
   int inner_steps;     /* s: V-cycles / CG steps per iteration (default 2)                     */
   int nu1, nu2;        /* damped-Jacobi pre / post sweeps (default 2, 2)                       */
   double omega;        /* Jacobi damping (default 2/3)                                         */
@@ -156,8 +160,9 @@ int pase_solve_batched(pase_handle* hs, int count, const int* nev, const double*
 int pase_residual(pase_handle h, int m, const double* U, const double* lambda, double* R,
                   double* relres);
 
-/* Step (a): W = U + E where E approximates A_h^-1 R after `inner_steps` V-cycles (or CG
- * steps on A_h w = M_h u lambda from w = u), R from pase_residual. */
+/* Step (a): W = U + E where E approximates A_h^-1 R after `inner_steps` V-cycles (or CG /
+ * V-cycle-preconditioned CG steps on A_h w = M_h u lambda from w = u), R from
+ * pase_residual (R = M_h U diag(lambda) - A_h U, the residual of that system at w = u). */
 int pase_linear_solve(pase_handle h, int m, const double* U, const double* lambda,
                       const double* R, double* W);
 

@@ -236,6 +236,11 @@ static int reserve(pase_ctx* h, int m) {
       PASE_TRY(dev_alloc_t(h, &w.ft2[l], k));
     }
   }
+  if (h->opt.linear_solver == PASE_SOLVER_CG || h->opt.linear_solver == PASE_SOLVER_MGCG) {
+    PASE_TRY(dev_alloc_t(h, &w.cgP, nm));
+    PASE_TRY(dev_alloc_t(h, &w.cgQ, nm));
+    PASE_TRY(dev_alloc_t(h, &w.cgs, 4 * (size_t)m));
+  }
   const int64_t m3 = 3 * (int64_t)m;
   int64_t pd = std::max<int64_t>((int64_t)kReduceBlocksHost * 2 * m, std::min<int64_t>(608 * m3 * m3, 32ll << 20));
   pd = std::max<int64_t>(pd, m3 * m3 * 4);
@@ -412,14 +417,66 @@ static LevelBufs<float> fp32_bufs(pase_ctx* h) {
   return B;
 }
 
-// Step (a): W = U + E, E from s V-cycles on A E = R (R already in w.R).
+// Z = B R with B one V-cycle from zero (R in w.R, Z in w.E); FP32 inside in MIXED precision.
+static int vcycle_precond(pase_ctx* h) {
+  Work& w = h->w;
+  const size_t nm = (size_t)h->N * w.m;
+  if (h->opt.precision == PASE_PREC_MIXED) {
+    LevelBufs<float> B = fp32_bufs(h);
+    PASE_TRY(launch_f64_to_f32(h, nm, w.R, B.b[0]));
+    PASE_TRY(vcycle<float>(h, B, 0, w.m, true));
+    return launch_f32_to_f64(h, nm, B.x[0], w.E);
+  }
+  LevelBufs<double> B = fp64_bufs(h);
+  return vcycle<double>(h, B, 0, w.m, true);
+}
+
+// Step (a), CG forms: s (preconditioned) CG steps per column on A w = M u lambda from
+// w = u.  The initial residual is R = M U Lambda - A U, already in w.R.  All scalars stay
+// on the device (column inner products, ratios), so the step has no host round trip.
+// Buffers: X = W, R = w.R, Z = w.E (MGCG) or R itself (CG), P = w.cgP, Q = A P = w.cgQ.
+static int step_cg(pase_ctx* h, const double* U, double* W) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int64_t N = h->N;
+  const int s = std::max(1, h->opt.inner_steps);
+  const bool pre = h->opt.linear_solver == PASE_SOLVER_MGCG;
+  const DevCSR& A = h->lv[0].A;
+  double* rz = w.cgs;
+  double* rz_new = w.cgs + m;
+  double* pq = w.cgs + 2 * m;
+  double* coef = w.cgs + 3 * m;
+  double* Z = pre ? w.E : w.R;
+  if (W != U) PASE_CUDA(cudaMemcpyAsync(W, U, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, h->stream));
+  if (pre) PASE_TRY(vcycle_precond(h));
+  PASE_TRY(launch_coldot(h, N, m, w.R, Z, rz));
+  PASE_CUDA(cudaMemcpyAsync(w.cgP, Z, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, h->stream));
+  int nb = 0;
+  for (int k = 0; k < s; ++k) {
+    // Q = A P with the column sums of P .* Q in the same pass
+    PASE_TRY(launch_csr<double>(h, CSR_MVDOT, m, A, A.val, nullptr, w.cgP, nullptr, nullptr, nullptr, nullptr,
+                                0.0, w.cgQ, nullptr, w.partial, &nb));
+    PASE_TRY(launch_reduce_partials(h, nb, m, w.partial, pq));
+    PASE_TRY(launch_ratio(h, m, rz, pq, coef));  // alpha
+    PASE_TRY(launch_cg_update(h, N, m, coef, w.cgP, w.cgQ, W, w.R));
+    if (k + 1 == s) break;
+    if (pre) PASE_TRY(vcycle_precond(h));
+    PASE_TRY(launch_coldot(h, N, m, w.R, Z, rz_new));
+    PASE_TRY(launch_ratio(h, m, rz_new, rz, coef));  // beta
+    PASE_TRY(launch_cg_dir(h, N, m, coef, Z, w.cgP));
+    std::swap(rz, rz_new);
+  }
+  return PASE_OK;
+}
+
+// Step (a): W = U + E, E from s V-cycles on A E = R (R already in w.R), or the CG forms.
 static int step_linear_solve(pase_ctx* h, const double* U, double* W) {
   Work& w = h->w;
   const int m = w.m;
   const int s = std::max(1, h->opt.inner_steps);
   const size_t nm = (size_t)h->N * m;
-  if (h->opt.linear_solver != PASE_SOLVER_VCYCLE)
-    return fail(PASE_ERR_INVALID_ARG, "only the V-cycle linear solver is available");
+  if (h->opt.linear_solver == PASE_SOLVER_CG || h->opt.linear_solver == PASE_SOLVER_MGCG) return step_cg(h, U, W);
+  if (h->opt.linear_solver != PASE_SOLVER_VCYCLE) return fail(PASE_ERR_INVALID_ARG, "unknown linear solver");
   if (h->opt.precision == PASE_PREC_MIXED) {
     LevelBufs<float> B = fp32_bufs(h);
     PASE_TRY(launch_f64_to_f32(h, nm, w.R, B.b[0]));
@@ -798,6 +855,7 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
   else pase_default_options(&h->opt);
   const pase_options& o = h->opt;
   if ((o.precision != PASE_PREC_FP64 && o.precision != PASE_PREC_MIXED) || o.inner_steps < 1 || o.nu1 < 0 ||
+      o.linear_solver < PASE_SOLVER_VCYCLE || o.linear_solver > PASE_SOLVER_MGCG ||
       o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||
       !(o.aug_tol > 0.0)) {
     delete h;

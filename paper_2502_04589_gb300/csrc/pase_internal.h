@@ -40,6 +40,12 @@ struct HostCSR {
 };
 
 int ensure_max_smem(const void* func, int bytes);
+int launch_coldot(pase_ctx* h, int64_t n, int m, const double* X, const double* Y, double* out);
+int launch_ratio(pase_ctx* h, int m, const double* num, const double* den, double* out);
+int launch_cg_update(pase_ctx* h, int64_t n, int m, const double* alpha, const double* P, const double* Q,
+                     double* X, double* R);
+int launch_cg_dir(pase_ctx* h, int64_t n, int m, const double* beta, const double* Z, double* P);
+int launch_f32_to_f64(pase_ctx* h, int64_t count, const float* x, double* y);
 int csr_from_abi(const pase_csr* in, HostCSR& out, const char* name);
 HostCSR csr_transpose(const HostCSR& a);
 HostCSR csr_multiply(const HostCSR& a, const HostCSR& b);  // a * b
@@ -95,6 +101,8 @@ struct Work {
   size_t eigwork_doubles = 0;
   double* smallvec = nullptr;                           // [16m]
   double *Rn = nullptr, *coef = nullptr;                // [n_c][m], [m][m]
+  double *cgP = nullptr, *cgQ = nullptr;                // CG direction and A times it [N][m]
+  double* cgs = nullptr;                                // CG scalars: (r,z) x2, (p,Ap), ratio [4m]
   int* status = nullptr;                                // device status words [8]
   // host pinned mirror for small readbacks
   double* h_small = nullptr;
@@ -153,6 +161,7 @@ enum CsrMode {
   CSR_MV = 0,       // Y1 = A X
   CSR_MV_AM = 1,    // Y1 = A X, Y2 = M X (shared pattern, second value array vm)
   CSR_RESID = 2,    // Y1 = B - A X
+  CSR_MVDOT = 7,    // Y1 = A X and per-block column sums of X .* (A X) (square A)
   CSR_JACOBI = 3,   // Y1 = X + omega dinv (B - A X)
   CSR_EIGRES = 4,   // Y1 = (M X) diag(lam) - A X, partial column sums of |Y1|^2, |MX|^2
   CSR_MV2 = 5,      // Y1 = A X, Y2 = A X2 (two inputs, one matrix)

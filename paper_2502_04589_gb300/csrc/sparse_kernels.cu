@@ -97,6 +97,12 @@ __global__ void __launch_bounds__(512) k_csr(int64_t n, int m, int64_t ldx, int6
       const int64_t ox = row * ldx + c0;
       if (MODE == CSR_MV) {
         V::store(Y1 + o, a1);
+      } else if (MODE == CSR_MVDOT) {
+        V::store(Y1 + o, a1);
+        T x[VW];
+        V::load(X + ox, x);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) sr[v] = fma((double)x[v], (double)a1[v], sr[v]);
       } else if (MODE == CSR_MV_AM || MODE == CSR_MV2) {
         V::store(Y1 + o, a1);
         V::store(Y2 + o, a2);
@@ -126,22 +132,24 @@ __global__ void __launch_bounds__(512) k_csr(int64_t n, int m, int64_t ldx, int6
       }
     }
   }
-  if (MODE == CSR_EIGRES) {
-    // block reduction of the column sums: red[2][rpb][m] with rpb*m <= 512*VW
-    __shared__ double red[2 * 512 * VW];
+  if (MODE == CSR_EIGRES || MODE == CSR_MVDOT) {
+    // block reduction of the column sums: red[nsum][rpb][m] with rpb*m <= 512*VW;
+    // EIGRES keeps two sums per column (|r|^2, |Mx|^2), MVDOT one (x . Ax)
+    constexpr int nsum = (MODE == CSR_EIGRES) ? 2 : 1;
+    __shared__ double red[nsum * 512 * VW];
     if (active) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         red[ty * m + c0 + v] = sr[v];
-        red[rpb * m + ty * m + c0 + v] = sm[v];
+        if (nsum == 2) red[(nsum - 1) * rpb * m + ty * m + c0 + v] = sm[v];
       }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
+    for (int j = threadIdx.x; j < nsum * m; j += blockDim.x) {
       const int half = j / m, c = j % m;
       double s = 0.0;
       for (int r = 0; r < rpb; ++r) s += red[half * rpb * m + r * m + c];
-      partial[(int64_t)blockIdx.x * 2 * m + j] = s;
+      partial[(int64_t)blockIdx.x * nsum * m + j] = s;
     }
   }
 }
@@ -171,7 +179,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   if (bs < tpr) bs = ((tpr + 31) / 32) * 32;
   if (bs > 512) bs = 512;
   const int rpb = bs / tpr;
-  const int grid = grid_for(A.nrows, rpb, mode == CSR_EIGRES ? kReduceBlocks : 0);
+  const int grid = grid_for(A.nrows, rpb, (mode == CSR_EIGRES || mode == CSR_MVDOT) ? kReduceBlocks : 0);
   if (nblocks_out) *nblocks_out = grid;
   if (A.nrows == 0) return PASE_OK;
   auto s = h->stream;
@@ -189,6 +197,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
     PASE_CSR_CASE(CSR_EIGRES)
     PASE_CSR_CASE(CSR_MV2)
     PASE_CSR_CASE(CSR_ADD)
+    PASE_CSR_CASE(CSR_MVDOT)
     default:
       return fail(PASE_ERR_INVALID_ARG, "launch_csr: bad mode");
   }
@@ -304,6 +313,128 @@ __global__ void k_fill(int64_t count, double v, double* __restrict__ x) {
 int launch_fill(pase_ctx* h, int64_t count, double v, double* x) {
   if (count == 0) return PASE_OK;
   k_fill<<<ew_grid(count), 256, 0, h->stream>>>(count, v, x);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// ------------------------------------------------------------------ CG building blocks
+// Column inner products out[j] = sum_i X[i][j] Y[i][j] of two [n][m] blocks: tpr = m/2
+// threads per row (one 16-byte column pair each), a grid-stride loop over rows, a fixed
+// per-block tree into partial[block][m] and the deterministic cross-block reduction.
+__global__ void __launch_bounds__(256) k_coldot(int64_t n, int m, int tpr, int rpb, const double* __restrict__ X,
+                                                const double* __restrict__ Y, double* __restrict__ partial) {
+  const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+  const bool active = ty < rpb;
+  const int c0 = 2 * tx;
+  double s0 = 0.0, s1 = 0.0;
+  if (active)
+    for (int64_t row = (int64_t)blockIdx.x * rpb + ty; row < n; row += (int64_t)gridDim.x * rpb) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(X + row * m + c0));
+      const double2 y = __ldg(reinterpret_cast<const double2*>(Y + row * m + c0));
+      s0 = fma(x.x, y.x, s0);
+      s1 = fma(x.y, y.y, s1);
+    }
+  __shared__ double red[512];  // rpb * m = (256 / tpr) * 2 tpr <= 512
+  if (active) {
+    red[ty * m + c0] = s0;
+    red[ty * m + c0 + 1] = s1;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += red[r * m + j];
+    partial[(int64_t)blockIdx.x * m + j] = s;
+  }
+}
+
+// out[j] = num[j] / den[j] if den[j] > 0, else 0 (a column whose CG has broken down or
+// converged exactly stops moving)
+__global__ void k_ratio(int m, const double* __restrict__ num, const double* __restrict__ den,
+                        double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) out[j] = den[j] > 0.0 ? num[j] / den[j] : 0.0;
+}
+
+// X += P diag(alpha), R -= Q diag(alpha), one 16-byte column pair per thread
+__global__ void k_cg_update(int64_t pairs, int m, const double* __restrict__ alpha, const double* __restrict__ P,
+                            const double* __restrict__ Q, double* __restrict__ X, double* __restrict__ R) {
+  const int hm = m / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pairs; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = 2 * (int)(i % hm);
+    const double a0 = alpha[c], a1 = alpha[c + 1];
+    const double2 p = __ldg(reinterpret_cast<const double2*>(P) + i);
+    const double2 q = __ldg(reinterpret_cast<const double2*>(Q) + i);
+    double2 x = reinterpret_cast<double2*>(X)[i];
+    double2 r = reinterpret_cast<double2*>(R)[i];
+    x.x = fma(a0, p.x, x.x);
+    x.y = fma(a1, p.y, x.y);
+    r.x = fma(-a0, q.x, r.x);
+    r.y = fma(-a1, q.y, r.y);
+    reinterpret_cast<double2*>(X)[i] = x;
+    reinterpret_cast<double2*>(R)[i] = r;
+  }
+}
+
+// P = Z + P diag(beta)
+__global__ void k_cg_dir(int64_t pairs, int m, const double* __restrict__ beta, const double* __restrict__ Z,
+                         double* __restrict__ P) {
+  const int hm = m / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pairs; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = 2 * (int)(i % hm);
+    const double2 z = __ldg(reinterpret_cast<const double2*>(Z) + i);
+    double2 p = reinterpret_cast<double2*>(P)[i];
+    p.x = fma(beta[c], p.x, z.x);
+    p.y = fma(beta[c + 1], p.y, z.y);
+    reinterpret_cast<double2*>(P)[i] = p;
+  }
+}
+
+__global__ void k_f32_to_f64(int64_t count, const float* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+int launch_coldot(pase_ctx* h, int64_t n, int m, const double* X, const double* Y, double* out) {
+  if (m <= 0 || m % 2 != 0 || m > 512) return fail(PASE_ERR_INVALID_ARG, "coldot: bad m");
+  if (n == 0) return launch_fill(h, m, 0.0, out);
+  const int tpr = m / 2, rpb = 256 / tpr;
+  const int grid = grid_for(n, rpb, kReduceBlocks);
+  k_coldot<<<grid, 256, 0, h->stream>>>(n, m, tpr, rpb, X, Y, h->w.partial);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return launch_reduce_partials(h, grid, m, h->w.partial, out);
+}
+
+int launch_ratio(pase_ctx* h, int m, const double* num, const double* den, double* out) {
+  k_ratio<<<(m + 127) / 128, 128, 0, h->stream>>>(m, num, den, out);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+int launch_cg_update(pase_ctx* h, int64_t n, int m, const double* alpha, const double* P, const double* Q,
+                     double* X, double* R) {
+  const int64_t pairs = n * (m / 2);
+  if (pairs == 0) return PASE_OK;
+  k_cg_update<<<ew_grid(pairs), 256, 0, h->stream>>>(pairs, m, alpha, P, Q, X, R);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+int launch_cg_dir(pase_ctx* h, int64_t n, int m, const double* beta, const double* Z, double* P) {
+  const int64_t pairs = n * (m / 2);
+  if (pairs == 0) return PASE_OK;
+  k_cg_dir<<<ew_grid(pairs), 256, 0, h->stream>>>(pairs, m, beta, Z, P);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+int launch_f32_to_f64(pase_ctx* h, int64_t count, const float* x, double* y) {
+  if (count == 0) return PASE_OK;
+  k_f32_to_f64<<<ew_grid(count), 256, 0, h->stream>>>(count, x, y);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;

@@ -18,6 +18,7 @@ PASE_PREC_FP64 = 0
 PASE_PREC_MIXED = 1
 PASE_SOLVER_VCYCLE = 0
 PASE_SOLVER_CG = 1
+PASE_SOLVER_MGCG = 2
 
 
 class PaseCSR(ctypes.Structure):

@@ -113,6 +113,43 @@ def test_linear_solve_parity(which, request):
         c.close()
 
 
+@pytest.mark.parametrize("solver,name", [(P.PASE_SOLVER_CG, "cg"), (P.PASE_SOLVER_MGCG, "mgcg")])
+@pytest.mark.parametrize("which", ["p2d", "p3d"])
+def test_linear_solve_cg_forms_parity(which, solver, name, request):
+    """CG and V-cycle-preconditioned CG step (a), FP64: the same recurrences as the
+    oracle, so only summation order differs."""
+    pb = request.getfixturevalue(which)
+    m = 16
+    c = Ctx(pb, linear_solver=solver, inner_steps=3)
+    try:
+        U = pin.start_vectors(5, pb.N, m)
+        lam = np.linspace(20.0, 300.0, m)
+        W = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        P.pase_linear_solve(c.h, m, dev(U), dev(lam), None, W)
+        hier = mg.Hierarchy(pb.A, pb.chain)
+        Wref = opase.linear_solve(pb.A, pb.M, U, lam, 3, hier, name)
+        assert _colrel(host(W) - U, Wref - U) < 1e-11
+    finally:
+        c.close()
+
+
+def test_linear_solve_mgcg_mixed_parity(p3d):
+    """MIXED precision: the V-cycle preconditioner runs in FP32 (unit roundoff 6e-8), the
+    CG recurrences in FP64; the correction agrees with the FP64 oracle to about 1e-6."""
+    pb = p3d
+    m = 16
+    c = Ctx(pb, P.PASE_PREC_MIXED, linear_solver=P.PASE_SOLVER_MGCG, inner_steps=3)
+    try:
+        U = pin.start_vectors(5, pb.N, m)
+        lam = np.linspace(20.0, 300.0, m)
+        W = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        P.pase_linear_solve(c.h, m, dev(U), dev(lam), None, W)
+        Wref = opase.linear_solve(pb.A, pb.M, U, lam, 3, mg.Hierarchy(pb.A, pb.chain), "mgcg")
+        assert _colrel(host(W) - U, Wref - U) < 1e-5
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("which", ["p2d", "p3d"])
 def test_project_parity(which, request):
     pb = request.getfixturevalue(which)
@@ -257,6 +294,26 @@ def test_solve_variable_kappa_2d():
     assert rc == P.PASE_OK, st
     ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
     _check_pairs(pb, lam, U, nev, ref, 1e-9)
+
+
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_solve_rough_kappa_mgcg(precision):
+    """Lognormal coefficient with sigma 1.9 (contrast ~1e6), where plain V-cycles stall:
+    V-cycle-preconditioned CG in step (a) converges."""
+    pb = pin.build_problem(2, 64, 8, kappa_seed=1634308976, sigma=1.9, mg_min=4)
+    nev = 12
+    rc, st, lam, U = _solve(pb, nev, 1e-8, precision, linear_solver=P.PASE_SOLVER_MGCG, inner_steps=3,
+                            max_iter=100)
+    assert rc == P.PASE_OK, st
+    ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+    _check_pairs(pb, lam, U, nev, ref, 1e-8)
+
+
+def test_solve_plain_cg():
+    pb = pin.build_problem(2, 32, 4, mg_min=4)
+    rc, st, lam, U = _solve(pb, 4, 1e-9, m=8, linear_solver=P.PASE_SOLVER_CG, inner_steps=10, max_iter=60)
+    assert rc == P.PASE_OK, st
+    _check_pairs(pb, lam, U, 4, spectrum.q1_laplace_eigenvalues(2, 32, 4), 1e-9)
 
 
 def test_solve_laplace_3d_32_cluster():
