@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 D, NFINE, NCOARSE, NEV, SEED = 3, 128, 16, 50, 0
 WORKLOAD = "laplace3d_q1_128_coarse16_nev50"
 METRIC = "DOF*nev/s per augmented-subspace iteration (3D Q1 128^3, nev 50, FP64)"
+# DRAM bytes (read + write) of one fine-level FP64 Jacobi sweep at the 128^3 workload, from
+# an ncu capture of the 64^3 case (profiles/k_csr_jacobi_laplace3d_64.md), scaled by rows
+JACOBI_TRAFFIC_BYTES = 3.277e9  # 400.1 MB at 64^3 scaled by rows (2,048,383 / 250,047)
 UNIT = "DOF*nev/s"
 
 
@@ -202,6 +205,31 @@ def run_batched(args, P, pin, torch, np, barrier):
             P.pase_destroy(h)
 
 
+def run_profile_kernel(args):
+    """One kernel of the path on the bench workload at --size, for ncu: two warm-up
+    launches, then three timed ones (capture with -k <kernel> -s 2 -c 1).  The handle is
+    created without the autotuner, so the sparse kernels run at 256 threads per block."""
+    import torch
+
+    from paper_2502_04589_gb300 import pase as P
+    pb, m = build_workload(args.size)
+    opt = P.pase_default_options()
+    opt.precision = P.PASE_PREC_MIXED if args.profile_kernel == "jacobi_fp32" else P.PASE_PREC_FP64
+    opt.coarse_level = pb.coarse_level
+    opt.autotune = 0
+    stream = torch.cuda.Stream()
+    h = P.pase_create(opt, stream.cuda_stream)
+    try:
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        P.pase_reserve(h, m)
+        ms = P.pase_time_kernel(h, args.profile_kernel, m, 3)
+    finally:
+        P.pase_destroy(h)
+    print(json.dumps({"profile_kernel": args.profile_kernel, "size": args.size, "N_h": pb.N, "nnz": pb.A.nnz,
+                      "block": m, "ms_per_launch": ms}), flush=True)
+    return 0
+
+
 def run_ours(args):
     # let up to 32 streams (the batched run) feed the GPU without false dependencies
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
@@ -236,7 +264,7 @@ def run_ours(args):
     U0h = pin.start_vectors(SEED + rank, pb.N, m)
     U0 = torch.from_numpy(U0h).cuda()
     U = U0.clone()
-    # dominant-kernel roofline: the fused A_h / M_h product (one pass over the pattern)
+    # the fused A_h / M_h product (one pass over the pattern), timed alone
     X = U0.clone()
     AX, MX = torch.empty_like(X), torch.empty_like(X)
     reps = 10
@@ -257,13 +285,10 @@ def run_ours(args):
     spmm_flops = 4.0 * nnz * m
     spmm_bytes = nnz * (4 + 16) + 8 * (pb.N + 1) + 3 * pb.N * m * 8
     peak_fp64 = 1.25e12
-    roofline = {"bound": "alu", "kernel": "k_csr<double, MV_AM> (fused A_h/M_h SpMM, FP64)",
-                "achieved": spmm_flops / (spmm_ms * 1e-3) / 1e12, "peak": peak_fp64 / 1e12,
-                "unit": "TFLOP/s", "frac": spmm_flops / (spmm_ms * 1e-3) / peak_fp64,
-                "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)",
-                "algorithmic_bytes": spmm_bytes,
-                "achieved_gbs": spmm_bytes / (spmm_ms * 1e-3) / 1e9, "ms": spmm_ms,
-                "clocks": kclocks}
+    spmm_live = {"kernel": "k_csr<double, MV_AM> (fused A_h/M_h SpMM, FP64)", "ms": spmm_ms,
+                 "tflops": spmm_flops / (spmm_ms * 1e-3) / 1e12,
+                 "frac": spmm_flops / (spmm_ms * 1e-3) / peak_fp64,
+                 "achieved_gbs": spmm_bytes / (spmm_ms * 1e-3) / 1e9, "clocks": kclocks}
 
     lam = torch.zeros(m, dtype=torch.float64, device="cuda")
     relres = torch.zeros(m, dtype=torch.float64, device="cuda")
@@ -274,6 +299,9 @@ def run_ours(args):
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
+    # the dominant kernel (fine-level FP64 damped-Jacobi sweep, most of step (a)) is timed
+    # live: the library brackets each of its launches with CUDA events on its stream
+    P.pase_profile_kernel(h, "jacobi_fp64")
     k0 = P.pase_kernel_count(h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -283,6 +311,22 @@ def run_ours(args):
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
+    jac_n, jac_ms_total = P.pase_profile_read(h)
+    P.pase_profile_kernel(h, None)
+    jac_ms = jac_ms_total / max(1, jac_n)
+    jac_flops = 2.0 * nnz * m + 3.0 * pb.N * m
+    jac_bytes = nnz * 12 + 16 * pb.N + 3 * pb.N * m * 8
+    roofline = {"bound": "alu", "kernel": "k_csr<double, JACOBI> (damped Jacobi sweep on A_h, FP64)",
+                "achieved": jac_flops / (jac_ms * 1e-3) / 1e12, "peak": peak_fp64 / 1e12,
+                "unit": "TFLOP/s", "frac": jac_flops / (jac_ms * 1e-3) / peak_fp64,
+                "traffic": JACOBI_TRAFFIC_BYTES,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table; no FP64 figure is measured "
+                               "in the peaks file)",
+                "flops_per_launch": jac_flops, "algorithmic_bytes": jac_bytes,
+                "achieved_gbs": jac_bytes / (jac_ms * 1e-3) / 1e9, "ms": jac_ms,
+                "launches_timed": jac_n, "launches_per_step": jac_n / max(1, args.steps),
+                "share_of_step": jac_ms_total / (ev0.elapsed_time(ev1)),
+                "timing": "CUDA events around each launch on the library stream, inside the timed steps"}
     launches = (P.pase_kernel_count(h) - k0) // max(1, args.steps)
     ms = ev0.elapsed_time(ev1) / args.steps
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -299,7 +343,7 @@ def run_ours(args):
         P.pase_spmm_am(h, m, X, AX, MX)
     e1.record(stream)
     torch.cuda.synchronize()
-    roofline["ms_on_iterated_block"] = e0.elapsed_time(e1) / reps
+    spmm_live["ms_on_iterated_block"] = e0.elapsed_time(e1) / reps
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()
@@ -337,8 +381,8 @@ def run_ours(args):
     hk = make(P.PASE_PREC_MIXED)
     for name, flops, nbytes, bound in (
             ("spmm_am_fp64", 4.0 * nnz * m, nnz * 20 + 8 * (N + 1) + 3 * N * m * 8, "alu"),
-            ("jacobi_fp64", 2.0 * nnz * m, nnz * 12 + 16 * N + 3 * N * m * 8, "alu"),
-            ("jacobi_fp32", 2.0 * nnz * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
+            ("jacobi_fp64", 2.0 * nnz * m + 3.0 * N * m, nnz * 12 + 16 * N + 3 * N * m * 8, "alu"),
+            ("jacobi_fp32", 2.0 * nnz * m + 3.0 * N * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
             ("gram_fp64", 1.0 * N * m * (m + 4), 2 * N * m * 8, "alu"),
             ("prolong_fp64", 2.0 * N * m * m, 2 * N * m * 8, "alu")):
         try:
@@ -398,7 +442,7 @@ def run_ours(args):
                            "block": m, "linear_solve": "2 V-cycles, damped Jacobi 2+2, omega 2/3",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (block 0.92 GB)"},
-                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "spmm_fp64": spmm_live, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "solve": solves, "batched": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -414,6 +458,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-kernel", default=None,
+                    help="only launch this kernel (spmm_am_fp64, jacobi_fp64, jacobi_fp32, ...) for ncu")
     ap.add_argument("--batch", type=int, default=64,
                     help="independent problems in the batched run (0 skips it)")
     ap.add_argument("--size", type=int, default=NFINE,
@@ -423,6 +469,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_kernel:
+        return run_profile_kernel(args)
     return run_ours(args)
 
 

@@ -227,6 +227,16 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_SYGV3 6         /* the same with n = 3m, k = m (step-(c) Rayleigh-Ritz) */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
+/* Live timing of one kernel while the handle works (pase_solve, pase_iterate, ...): with
+ * kernel = PASE_KERNEL_SPMM_AM_FP64, _JACOBI_FP64 or _JACOBI_FP32, every launch of that
+ * kernel on the fine level is bracketed by a pair of CUDA events on the handle's stream
+ * (at most 4096 launches between reads; later ones are not timed).  Graph replay of step
+ * (a) is suspended while a kernel is selected.  kernel = -1 stops.
+ * pase_profile_read waits for the handle's stream, returns the number of timed launches
+ * and their summed duration in ms since the last read, and starts a new count. */
+int pase_profile_kernel(pase_handle h, int kernel);
+int pase_profile_read(pase_handle h, int64_t* launches, double* total_ms);
+
 /* Number of library kernels launched by this handle so far. */
 int64_t pase_kernel_count(pase_handle h);
 

@@ -135,6 +135,27 @@ struct Stage {
   }
 };
 
+// ------------------------------------------------------------------ live kernel timing
+constexpr size_t kProfMaxLaunches = 4096;
+void prof_begin(pase_ctx* h, int id) {
+  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches) return;
+  while (h->prof_ev.size() < 2 * (h->prof_n + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    h->prof_ev.push_back(e);
+  }
+  cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
+}
+void prof_end(pase_ctx* h, int id) {
+  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches || h->prof_ev.size() < 2 * (h->prof_n + 1))
+    return;
+  cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
+  h->prof_n++;
+}
+
 // ------------------------------------------------------------------ autotuner
 // For every multigrid matrix, time the damped-Jacobi sweep (the precision the linear solve
 // runs in) at 128, 256 and 512 threads per block and keep the fastest.  Deterministic
@@ -495,7 +516,8 @@ static int step_linear_solve(pase_ctx* h, const double* U, double* W) {
 // of them runs eagerly and also sets up kernel attributes); later calls with that pair
 // replay it, calls with other buffers run eagerly.
 static int step_linear_solve_graphed(pase_ctx* h, const double* U, double* W) {
-  if (!h->opt.use_graphs || !h->graphs_ok || h->stream == nullptr) return step_linear_solve(h, U, W);
+  if (!h->opt.use_graphs || !h->graphs_ok || h->stream == nullptr || h->prof_kernel >= 0)
+    return step_linear_solve(h, U, W);
   if (h->ls_graph && h->ls_graph_U == U && h->ls_graph_W == W) {
     PASE_CUDA(cudaGraphLaunch(h->ls_graph, h->stream));
     h->launches += h->ls_graph_kernels;
@@ -876,6 +898,7 @@ int pase_destroy(pase_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->ls_graph) cudaGraphExecDestroy(h->ls_graph);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_small) cudaFreeHost(h->w.h_small);
   if (h->w.h_status) cudaFreeHost(h->w.h_status);
@@ -1283,6 +1306,33 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_nconv = 0;
   if (stp) *stp = st;
   return rc;
+}
+
+int pase_profile_kernel(pase_handle h, int kernel) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (kernel != -1 && kernel != PASE_KERNEL_SPMM_AM_FP64 && kernel != PASE_KERNEL_JACOBI_FP64 &&
+      kernel != PASE_KERNEL_JACOBI_FP32)
+    return fail(PASE_ERR_INVALID_ARG, "pase_profile_kernel: only the fine-level sparse kernels can be timed live");
+  if (h->stream) PASE_CUDA(cudaStreamSynchronize(h->stream));
+  h->prof_kernel = kernel;
+  h->prof_n = 0;
+  return PASE_OK;
+}
+
+int pase_profile_read(pase_handle h, int64_t* launches, double* total_ms) {
+  if (!h || !launches || !total_ms) return fail(PASE_ERR_INVALID_ARG, "pase_profile_read: bad arguments");
+  if (h->stream) PASE_CUDA(cudaStreamSynchronize(h->stream));
+  else PASE_CUDA(cudaDeviceSynchronize());
+  double sum = 0.0;
+  for (size_t i = 0; i < h->prof_n; ++i) {
+    float ms = 0.f;
+    PASE_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    sum += ms;
+  }
+  *launches = (int64_t)h->prof_n;
+  *total_ms = sum;
+  h->prof_n = 0;
+  return PASE_OK;
 }
 
 int pase_solve_batched(pase_handle* hs, int count, const int* nev, const double* tol, const int* m,

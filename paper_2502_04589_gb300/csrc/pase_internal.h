@@ -40,6 +40,9 @@ struct HostCSR {
 };
 
 int ensure_max_smem(const void* func, int bytes);
+// bracket a launch of kernel `id` with timing events when that kernel is selected
+void prof_begin(pase_ctx* h, int id);
+void prof_end(pase_ctx* h, int id);
 int launch_coldot(pase_ctx* h, int64_t n, int m, const double* X, const double* Y, double* out);
 int launch_ratio(pase_ctx* h, int m, const double* num, const double* den, double* out);
 int launch_cg_update(pase_ctx* h, int64_t n, int m, const double* alpha, const double* P, const double* Q,
@@ -136,6 +139,10 @@ struct pase_ctx {
   const double* ls_graph_U = nullptr;
   double* ls_graph_W = nullptr;
   int64_t ls_graph_kernels = 0;
+  // live timing of one kernel (pase_profile_kernel): event pairs on the handle's stream
+  int prof_kernel = -1;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_n = 0;
   const double* ls_last_U = nullptr;  // buffers of the previous step-(a) call
   const double* ls_last_W = nullptr;
   bool graphs_ok = true;

@@ -184,6 +184,12 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   if (A.nrows == 0) return PASE_OK;
   auto s = h->stream;
   const T om = (T)omega;
+  int prof_id = -1;
+  if (h->prof_kernel >= 0 && !h->lv.empty() && &A == &h->lv[0].A) {
+    if (mode == CSR_MV_AM && sizeof(T) == 8) prof_id = PASE_KERNEL_SPMM_AM_FP64;
+    if (mode == CSR_JACOBI) prof_id = sizeof(T) == 8 ? PASE_KERNEL_JACOBI_FP64 : PASE_KERNEL_JACOBI_FP32;
+  }
+  prof_begin(h, prof_id);
 #define PASE_CSR_CASE(MD)                                                                   \
   case MD:                                                                                  \
     k_csr<T, MD><<<grid, bs, 0, s>>>(A.nrows, m, ldx, ldy, tpr, rpb, A.rowptr, A.col, va, vm, X, X2, \
@@ -202,6 +208,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
       return fail(PASE_ERR_INVALID_ARG, "launch_csr: bad mode");
   }
 #undef PASE_CSR_CASE
+  prof_end(h, prof_id);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;

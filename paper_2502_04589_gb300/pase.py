@@ -58,7 +58,7 @@ class PaseError(RuntimeError):
 _lib = None
 
 EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
-            "pase_solve_batched",
+            "pase_solve_batched", "pase_profile_kernel", "pase_profile_read",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
             "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_residual_noalloc",
             "pase_time_kernel",
@@ -95,6 +95,8 @@ def load_library(path=LIB_PATH):
     L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
     L.pase_residual_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.pase_time_kernel.argtypes = [vp, i32, i32, i32, ctypes.POINTER(dbl)]
+    L.pase_profile_kernel.argtypes = [vp, i32]
+    L.pase_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
     L.pase_destroy.argtypes = [vp]
@@ -106,6 +108,7 @@ def load_library(path=LIB_PATH):
                  "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
                  "pase_iterate", "pase_spmm_am", "pase_residual_noalloc", "pase_time_kernel",
+                 "pase_profile_kernel", "pase_profile_read",
                  "pase_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
@@ -264,6 +267,20 @@ def pase_time_kernel(h, kernel, m, reps=10):
     ms = ctypes.c_double(0.0)
     _check(load_library().pase_time_kernel(h, KERNELS.get(kernel, kernel), m, reps, ctypes.byref(ms)))
     return ms.value
+
+
+def pase_profile_kernel(h, kernel):
+    """Time every fine-level launch of `kernel` (name or id; None stops) while h works."""
+    k = -1 if kernel is None else KERNELS.get(kernel, kernel)
+    _check(load_library().pase_profile_kernel(h, k))
+
+
+def pase_profile_read(h):
+    """(launches, total_ms) timed since the last read."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(load_library().pase_profile_read(h, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def pase_kernel_count(h):
