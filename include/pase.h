@@ -120,6 +120,9 @@ int pase_create(pase_handle* h, const pase_options* opt, void* cuda_stream);
  * product P[0] P[1] ... P[c-1], c = coarse_level, is I_H^h (§3 lets the interpolation be
  * one matrix or a product of several).  Levels below c serve the multigrid solver only.  A_H and
  * M_H live on level c.  A_h and M_h must share one sparsity pattern (as do A_H, M_H).
+ * A_H and M_H may both be NULL: the library then forms them as the Galerkin products
+ * through the chain (the coarse pencil of nested spaces, computed on the host with
+ * OpenMP), which saves the caller forming them for large meshes.
  * Setup validates the CSR arrays, builds the Galerkin multigrid levels
  * A_{k+1} = P[k]^T A_k P[k], the direct interpolation I_H^h and its transpose, a dense
  * inverse of the coarsest multigrid operator, and uploads everything to the device. */

@@ -914,13 +914,17 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
   HostCSR A0, M0, AHc, MHc;
   PASE_TRY(csr_from_abi(A_h, A0, "A_h"));
   PASE_TRY(csr_from_abi(M_h, M0, "M_h"));
-  PASE_TRY(csr_from_abi(A_H, AHc, "A_H"));
-  PASE_TRY(csr_from_abi(M_H, MHc, "M_H"));
+  const bool coarse_given = A_H != nullptr || M_H != nullptr;
+  if (coarse_given) {
+    PASE_TRY(csr_from_abi(A_H, AHc, "A_H"));
+    PASE_TRY(csr_from_abi(M_H, MHc, "M_H"));
+  }
   std::vector<HostCSR> Pc(n_interp);
   for (int k = 0; k < n_interp; ++k) PASE_TRY(csr_from_abi(&P[k], Pc[k], "P"));
   if (A0.nrows != A0.ncols || A0.nrows == 0) return fail(PASE_ERR_SHAPE_MISMATCH, "A_h must be square and non-empty");
   if (!same_pattern(A0, M0)) return fail(PASE_ERR_PATTERN_MISMATCH, "A_h and M_h must share one sparsity pattern");
-  if (!same_pattern(AHc, MHc)) return fail(PASE_ERR_PATTERN_MISMATCH, "A_H and M_H must share one sparsity pattern");
+  if (coarse_given && !same_pattern(AHc, MHc))
+    return fail(PASE_ERR_PATTERN_MISMATCH, "A_H and M_H must share one sparsity pattern");
   int c = h->opt.coarse_level < 0 ? n_interp : h->opt.coarse_level;
   if (c < 1 || c > n_interp) return fail(PASE_ERR_INVALID_ARG, "coarse_level out of range");
   int64_t rows = A0.nrows;
@@ -934,6 +938,12 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
   std::vector<HostCSR> Al(h->L);
   Al[0] = A0;
   for (int k = 0; k < n_interp; ++k) Al[k + 1] = csr_galerkin(Pc[k], Al[k]);
+  if (!coarse_given) {  // the coarse pencil of nested spaces: Galerkin products through the chain
+    AHc = Al[c];
+    MHc = M0;
+    for (int k = 0; k < c; ++k) MHc = csr_galerkin(Pc[k], MHc);
+    if (!same_pattern(AHc, MHc)) return fail(PASE_ERR_PATTERN_MISMATCH, "Galerkin A_H and M_H patterns differ");
+  }
   if (AHc.nrows != Al[c].nrows || AHc.ncols != Al[c].nrows)
     return fail(PASE_ERR_SHAPE_MISMATCH, "A_H does not match the size of the coarse level");
   const HostCSR& Ac = Al[h->L - 1];

@@ -175,17 +175,19 @@ def pase_create(opt=None, stream=None):
     return h
 
 
-def pase_setup(h, A_h, M_h, P, A_H, M_H):
-    """A_h, M_h, A_H, M_H: scipy CSR; P: list of scipy CSR (the interpolation chain)."""
+def pase_setup(h, A_h, M_h, P, A_H=None, M_H=None):
+    """A_h, M_h, A_H, M_H: scipy CSR; P: list of scipy CSR (the interpolation chain).
+    A_H and M_H may both be None (the library forms the Galerkin coarse pencil)."""
     keep = []
     def conv(X):
         c, k = csr_from_scipy(X)
         keep.append(k)
         return c
-    cA, cM, cAH, cMH = conv(A_h), conv(M_h), conv(A_H), conv(M_H)
+    cA, cM = conv(A_h), conv(M_h)
+    cAH = ctypes.byref(conv(A_H)) if A_H is not None else None
+    cMH = ctypes.byref(conv(M_H)) if M_H is not None else None
     arr = (PaseCSR * len(P))(*[conv(p) for p in P])
-    return _check(load_library().pase_setup(h, ctypes.byref(cA), ctypes.byref(cM), len(P), arr,
-                                            ctypes.byref(cAH), ctypes.byref(cMH)))
+    return _check(load_library().pase_setup(h, ctypes.byref(cA), ctypes.byref(cM), len(P), arr, cAH, cMH))
 
 
 def pase_reserve(h, m):

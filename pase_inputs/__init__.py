@@ -24,6 +24,8 @@ Conventions
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 import scipy.sparse as sp
 
@@ -62,6 +64,13 @@ def start_vectors(seed: int, n_rows: int, n_cols: int) -> np.ndarray:
     """
     u = uniform01(seed, n_rows * n_cols)
     return (2.0 * u - 1.0).reshape(n_rows, n_cols)
+
+
+def start_vector_rows(seed: int, n_cols: int, row0: int, row1: int) -> np.ndarray:
+    """Rows row0..row1-1 of the start block of start_vectors(seed, ., n_cols), generated
+    alone (entry (i, j) is still output i*n_cols + j), for blocks too large to build at once."""
+    u = uniform01(seed, (row1 - row0) * n_cols, start=row0 * n_cols)
+    return (2.0 * u - 1.0).reshape(row1 - row0, n_cols)
 
 
 def standard_normals(seed: int, count: int) -> np.ndarray:
@@ -235,17 +244,31 @@ class Problem:
                 sizes.append(sizes[-1] // 2)
         self.mesh_sizes = sizes
         self.chain = [q1_interpolation(d, sizes[k], sizes[k + 1]) for k in range(len(sizes) - 1)]
-        As, Ms = [self.A], [self.M]
-        for P in self.chain:
-            As.append(galerkin(P, As[-1]))
-            Ms.append(galerkin(P, Ms[-1]))
-        self.levels_A, self.levels_M = As, Ms
-        self.A_H = As[self.coarse_level]
-        self.M_H = Ms[self.coarse_level]
+
+    # The coarse pencil and the direct interpolation are built on first use, so that large
+    # fine meshes can be handed to a library that forms them itself.
+    @functools.cached_property
+    def _coarse(self):
+        A, M = self.A, self.M
+        for k in range(self.coarse_level):
+            A, M = galerkin(self.chain[k], A), galerkin(self.chain[k], M)
+        return A, M
+
+    @property
+    def A_H(self):
+        return self._coarse[0]
+
+    @property
+    def M_H(self):
+        return self._coarse[1]
+
+    @functools.cached_property
+    def P(self):
+        """Direct V_H -> V_h interpolation (product of the chain down to the coarse level)."""
         P = self.chain[0] if self.chain else sp.identity(self.A.shape[0], format="csr")
         for k in range(1, self.coarse_level):
             P = P @ self.chain[k]
-        self.P = canonical_csr(P)  # direct V_H -> V_h interpolation
+        return canonical_csr(P)
 
     @property
     def N(self):

@@ -171,8 +171,10 @@ def test_project_parity(which, request):
         c.close()
 
 
-@pytest.mark.parametrize("which,m", [("p2d", 8), ("p2d", 16), ("p3d", 24)])
+@pytest.mark.parametrize("which,m", [("p2d", 8), ("p2d", 16), ("p3d", 24), ("p3d", 96)])
 def test_augmented_eig_parity(which, m, request):
+    """m = 96 gives Rayleigh-Ritz blocks of 3m = 288 whose triangles no longer fit in
+    shared memory, so the global-memory variants of the small eigensolver run."""
     pb = request.getfixturevalue(which)
     c = Ctx(pb, aug_adaptive=0, aug_max_iter=200)
     try:
@@ -324,6 +326,33 @@ def test_solve_laplace_3d_32_cluster():
     rc, st, lam, U = _solve(pb, nev, 1e-8)
     assert rc == P.PASE_OK, st
     _check_pairs(pb, lam, U, nev, spectrum.q1_laplace_eigenvalues(3, 32, nev), 1e-8)
+
+
+def test_setup_forms_coarse_pencil_when_not_given():
+    """A_H = M_H = NULL: the library's Galerkin products through the chain give the same
+    solve as the caller's."""
+    pb = pin.build_problem(2, 64, 8, kappa_seed=21, mg_min=4)
+    nev, m = 6, 16
+    out = []
+    for given in (True, False):
+        opt = P.pase_default_options()
+        opt.coarse_level = pb.coarse_level
+        h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+        try:
+            if given:
+                P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+            else:
+                P.pase_setup(h, pb.A, pb.M, pb.chain)
+            U0 = dev(pin.start_vectors(0, pb.N, m))
+            U = torch.empty_like(U0)
+            lam = torch.empty(m, dtype=torch.float64, device="cuda")
+            rc, st = P.pase_solve(h, nev, 1e-9, m, U0, lam, U)
+            assert rc == P.PASE_OK
+            out.append((st["iterations"], host(lam)[:nev]))  # guard columns are not converged
+        finally:
+            P.pase_destroy(h)
+    assert out[0][0] == out[1][0]
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-12)
 
 
 def test_coarse_start():
