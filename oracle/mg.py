@@ -20,7 +20,10 @@ import scipy.linalg as sl
 
 
 class Hierarchy:
-    def __init__(self, A0, chain, omega=2.0 / 3.0, nu1=2, nu2=2):
+    """fine_smoother (optional): a callable r -> correction that replaces each damped
+    Jacobi sweep on level 0 (x <- x + S(b - A x)); coarser levels keep Jacobi."""
+
+    def __init__(self, A0, chain, omega=2.0 / 3.0, nu1=2, nu2=2, fine_smoother=None):
         self.A = [A0.tocsr()]
         for P in chain:
             self.A.append((P.T @ (self.A[-1] @ P)).tocsr())
@@ -28,6 +31,7 @@ class Hierarchy:
         self.PT = [P.T.tocsr() for P in chain]
         self.Dinv = [1.0 / A.diagonal() for A in self.A]
         self.omega, self.nu1, self.nu2 = omega, nu1, nu2
+        self.fine_smoother = fine_smoother
         self.coarse_chol = sl.cho_factor(self.A[-1].toarray(), lower=True)
 
     @property
@@ -36,7 +40,10 @@ class Hierarchy:
 
     def smooth(self, l, b, x, sweeps):
         for _ in range(sweeps):
-            x = x + self.omega * self.Dinv[l][:, None] * (b - self.A[l] @ x)
+            if l == 0 and self.fine_smoother is not None:
+                x = x + self.fine_smoother(b - self.A[l] @ x)
+            else:
+                x = x + self.omega * self.Dinv[l][:, None] * (b - self.A[l] @ x)
         return x
 
     def vcycle(self, l, b, x=None):

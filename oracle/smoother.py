@@ -1,0 +1,210 @@
+"""Learned fine-level smoother: a small convolutional network in place of damped Jacobi
+inside the V-cycle of the step-(a) linear solve (test infrastructure only).
+
+The paper has no learned smoother; this module states the definition the CUDA path is
+checked against, in plain float64 NumPy:
+
+Grid.  The fine level is the (n-1)^d interior-node grid of the uniform n^d Q1 mesh,
+node i = sum_k c_k (n-1)^k (x fastest).  The node feature f_i is the mean of log kappa
+over the 2^d elements that contain node i.
+
+Network (per column of a block, independently).  Input channels: s_i = (D^-1 r)_i / rho
+and f_i, rho = sqrt(mean_i (D^-1 r)_i^2) (the column's root-mean-square Jacobi-scaled
+residual; rho = 0 gives a zero correction).  Four 3^d convolutions with zero padding,
+2 -> 16 -> 16 -> 16 -> 1 channels, ReLU after the first three.  Convolution:
+    y[b, co, i] = bias[co] + sum_ci sum_t W[co, ci, t] x[b, ci, i + o_t],
+tap t = sum_k (o_k + 1) 3^k for offsets o in {-1, 0, 1}^d (x fastest).
+Correction: delta = rho * y, so S(alpha r) = alpha S(r) for alpha > 0.
+
+Parameters: one flat vector [W1, b1, W2, b2, W3, b3, W4, b4], W_l in [co][ci][t] order.
+The forward pass uses the parameters rounded to bfloat16 (round to nearest even); the
+master copy that Adam updates stays in float32 (straight-through: the gradient with
+respect to the rounded parameters is applied to the master copy).
+
+Training loss (per column j; r = A e is the residual of the error e that the solver's
+iterate still carries):  L_j = (e - delta)^T A (e - delta) / (e^T r), the squared energy
+norm of the error left after one smoothing step relative to the error before it; the
+batch loss is the mean over columns.  Adam as in Kingma & Ba (2015).
+
+Use in the V-cycle: on level 0 each of the nu1 pre- and nu2 post-smoothing sweeps
+x <- x + omega D^-1 (b - A x) becomes x <- x + S(b - A x); coarser levels keep Jacobi.
+
+Parity: pinned in tests/test_oracle_pins.py (convolution against scipy.ndimage,
+finite-difference gradients, positive homogeneity, the Jacobi-equivalent weights,
+Adam's first step in closed form, the loss at delta = 0 and delta = e).
+"""
+import numpy as np
+
+CHANNELS = 16
+
+
+def layer_shapes(d):
+    """(c_in, c_out, relu) of the four layers."""
+    return [(2, CHANNELS, True), (CHANNELS, CHANNELS, True), (CHANNELS, CHANNELS, True), (CHANNELS, 1, False)]
+
+
+def taps(d):
+    return 3 ** d
+
+
+def n_params(d):
+    return sum(co * ci * taps(d) + co for ci, co, _ in layer_shapes(d))
+
+
+def unpack(params, d):
+    """[(W [co][ci][t], b [co], relu)] views of the flat parameter vector."""
+    out, o = [], 0
+    T = taps(d)
+    for ci, co, relu in layer_shapes(d):
+        W = params[o:o + co * ci * T].reshape(co, ci, T)
+        o += co * ci * T
+        b = params[o:o + co]
+        o += co
+        out.append((W, b, relu))
+    assert o == len(params)
+    return out
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def offsets(d):
+    """Offset vectors o_t, t = sum_k (o_k + 1) 3^k."""
+    T = taps(d)
+    return [tuple((t // 3 ** k) % 3 - 1 for k in range(d)) for t in range(T)]
+
+
+def _shift(X, o, d, n1):
+    """X[..., i + o] on the grid with zero outside; X [..., N] with N = n1^d (x fastest)."""
+    lead = X.shape[:-1]
+    G = X.reshape(lead + (n1,) * d)  # axes: ..., c_{d-1}, ..., c_0
+    out = np.zeros_like(G)
+    src, dst = [], []
+    for k in reversed(range(d)):  # grid axis order: highest coordinate first
+        ok = o[k]
+        if ok == 0:
+            src.append(slice(None))
+            dst.append(slice(None))
+        elif ok > 0:
+            src.append(slice(ok, None))
+            dst.append(slice(None, -ok))
+        else:
+            src.append(slice(None, ok))
+            dst.append(slice(-ok, None))
+    out[(Ellipsis,) + tuple(dst)] = G[(Ellipsis,) + tuple(src)]
+    return out.reshape(X.shape)
+
+
+def conv(X, W, b, d, n1):
+    """X [B][ci][N] -> [B][co][N], zero padding."""
+    B, ci, N = X.shape
+    co = W.shape[0]
+    Y = np.broadcast_to(b[None, :, None], (B, co, N)).astype(np.float64).copy()
+    for t, o in enumerate(offsets(d)):
+        Xs = _shift(X, o, d, n1)
+        Y += np.einsum("oc,bcn->bon", W[:, :, t], Xs)
+    return Y
+
+
+def node_features(d, n, log_kappa):
+    """Mean of log kappa over the 2^d elements around each interior node."""
+    n1 = n - 1
+    L = np.asarray(log_kappa, dtype=np.float64).reshape((n,) * d)
+    acc = np.zeros((n1,) * d)
+    for corner in range(2 ** d):
+        sl = []
+        for k in reversed(range(d)):
+            lo = (corner >> k) & 1
+            sl.append(slice(lo, lo + n1))
+        acc += L[tuple(sl)]
+    return (acc / 2 ** d).reshape(-1)
+
+
+def forward(params, s, feat, d, n1, round_bf16=True):
+    """s [B][N] (normalised Jacobi-scaled residual), feat [N] -> y [B][N] and a cache."""
+    p = bf16_round(params) if round_bf16 else np.asarray(params, dtype=np.float64)
+    B = s.shape[0]
+    x = np.stack([s, np.broadcast_to(feat, s.shape)], axis=1)
+    cache = []
+    for W, bb, relu in unpack(p, d):
+        z = conv(x, W, bb, d, n1)
+        cache.append((x, z))
+        x = np.maximum(z, 0.0) if relu else z
+    return x[:, 0, :], (p, cache)
+
+
+def backward(cache, gy, d, n1):
+    """Gradient of sum(gy * y) with respect to the (rounded) parameters, flat."""
+    p, layers = cache
+    grads = []
+    g = gy[:, None, :]
+    for li in reversed(range(len(layers))):
+        W, bb, relu = unpack(p, d)[li]
+        x, z = layers[li]
+        if relu:
+            g = g * (z > 0.0)
+        gW = np.zeros_like(W)
+        for t, o in enumerate(offsets(d)):
+            gW[:, :, t] = np.einsum("bon,bcn->oc", g, _shift(x, o, d, n1))
+        gb = g.sum(axis=(0, 2))
+        grads.append((gW, gb))
+        if li > 0:  # gradient with respect to this layer's input (transposed convolution)
+            gx = np.zeros_like(x)
+            for t, o in enumerate(offsets(d)):
+                gx += _shift(np.einsum("oc,bon->bcn", W[:, :, t], g), tuple(-v for v in o), d, n1)
+            g = gx
+    flat = []
+    for gW, gb in reversed(grads):
+        flat.append(gW.reshape(-1))
+        flat.append(gb)
+    return np.concatenate(flat)
+
+
+def normalise(r, dinv):
+    """r [N][B] -> s [B][N] and rho [B]."""
+    q = (dinv[:, None] * r).T
+    rho = np.sqrt(np.mean(q * q, axis=1))
+    s = np.where(rho[:, None] > 0, q / np.where(rho > 0, rho, 1.0)[:, None], 0.0)
+    return s, rho
+
+
+def apply(params, r, dinv, feat, d, n1, round_bf16=True):
+    """The correction delta = S(r) for a residual block r [N][B]; returns [N][B]."""
+    s, rho = normalise(r, dinv)
+    y, _ = forward(params, s, feat, d, n1, round_bf16)
+    return (y * rho[:, None]).T
+
+
+def loss_and_grad(params, e, r, A, dinv, feat, d, n1, round_bf16=True):
+    """Batch loss mean_j (e_j - delta_j)^T A (e_j - delta_j) / (e_j^T r_j) and its gradient.
+    e, r: [N][B] with r = A e."""
+    s, rho = normalise(r, dinv)
+    y, cache = forward(params, s, feat, d, n1, round_bf16)
+    delta = (y * rho[:, None]).T
+    E = e - delta
+    AE = A @ E
+    den = np.einsum("ij,ij->j", e, r)
+    B = e.shape[1]
+    L = np.einsum("ij,ij->j", E, AE) / den
+    gy = (-2.0 * AE * rho[None, :] / (B * den[None, :])).T
+    return float(L.mean()), L, backward(cache, gy, d, n1)
+
+
+def adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (step number t >= 1); returns new (params, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def fine_smoother(params, dinv, feat, d, n1, round_bf16=True):
+    """Callable x-correction S(r) for `mg.Hierarchy(..., fine_smoother=...)`."""
+    return lambda r: apply(params, r, dinv, feat, d, n1, round_bf16)

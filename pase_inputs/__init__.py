@@ -92,6 +92,35 @@ def standard_normals(seed: int, count: int) -> np.ndarray:
     return out[:count]
 
 
+def smoother_init(d: int, omega: float = 2.0 / 3.0, seed: int = 0, noise: float = 0.02) -> np.ndarray:
+    """Initial parameters of the learned smoother network (2 -> 16 -> 16 -> 16 -> 1
+    channels, 3^d taps, layout [W1, b1, ..., W4, b4], W in [c_out][c_in][tap] order):
+    weights that reproduce damped Jacobi plus seeded normal noise of standard deviation
+    `noise` on every parameter (normal k of standard_normals(seed, .) on parameter k).
+
+    Jacobi part: channel 0 of layer 1 passes +s and channel 1 passes -s through the
+    centre tap, layers 2 and 3 copy those two channels, layer 4 outputs
+    omega * (ch0 - ch1), so with ReLU the output is omega * s."""
+    T = 3 ** d
+    c = (T - 1) // 2
+    shapes = [(2, 16), (16, 16), (16, 16), (16, 1)]
+    parts = []
+    for li, (ci, co) in enumerate(shapes):
+        W = np.zeros((co, ci, T))
+        b = np.zeros(co)
+        if li == 0:
+            W[0, 0, c], W[1, 0, c] = 1.0, -1.0
+        elif li < 3:
+            W[0, 0, c], W[1, 1, c] = 1.0, 1.0
+        else:
+            W[0, 0, c], W[0, 1, c] = omega, -omega
+        parts += [W.reshape(-1), b]
+    p = np.concatenate(parts)
+    if noise:
+        p = p + noise * standard_normals(seed, p.size)
+    return p.astype(np.float32)
+
+
 def lognormal_kappa(d: int, n: int, seed: int, sigma: float = 1.0) -> np.ndarray:
     """Per-element coefficient kappa_e = exp(sigma * g_e), g_e ~ N(0,1) i.i.d.
 
