@@ -82,7 +82,13 @@ typedef struct {
                           once into a CUDA graph and replayed (needs a non-NULL stream)        */
   int autotune;        /* 1 (default): pase_reserve times the sparse kernel at a few block
                           sizes for every multigrid matrix and keeps the fastest            */
+  int smoother;        /* PASE_SMOOTHER_JACOBI (default) or PASE_SMOOTHER_LEARNED: the fine-
+                          level sweeps of the V-cycle use the learned network once
+                          pase_set_grid and parameters are given (Jacobi until then)      */
 } pase_options;
+
+#define PASE_SMOOTHER_JACOBI 0
+#define PASE_SMOOTHER_LEARNED 1
 
 /* Per-solve statistics (all times in milliseconds, device-event timed). */
 typedef struct {
@@ -239,6 +245,51 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
  * and their summed duration in ms since the last read, and starts a new count. */
 int pase_profile_kernel(pase_handle h, int kernel);
 int pase_profile_read(pase_handle h, int64_t* launches, double* total_ms);
+
+/* ---- learned fine-level smoother (the paper has no counterpart: a growth item) -------
+ * A 3^dim convolutional network, 2 -> 16 -> 16 -> 16 -> 1 channels with ReLU after the
+ * first three layers and zero padding, replaces each damped-Jacobi sweep on the fine
+ * level of the V-cycle by x <- x + S(b - A x).  Per column: q = D^-1 r, rho = RMS(q),
+ * S(r) = rho * net(q / rho, f), f = mean log kappa of the elements around each node.
+ * Parameters: one float vector [W1, b1, ..., W4, b4], W_l in [c_out][c_in][tap] order,
+ * tap t = sum_k (o_k + 1) 3^k for offsets o in {-1,0,1}^dim (x fastest); the network
+ * computes with them rounded to bfloat16 and accumulates in FP32.  Training minimises
+ * the squared energy norm of the error left after one step relative to the error before
+ * it, (e - S(Ae))^T A (e - S(Ae)) / e^T A e, with Adam on the FP32 master copy.
+ * Training uses the handle's workspace: do not interleave it with a solve. */
+
+/* The fine level is the interior-node grid of a uniform n^dim mesh ((n-1)^dim nodes,
+ * x fastest; must equal the size of A_h).  log_kappa: n^dim per-element values (host;
+ * NULL = all zero).  Call once, after pase_setup. */
+int pase_set_grid(pase_handle h, int dim, int n, const double* log_kappa);
+/* Number of network parameters P for dim = 2 (5089) or 3 (15169); 0 otherwise. */
+int pase_smoother_nparams(int dim);
+/* Optimiser state (host memory, 3P + 1 floats): [parameters | Adam first moments |
+ * Adam second moments | step count].  get = 1 reads it, get = 0 sets it (setting the
+ * parameters enables the learned smoother for PASE_SMOOTHER_LEARNED handles). */
+int pase_smoother_state(pase_handle h, float* state, int64_t count, int get);
+/* D = S(R) for a residual block R [N][m] (host or device; m a multiple of 8). */
+int pase_smoother_apply(pase_handle h, int m, const double* R, double* D);
+/* One training step on a batch of 8 columns: E = errors, R = A E ([N][8], host or
+ * device).  loss8 (host, 8) receives each column's loss, grad (host, P; may be NULL) the
+ * gradient of the batch loss (the mean over the columns) with respect to the rounded
+ * parameters; update = 1 also applies one Adam step (lr, beta1, beta2, eps). */
+int pase_smoother_step(pase_handle h, const double* E, const double* R, int update, float lr, float beta1,
+                       float beta2, float eps, double* loss8, double* grad);
+/* Training on samples the solver generates on this handle's problem: per step, eight
+ * random errors e0 (uniform, seeded), b = A e0, then k = (step/2) mod (max_cycles+1)
+ * damped-Jacobi V-cycles from zero, and for odd steps one more coarse-grid correction
+ * without smoothing (the state the post-smoother sees); the pair is the remaining error
+ * e and its residual r = A e.  losses (host, 3): mean loss of the first 10 steps, of the
+ * last 10 steps, and of the damped Jacobi correction on the last 10 steps' samples. */
+typedef struct {
+  int steps;
+  float lr, beta1, beta2, eps;
+  unsigned seed;
+  int max_cycles;
+} pase_train_options;
+void pase_default_train_options(pase_train_options* o);
+int pase_train_smoother(pase_handle h, const pase_train_options* o, double* losses);
 
 /* Number of library kernels launched by this handle so far. */
 int64_t pase_kernel_count(pase_handle h);

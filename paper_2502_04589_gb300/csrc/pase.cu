@@ -373,6 +373,43 @@ static int jacobi_sweeps(pase_ctx* h, const Level& L, int m, const T* b, T* x, T
 }
 
 template <typename T>
+static int vcycle(pase_ctx* h, LevelBufs<T>& B, int l, int m, bool x_zero);
+
+// Fine level of the V-cycle with the learned smoother: each of the nu1 pre- and nu2
+// post-smoothing sweeps is x <- x + S(b - A x) (the first from zero is x = S(b)).
+template <typename T>
+static int vcycle_fine_learned(pase_ctx* h, LevelBufs<T>& B, int m, bool x_zero) {
+  const Level& L = h->lv[0];
+  T* b = B.b[0];
+  T* x = B.x[0];
+  T* r = B.t1[0];
+  const T* dinv = dinv_of<T>(L);
+  for (int s = 0; s < h->opt.nu1; ++s) {
+    if (x_zero && s == 0) {
+      PASE_TRY(sm_apply<T>(h, m, b, m, dinv, x, m, false));
+      continue;
+    }
+    PASE_TRY(launch_csr<T>(h, CSR_RESID, m, L.A, aval<T>(L.A), nullptr, x, nullptr, b, nullptr, nullptr, 0.0, r,
+                           nullptr, nullptr, nullptr));
+    PASE_TRY(sm_apply<T>(h, m, r, m, dinv, x, m, true));
+  }
+  if (x_zero && h->opt.nu1 == 0) PASE_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * L.A.nrows * m, h->stream));
+  PASE_TRY(launch_csr<T>(h, CSR_RESID, m, L.A, aval<T>(L.A), nullptr, x, nullptr, b, nullptr, nullptr, 0.0, B.t2[0],
+                         nullptr, nullptr, nullptr));
+  PASE_TRY(launch_csr<T>(h, CSR_MV, m, L.PT, aval<T>(L.PT), nullptr, B.t2[0], nullptr, nullptr, nullptr, nullptr, 0.0,
+                         B.b[1], nullptr, nullptr, nullptr));
+  PASE_TRY(vcycle<T>(h, B, 1, m, true));
+  PASE_TRY(launch_csr<T>(h, CSR_ADD, m, L.P, aval<T>(L.P), nullptr, B.x[1], nullptr, x, nullptr, nullptr, 0.0, x,
+                         nullptr, nullptr, nullptr));
+  for (int s = 0; s < h->opt.nu2; ++s) {
+    PASE_TRY(launch_csr<T>(h, CSR_RESID, m, L.A, aval<T>(L.A), nullptr, x, nullptr, b, nullptr, nullptr, 0.0, r,
+                           nullptr, nullptr, nullptr));
+    PASE_TRY(sm_apply<T>(h, m, r, m, dinv, x, m, true));
+  }
+  return PASE_OK;
+}
+
+template <typename T>
 static int vcycle(pase_ctx* h, LevelBufs<T>& B, int l, int m, bool x_zero) {
   const int Lc = h->L - 1;
   T* b = B.b[l];
@@ -380,6 +417,7 @@ static int vcycle(pase_ctx* h, LevelBufs<T>& B, int l, int m, bool x_zero) {
   if (l == Lc) {
     return dense_mm<T>(h, h->ncoarsest, m, cinv_of<T>(h), b, x);
   }
+  if (l == 0 && sm_active(h)) return vcycle_fine_learned<T>(h, B, m, x_zero);
   const Level& L = h->lv[l];
   T* cur = nullptr;
   PASE_TRY(jacobi_sweeps<T>(h, L, m, b, x, B.t1[l], h->opt.nu1, x_zero, &cur));
@@ -846,6 +884,7 @@ void pase_default_options(pase_options* o) {
   o->verbose = 0;
   o->use_graphs = 1;
   o->autotune = 1;
+  o->smoother = PASE_SMOOTHER_JACOBI;
 }
 
 const char* pase_status_string(int code) {
@@ -878,6 +917,7 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
   const pase_options& o = h->opt;
   if ((o.precision != PASE_PREC_FP64 && o.precision != PASE_PREC_MIXED) || o.inner_steps < 1 || o.nu1 < 0 ||
       o.linear_solver < PASE_SOLVER_VCYCLE || o.linear_solver > PASE_SOLVER_MGCG ||
+      (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
       o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||
       !(o.aug_tol > 0.0)) {
     delete h;
@@ -899,6 +939,7 @@ int pase_destroy(pase_handle h) {
   else cudaDeviceSynchronize();
   if (h->ls_graph) cudaGraphExecDestroy(h->ls_graph);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  sm_free(h);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_small) cudaFreeHost(h->w.h_small);
   if (h->w.h_status) cudaFreeHost(h->w.h_status);
@@ -1316,6 +1357,131 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_nconv = 0;
   if (stp) *stp = st;
   return rc;
+}
+
+// ------------------------------------------------------------------ learned smoother ABI
+static void invalidate_graph(pase_ctx* h) {
+  if (h->ls_graph) cudaGraphExecDestroy(h->ls_graph);
+  h->ls_graph = nullptr;
+  h->ls_graph_U = nullptr;
+  h->ls_graph_W = nullptr;
+  h->ls_last_U = nullptr;
+  h->ls_last_W = nullptr;
+}
+
+int pase_set_grid(pase_handle h, int dim, int n, const double* log_kappa) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (!h->ready) return fail(PASE_ERR_STATE, "pase_set_grid: pase_setup has not completed");
+  return sm_set_grid(h, dim, n, log_kappa);
+}
+
+int pase_smoother_nparams(int dim) { return smoother_nparams(dim); }
+
+int pase_smoother_state(pase_handle h, float* state, int64_t count, int get) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  PASE_TRY(sm_state(h, state, count, get != 0));
+  if (!get) invalidate_graph(h);  // a captured step (a) may hold the Jacobi sweeps
+  return PASE_OK;
+}
+
+static int ensure_workspace(pase_ctx* h) { return h->w.m == 0 ? reserve(h, 8) : PASE_OK; }
+
+int pase_smoother_apply(pase_handle h, int m, const double* R, double* D) {
+  PASE_TRY(check_m(h, m));
+  if (!R || !D) return fail(PASE_ERR_INVALID_ARG, "pase_smoother_apply: null argument");
+  if (!h->sm || !h->sm->has_params) return fail(PASE_ERR_STATE, "pase_smoother_apply: no grid or parameters");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m * sizeof(double);
+  const void* dR;
+  void* dD;
+  PASE_TRY(st.in(R, nm, &dR));
+  PASE_TRY(st.out(D, nm, &dD));
+  PASE_TRY(sm_apply<double>(h, m, (const double*)dR, m, h->lv[0].dinv, (double*)dD, m, false));
+  return st.finish();
+}
+
+int pase_smoother_step(pase_handle h, const double* E, const double* R, int update, float lr, float beta1,
+                       float beta2, float eps, double* loss8, double* grad) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (!E || !R || !loss8) return fail(PASE_ERR_INVALID_ARG, "pase_smoother_step: null argument");
+  if (!h->sm || !h->sm->has_params) return fail(PASE_ERR_STATE, "pase_smoother_step: no grid or parameters");
+  PASE_TRY(ensure_workspace(h));
+  Stage st(h);
+  const size_t nb = (size_t)h->N * 8 * sizeof(double);
+  const void *dE, *dR;
+  PASE_TRY(st.in(E, nb, &dE));
+  PASE_TRY(st.in(R, nb, &dR));
+  PASE_TRY(sm_step(h, (const double*)dE, (const double*)dR, update != 0, lr, beta1, beta2, eps, loss8));
+  if (grad) PASE_TRY(sm_grad_to_host(h, grad));
+  if (update) invalidate_graph(h);
+  return st.finish();
+}
+
+void pase_default_train_options(pase_train_options* o) {
+  if (!o) return;
+  o->steps = 500;
+  o->lr = 1e-3f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->seed = 0;
+  o->max_cycles = 2;
+}
+
+int pase_train_smoother(pase_handle h, const pase_train_options* o, double* losses) {
+  if (!h || !o || !losses) return fail(PASE_ERR_INVALID_ARG, "pase_train_smoother: null argument");
+  if (o->steps < 1 || o->max_cycles < 0 || !(o->lr > 0.f))
+    return fail(PASE_ERR_INVALID_ARG, "pase_train_smoother: bad options");
+  if (!h->sm || !h->sm->has_params) return fail(PASE_ERR_STATE, "pase_train_smoother: no grid or parameters");
+  PASE_TRY(ensure_workspace(h));
+  Smoother* s = h->sm;
+  const int B = 8;
+  const int64_t N = h->N;
+  const Level& L0 = h->lv[0];
+  LevelBufs<double> VB = fp64_bufs(h);
+  struct Suspend {
+    pase_ctx* h;
+    ~Suspend() { h->sm_suspend = false; }
+  } guard{h};
+  h->sm_suspend = true;  // samples come from the Jacobi multigrid
+  invalidate_graph(h);
+  const int window = std::min(10, o->steps);
+  double first = 0.0, last = 0.0, jac = 0.0, l8[8], j8[8];
+  for (int step = 0; step < o->steps; ++step) {
+    const unsigned seed = o->seed * 2654435761u + (unsigned)step + 1u;
+    PASE_TRY(launch_hash_fill(h, N, B, B, seed, s->e));
+    PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.A, L0.A.val, nullptr, s->e, nullptr, nullptr, nullptr, nullptr, 0.0,
+                                VB.b[0], nullptr, nullptr, nullptr));
+    PASE_CUDA(cudaMemsetAsync(VB.x[0], 0, sizeof(double) * N * B, h->stream));
+    const int k = (step / 2) % (o->max_cycles + 1);
+    for (int c = 0; c < k; ++c) PASE_TRY(vcycle<double>(h, VB, 0, B, c == 0));
+    if ((step & 1) && h->L > 1) {  // coarse-grid correction without smoothing
+      PASE_TRY(launch_csr<double>(h, CSR_RESID, B, L0.A, L0.A.val, nullptr, VB.x[0], nullptr, VB.b[0], nullptr,
+                                  nullptr, 0.0, VB.t2[0], nullptr, nullptr, nullptr));
+      PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.PT, L0.PT.val, nullptr, VB.t2[0], nullptr, nullptr, nullptr,
+                                  nullptr, 0.0, VB.b[1], nullptr, nullptr, nullptr));
+      PASE_TRY(vcycle<double>(h, VB, 1, B, true));
+      PASE_TRY(launch_csr<double>(h, CSR_ADD, B, L0.P, L0.P.val, nullptr, VB.x[1], nullptr, VB.x[0], nullptr, nullptr,
+                                  0.0, VB.x[0], nullptr, nullptr, nullptr));
+    }
+    PASE_TRY(launch_axpy(h, N * B, -1.0, VB.x[0], s->e, s->e));  // e = e0 - x
+    PASE_TRY(launch_csr<double>(h, CSR_RESID, B, L0.A, L0.A.val, nullptr, VB.x[0], nullptr, VB.b[0], nullptr, nullptr,
+                                0.0, s->r, nullptr, nullptr, nullptr));
+    PASE_TRY(sm_step(h, s->e, s->r, true, o->lr, o->beta1, o->beta2, o->eps, l8));
+    double mean = 0.0;
+    for (int b = 0; b < B; ++b) mean += l8[b] / B;
+    if (!isfinite(mean)) return fail(PASE_ERR_NAN, "pase_train_smoother: loss is not finite");
+    if (step < window) first += mean / window;
+    if (step >= o->steps - window) {
+      last += mean / window;
+      PASE_TRY(sm_jacobi_loss(h, s->e, s->r, j8));
+      for (int b = 0; b < B; ++b) jac += j8[b] / (B * window);
+    }
+  }
+  losses[0] = first;
+  losses[1] = last;
+  losses[2] = jac;
+  return PASE_OK;
 }
 
 int pase_profile_kernel(pase_handle h, int kernel) {

@@ -112,6 +112,33 @@ struct Work {
   int* h_status = nullptr;
 };
 
+// learned fine-level smoother (smoother.cu)
+struct Smoother {
+  int dim = 0, n = 0, n1 = 0, T = 0, P = 0;
+  int64_t N = 0;
+  bool has_params = false;
+  int t = 0;  // Adam steps taken
+  float* feat = nullptr;                                                             // node feature [N]
+  float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *peff = nullptr;  // [P]
+  float* wt = nullptr;                                                               // transposed layer weights
+  double *grad = nullptr, *partial = nullptr, *colpart = nullptr;
+  float *act0 = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr, *ga = nullptr, *gb = nullptr;
+  double *E = nullptr, *AE = nullptr, *e = nullptr, *r = nullptr;  // [N][8] training blocks
+  double* sums = nullptr;                                          // small device scalars
+  double* h_sums = nullptr;                                        // pinned mirror
+};
+int smoother_nparams(int dim);
+bool sm_active(const pase_ctx* h);
+int sm_set_grid(pase_ctx* h, int dim, int n, const double* logk_host);
+int sm_state(pase_ctx* h, float* buf, int64_t count, bool get);
+template <typename T>
+int sm_apply(pase_ctx* h, int m, const T* R, int64_t ldr, const T* dinv, T* X, int64_t ldx, bool add);
+int sm_step(pase_ctx* h, const double* e, const double* r, bool update, float lr, float b1, float b2, float eps,
+            double* loss_cols);
+int sm_jacobi_loss(pase_ctx* h, const double* e, const double* r, double* loss_cols);
+int sm_grad_to_host(pase_ctx* h, double* grad_host);
+void sm_free(pase_ctx* h);
+
 }  // namespace pase
 
 struct pase_ctx {
@@ -147,6 +174,8 @@ struct pase_ctx {
   const double* ls_last_W = nullptr;
   bool graphs_ok = true;
   int tuned_m = 0;
+  pase::Smoother* sm = nullptr;  // learned smoother (pase_set_grid)
+  bool sm_suspend = false;       // Jacobi while the trainer generates samples
   double aug_tol_now = 0;    // current inner tolerance
   std::vector<void*> allocations;
 };

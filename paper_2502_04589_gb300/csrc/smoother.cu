@@ -1,0 +1,604 @@
+// Learned fine-level smoother: a 3^d convolutional network (2 -> 16 -> 16 -> 16 -> 1
+// channels, ReLU after the first three layers, zero padding) that replaces the damped
+// Jacobi sweeps of the V-cycle on the fine level, x <- x + S(b - A x).  The paper has no
+// learned smoother; this is a growth item of the GPU path, defined as follows.
+//
+// Grid: the fine level is the (n-1)^d interior-node grid of the uniform n^d Q1 mesh,
+// node i = sum_k c_k (n-1)^k (x fastest); node feature f_i = mean log kappa over the
+// 2^d elements around node i.  Per column j of a residual block r:
+//   q = D^-1 r_j, rho_j = sqrt(mean_i q_i^2), input channels (q / rho_j, f),
+//   S(r)_j = rho_j * net(q / rho_j, f)        (zero when rho_j = 0).
+// Convolution: y[b][co][i] = bias[co] + sum_ci sum_t W[co][ci][t] x[b][ci][i + o_t],
+// tap t = sum_k (o_k + 1) 3^k.  Parameters are one flat float vector
+// [W1, b1, W2, b2, W3, b3, W4, b4]; the network computes with the parameters rounded to
+// bfloat16 and accumulates in FP32; Adam updates the FP32 master copy.
+//
+// Training loss per column (e = the error the solver's iterate carries, r = A e):
+//   L = (e - S(r))^T A (e - S(r)) / (e^T r),
+// the squared energy norm of the error left after one smoothing step relative to the
+// error before it.  Its gradient with respect to the network output is
+// -2 rho (A (e - S(r))) / (B e^T r) for a batch of B columns.
+//
+// Layout: activations [B][C][N] FP32 (nodes fastest, so neighbouring threads read
+// neighbouring nodes); the residual / correction blocks stay node-major [N][m].
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "pase_internal.h"
+
+namespace pase {
+
+constexpr int kSmC = 16;       // hidden channels
+constexpr int kSmBatch = 8;    // columns per network pass
+constexpr int kSmWgBlocks = 608;
+
+template <int DIM>
+struct Taps {
+  static constexpr int T = DIM == 2 ? 9 : 27;
+};
+
+// interior-grid coordinates of node i
+template <int DIM>
+__device__ __forceinline__ void node_coords(int64_t i, int n1, int& cx, int& cy, int& cz) {
+  cx = (int)(i % n1);
+  const int64_t rest = i / n1;
+  if (DIM == 2) {
+    cy = (int)rest;
+    cz = 0;
+  } else {
+    cy = (int)(rest % n1);
+    cz = (int)(rest / n1);
+  }
+}
+
+// ------------------------------------------------------------------ features, scaling
+__global__ void k_sm_feat(int dim, int n, int n1, int64_t N, const double* __restrict__ logk, float* __restrict__ f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int cx = (int)(i % n1);
+    const int64_t rest = i / n1;
+    const int cy = (int)(rest % n1), cz = dim == 3 ? (int)(rest / n1) : 0;
+    double s = 0.0;
+    const int corners = 1 << dim;
+    for (int q = 0; q < corners; ++q) {
+      const int ex = cx + (q & 1), ey = cy + ((q >> 1) & 1), ez = dim == 3 ? cz + ((q >> 2) & 1) : 0;
+      s += logk ? logk[(int64_t)ex + (int64_t)n * (ey + (int64_t)n * ez)] : 0.0;
+    }
+    f[i] = (float)(s / corners);
+  }
+}
+
+// partial[blk][b] = sum over the block's rows of (dinv_i R[i][c0+b])^2, b < bc
+template <typename T>
+__global__ void __launch_bounds__(256) k_sm_colsq(int64_t N, int c0, int bc, const T* __restrict__ R, int64_t ldr,
+                                                  const T* __restrict__ dinv, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int b = threadIdx.x % kSmBatch, g = threadIdx.x / kSmBatch;  // 32 row groups x 8 columns
+  double s = 0.0;
+  if (b < bc)
+    for (int64_t i = (int64_t)blockIdx.x * 32 + g; i < N; i += (int64_t)gridDim.x * 32) {
+      const double q = (double)dinv[i] * (double)R[i * ldr + c0 + b];
+      s = fma(q, q, s);
+    }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < kSmBatch) {
+    double t = 0.0;
+    for (int q = 0; q < 32; ++q) t += red[q * kSmBatch + threadIdx.x];
+    partial[(int64_t)blockIdx.x * kSmBatch + threadIdx.x] = t;
+  }
+}
+
+// rho[b] = sqrt(sum[b] / N)
+__global__ void k_sm_rho(int bc, int64_t N, const double* __restrict__ sums, double* __restrict__ rho) {
+  const int b = threadIdx.x;
+  if (b < bc) rho[b] = sqrt(sums[b] / (double)N);
+}
+
+// act0[b][0][i] = dinv_i R[i][c0+b] / rho_b, act0[b][1][i] = f_i
+template <typename T>
+__global__ void k_sm_gather(int64_t N, int c0, int bc, const T* __restrict__ R, int64_t ldr, const T* __restrict__ dinv,
+                            const double* __restrict__ rho, const float* __restrict__ feat, float* __restrict__ act0) {
+  const int b = blockIdx.y;
+  const double rb = rho[b];
+  const double inv = rb > 0.0 ? 1.0 / rb : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    act0[((int64_t)b * 2) * N + i] = (float)((double)dinv[i] * (double)R[i * ldr + c0 + b] * inv);
+    act0[((int64_t)b * 2 + 1) * N + i] = feat[i];
+  }
+}
+
+// X[i][c0+b] (+)= rho_b y[b][i]
+template <typename T>
+__global__ void k_sm_scatter(int64_t N, int c0, int bc, const float* __restrict__ y, const double* __restrict__ rho,
+                             T* __restrict__ X, int64_t ldx, int add) {
+  const int b = blockIdx.y;
+  const double rb = rho[b];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = rb * (double)y[(int64_t)b * N + i];
+    T* p = X + i * ldx + c0 + b;
+    *p = add ? (T)((double)*p + d) : (T)d;
+  }
+}
+
+// ------------------------------------------------------------------ convolution
+// Z[b][co][i] = bias[co] + sum_ci sum_t W[co][ci][t] act(X[b][ci][i + o_t]) (zero outside
+// the grid); act = ReLU when relu_in, identity otherwise; the result is multiplied by
+// [mask[b][co][i] > 0] when mask is given (backward pass through a ReLU).
+template <int DIM, int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_sm_conv(int64_t N, int n1, const float* __restrict__ X, int relu_in,
+                                                 const float* __restrict__ W, const float* __restrict__ bias,
+                                                 const float* __restrict__ mask, float* __restrict__ Z) {
+  constexpr int T = Taps<DIM>::T;
+  __shared__ float ws[COUT * CIN * T + COUT];
+  for (int k = threadIdx.x; k < COUT * CIN * T; k += blockDim.x) ws[k] = W[k];
+  for (int k = threadIdx.x; k < COUT; k += blockDim.x) ws[COUT * CIN * T + k] = bias ? bias[k] : 0.f;
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int cx, cy, cz;
+  node_coords<DIM>(i, n1, cx, cy, cz);
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = ws[COUT * CIN * T + co];
+  const int64_t n1l = n1;
+  for (int ci = 0; ci < CIN; ++ci) {
+    const float* xb = X + ((int64_t)b * CIN + ci) * N;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+      const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+      float v = ok ? xb[i + ox + oy * n1l + oz * n1l * n1l] : 0.f;
+      if (relu_in) v = fmaxf(v, 0.f);
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(ws[(co * CIN + ci) * T + t], v, acc[co]);
+    }
+  }
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) {
+    float o = acc[co];
+    const int64_t idx = ((int64_t)b * COUT + co) * N + i;
+    if (mask && !(mask[idx] > 0.f)) o = 0.f;
+    Z[idx] = o;
+  }
+}
+
+// Weight gradient of one layer: partial[blk][(co*CIN + ci)*T + t] = sum over the block's
+// grid rows and all b of G[b][co][i] act(X[b][ci][i + o_t]); bias gradients after the
+// weights (partial[blk][COUT*CIN*T + co] = sum G[b][co][i]).  A grid row is a run of n1
+// nodes along x; the block's rows are [r0, r1).
+template <int DIM, int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_sm_wgrad(int B, int64_t N, int n1, const float* __restrict__ X, int relu_in,
+                                                  const float* __restrict__ G, int64_t rows_per_block,
+                                                  double* __restrict__ partial) {
+  constexpr int T = Taps<DIM>::T;
+  constexpr int W = COUT * CIN * T + COUT;
+  const int64_t nrows = N / n1;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < nrows ? r0 + rows_per_block : nrows;
+  const int64_t n1l = n1;
+  for (int it = threadIdx.x; it < COUT * T + COUT; it += blockDim.x) {
+    if (it < COUT * T) {
+      const int co = it / T, t = it % T;
+      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+      const int x0 = ox < 0 ? 1 : 0, x1 = ox > 0 ? n1 - 1 : n1;
+      float acc[CIN];
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) acc[ci] = 0.f;
+      for (int b = 0; b < B; ++b)
+        for (int64_t row = r0; row < r1; ++row) {
+          const int ry = DIM == 2 ? (int)row : (int)(row % n1);
+          const int rz = DIM == 2 ? 0 : (int)(row / n1);
+          if ((unsigned)(ry + oy) >= (unsigned)n1 || (DIM == 3 && (unsigned)(rz + oz) >= (unsigned)n1)) continue;
+          const float* g = G + ((int64_t)b * COUT + co) * N + row * n1l;
+          const int64_t shift = ox + oy * n1l + oz * n1l * n1l;
+          for (int x = x0; x < x1; ++x) {
+            const float gv = g[x];
+            const int64_t src = row * n1l + x + shift;
+#pragma unroll
+            for (int ci = 0; ci < CIN; ++ci) {
+              float v = X[((int64_t)b * CIN + ci) * N + src];
+              if (relu_in) v = fmaxf(v, 0.f);
+              acc[ci] = fmaf(gv, v, acc[ci]);
+            }
+          }
+        }
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) partial[(int64_t)blockIdx.x * W + (co * CIN + ci) * T + t] = (double)acc[ci];
+    } else {
+      const int co = it - COUT * T;
+      double s = 0.0;
+      for (int b = 0; b < B; ++b) {
+        const float* g = G + ((int64_t)b * COUT + co) * N;
+        float a = 0.f;
+        for (int64_t i = r0 * n1l; i < r1 * n1l; ++i) a += g[i];
+        s += a;
+      }
+      partial[(int64_t)blockIdx.x * W + COUT * CIN * T + co] = s;
+    }
+  }
+}
+
+// Wt[(co'*CIN' + ci')*T + t] = W[(ci'*CIN + co')*T + (T-1-t)] with CIN' = COUT, COUT' = CIN:
+// the weights of the transposed convolution (input gradient), taps mirrored.
+__global__ void k_sm_transpose(int cin, int cout, int T, const float* __restrict__ W, float* __restrict__ Wt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cin * cout * T) return;
+  const int t = k % T, rest = k / T;
+  const int ci2 = rest % cout, co2 = rest / cout;  // Wt index (co2 in [0,cin), ci2 in [0,cout))
+  Wt[k] = W[((int64_t)ci2 * cin + co2) * T + (T - 1 - t)];
+}
+
+// Adam on the FP32 master parameters; peff = the parameters rounded to bfloat16
+__global__ void k_sm_adam(int P, const double* __restrict__ grad, float* __restrict__ p, float* __restrict__ m,
+                          float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                          float* __restrict__ peff) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  const float g = (float)grad[k];
+  const float mk = b1 * m[k] + (1.f - b1) * g;
+  const float vk = b2 * v[k] + (1.f - b2) * g * g;
+  m[k] = mk;
+  v[k] = vk;
+  const float pk = p[k] - lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+  p[k] = pk;
+  peff[k] = __bfloat162float(__float2bfloat16_rn(pk));
+}
+
+__global__ void k_sm_round(int P, const float* __restrict__ p, float* __restrict__ peff) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < P) peff[k] = __bfloat162float(__float2bfloat16_rn(p[k]));
+}
+
+// E[i][b] = e[i][b] - rho_b y[b][i]   ([N][B] blocks, B = kSmBatch)
+__global__ void k_sm_err(int64_t N, int B, const double* __restrict__ e, const float* __restrict__ y,
+                         const double* __restrict__ rho, double* __restrict__ E) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N * B; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / B;
+    const int b = (int)(k % B);
+    E[k] = e[k] - rho[b] * (double)y[(int64_t)b * N + i];
+  }
+}
+
+// gy[b][i] = -2 rho_b AE[i][b] / (B den_b)
+__global__ void k_sm_outgrad(int64_t N, int B, const double* __restrict__ AE, const double* __restrict__ rho,
+                             const double* __restrict__ den, float* __restrict__ gy) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N * B; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / B;
+    const int b = (int)(k % B);
+    gy[(int64_t)b * N + i] = (float)(-2.0 * rho[b] * AE[k] / ((double)B * den[b]));
+  }
+}
+
+// E[i][b] = e[i][b] - omega dinv_i r[i][b]  (the damped Jacobi correction, for comparison)
+__global__ void k_sm_jacobi_err(int64_t N, int B, const double* __restrict__ e, const double* __restrict__ r,
+                                const double* __restrict__ dinv, double omega, double* __restrict__ E) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N * B; k += (int64_t)gridDim.x * blockDim.x)
+    E[k] = e[k] - omega * dinv[k / B] * r[k];
+}
+
+static inline int sm_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------------------ host side
+struct LayerOff {
+  int64_t W, b;
+  int cin, cout;
+};
+static void layer_offsets(int T, LayerOff L[4]) {
+  const int cin[4] = {2, kSmC, kSmC, kSmC}, cout[4] = {kSmC, kSmC, kSmC, 1};
+  int64_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    L[l].cin = cin[l];
+    L[l].cout = cout[l];
+    L[l].W = o;
+    o += (int64_t)cin[l] * cout[l] * T;
+    L[l].b = o;
+    o += cout[l];
+  }
+}
+
+int smoother_nparams(int dim) {
+  if (dim != 2 && dim != 3) return 0;
+  const int T = dim == 2 ? 9 : 27;
+  LayerOff L[4];
+  layer_offsets(T, L);
+  return (int)(L[3].b + 1);
+}
+
+bool sm_active(const pase_ctx* h) {
+  return h->opt.smoother == PASE_SMOOTHER_LEARNED && h->sm && h->sm->has_params && !h->sm_suspend &&
+         h->sm->N == h->N;
+}
+
+static int sm_check(pase_ctx* h) {
+  if (!h->sm || h->sm->dim == 0) return fail(PASE_ERR_STATE, "learned smoother: pase_set_grid has not been called");
+  return PASE_OK;
+}
+
+static int sync_stream(pase_ctx* h) {
+  if (h->stream) PASE_CUDA(cudaStreamSynchronize(h->stream));
+  else PASE_CUDA(cudaDeviceSynchronize());
+  return PASE_OK;
+}
+
+int sm_set_grid(pase_ctx* h, int dim, int n, const double* logk_host) {
+  if (dim != 2 && dim != 3) return fail(PASE_ERR_INVALID_ARG, "pase_set_grid: dim must be 2 or 3");
+  if (n < 3) return fail(PASE_ERR_INVALID_ARG, "pase_set_grid: n must be at least 3");
+  int64_t N = 1, ne = 1;
+  for (int k = 0; k < dim; ++k) {
+    N *= (n - 1);
+    ne *= n;
+  }
+  if (N != h->N) return fail(PASE_ERR_SHAPE_MISMATCH, "pase_set_grid: (n-1)^dim differs from the fine level size");
+  if (h->sm) return fail(PASE_ERR_STATE, "pase_set_grid: the grid is already set");
+  Smoother* s = new (std::nothrow) Smoother();
+  if (!s) return fail(PASE_ERR_OUT_OF_MEMORY, "pase_set_grid: host allocation");
+  h->sm = s;
+  s->dim = dim;
+  s->n = n;
+  s->n1 = n - 1;
+  s->N = N;
+  s->T = dim == 2 ? 9 : 27;
+  s->P = smoother_nparams(dim);
+  const int64_t NB = N * kSmBatch;
+  PASE_TRY(dev_alloc_t(h, &s->feat, N));
+  PASE_TRY(dev_alloc_t(h, &s->params, s->P));
+  PASE_TRY(dev_alloc_t(h, &s->adam_m, s->P));
+  PASE_TRY(dev_alloc_t(h, &s->adam_v, s->P));
+  PASE_TRY(dev_alloc_t(h, &s->peff, s->P));
+  PASE_TRY(dev_alloc_t(h, &s->wt, kSmC * kSmC * 27));
+  PASE_TRY(dev_alloc_t(h, &s->grad, s->P));
+  PASE_TRY(dev_alloc_t(h, &s->partial, (int64_t)kSmWgBlocks * (kSmC * kSmC * 27 + kSmC)));
+  PASE_TRY(dev_alloc_t(h, &s->colpart, (int64_t)kReduceBlocksHost * kSmBatch));
+  PASE_TRY(dev_alloc_t(h, &s->act0, 2 * NB));
+  PASE_TRY(dev_alloc_t(h, &s->z1, kSmC * NB));
+  PASE_TRY(dev_alloc_t(h, &s->z2, kSmC * NB));
+  PASE_TRY(dev_alloc_t(h, &s->z3, kSmC * NB));
+  PASE_TRY(dev_alloc_t(h, &s->y, NB));
+  PASE_TRY(dev_alloc_t(h, &s->ga, kSmC * NB));
+  PASE_TRY(dev_alloc_t(h, &s->gb, kSmC * NB));
+  PASE_TRY(dev_alloc_t(h, &s->E, NB));
+  PASE_TRY(dev_alloc_t(h, &s->AE, NB));
+  PASE_TRY(dev_alloc_t(h, &s->e, NB));
+  PASE_TRY(dev_alloc_t(h, &s->r, NB));
+  PASE_TRY(dev_alloc_t(h, &s->sums, 8 * kSmBatch));
+  PASE_CUDA(cudaMallocHost(&s->h_sums, sizeof(double) * 8 * kSmBatch));
+  double* dl = nullptr;
+  if (logk_host) {
+    PASE_TRY(dev_alloc_t(h, &dl, ne));
+    PASE_CUDA(cudaMemcpyAsync(dl, logk_host, sizeof(double) * ne, cudaMemcpyHostToDevice, h->stream));
+  }
+  k_sm_feat<<<sm_grid(N), 256, 0, h->stream>>>(dim, n, n - 1, N, dl, s->feat);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_CUDA(cudaMemsetAsync(s->params, 0, sizeof(float) * s->P, h->stream));
+  PASE_CUDA(cudaMemsetAsync(s->peff, 0, sizeof(float) * s->P, h->stream));
+  PASE_CUDA(cudaMemsetAsync(s->adam_m, 0, sizeof(float) * s->P, h->stream));
+  PASE_CUDA(cudaMemsetAsync(s->adam_v, 0, sizeof(float) * s->P, h->stream));
+  return sync_stream(h);
+}
+
+// state = [params | adam m | adam v | t] (3P + 1 floats, host memory)
+int sm_state(pase_ctx* h, float* buf, int64_t count, bool get) {
+  PASE_TRY(sm_check(h));
+  Smoother* s = h->sm;
+  if (count != 3 * (int64_t)s->P + 1) return fail(PASE_ERR_INVALID_ARG, "smoother state: count must be 3P + 1");
+  if (!buf) return fail(PASE_ERR_INVALID_ARG, "smoother state: null buffer");
+  if (get) {
+    PASE_CUDA(cudaMemcpyAsync(buf, s->params, sizeof(float) * s->P, cudaMemcpyDeviceToHost, h->stream));
+    PASE_CUDA(cudaMemcpyAsync(buf + s->P, s->adam_m, sizeof(float) * s->P, cudaMemcpyDeviceToHost, h->stream));
+    PASE_CUDA(cudaMemcpyAsync(buf + 2 * s->P, s->adam_v, sizeof(float) * s->P, cudaMemcpyDeviceToHost, h->stream));
+    PASE_TRY(sync_stream(h));
+    buf[3 * s->P] = (float)s->t;
+    return PASE_OK;
+  }
+  for (int64_t k = 0; k < count; ++k)
+    if (!isfinite(buf[k])) return fail(PASE_ERR_NAN, "smoother state: non-finite value");
+  if (buf[3 * s->P] < 0.f) return fail(PASE_ERR_INVALID_ARG, "smoother state: negative step count");
+  PASE_CUDA(cudaMemcpyAsync(s->params, buf, sizeof(float) * s->P, cudaMemcpyHostToDevice, h->stream));
+  PASE_CUDA(cudaMemcpyAsync(s->adam_m, buf + s->P, sizeof(float) * s->P, cudaMemcpyHostToDevice, h->stream));
+  PASE_CUDA(cudaMemcpyAsync(s->adam_v, buf + 2 * s->P, sizeof(float) * s->P, cudaMemcpyHostToDevice, h->stream));
+  k_sm_round<<<(s->P + 255) / 256, 256, 0, h->stream>>>(s->P, s->params, s->peff);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_TRY(sync_stream(h));
+  s->t = (int)buf[3 * s->P];
+  s->has_params = true;
+  return PASE_OK;
+}
+
+template <int DIM, int CIN, int COUT>
+static int conv_launch(pase_ctx* h, int B, const float* X, int relu_in, const float* W, const float* bias,
+                       const float* mask, float* Z) {
+  const Smoother* s = h->sm;
+  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)B);
+  k_sm_conv<DIM, CIN, COUT><<<grid, 256, 0, h->stream>>>(s->N, s->n1, X, relu_in, W, bias, mask, Z);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+template <int DIM>
+static int forward(pase_ctx* h, int B) {
+  Smoother* s = h->sm;
+  LayerOff L[4];
+  layer_offsets(s->T, L);
+  const float* p = s->peff;
+  PASE_TRY((conv_launch<DIM, 2, kSmC>(h, B, s->act0, 0, p + L[0].W, p + L[0].b, nullptr, s->z1)));
+  PASE_TRY((conv_launch<DIM, kSmC, kSmC>(h, B, s->z1, 1, p + L[1].W, p + L[1].b, nullptr, s->z2)));
+  PASE_TRY((conv_launch<DIM, kSmC, kSmC>(h, B, s->z2, 1, p + L[2].W, p + L[2].b, nullptr, s->z3)));
+  PASE_TRY((conv_launch<DIM, kSmC, 1>(h, B, s->z3, 1, p + L[3].W, p + L[3].b, nullptr, s->y)));
+  return PASE_OK;
+}
+
+template <typename T>
+static int normalise(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, const T* dinv) {
+  Smoother* s = h->sm;
+  int64_t g = (s->N + 31) / 32;
+  if (g > kReduceBlocksHost) g = kReduceBlocksHost;
+  k_sm_colsq<T><<<(unsigned)g, 256, 0, h->stream>>>(s->N, c0, bc, R, ldr, dinv, s->colpart);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_TRY(launch_reduce_partials(h, (int)g, kSmBatch, s->colpart, s->sums));
+  k_sm_rho<<<1, 32, 0, h->stream>>>(bc, s->N, s->sums, s->sums + kSmBatch);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  dim3 grid((unsigned)std::min<int64_t>((s->N + 255) / 256, 1024), (unsigned)bc);
+  k_sm_gather<T><<<grid, 256, 0, h->stream>>>(s->N, c0, bc, R, ldr, dinv, s->sums + kSmBatch, s->feat, s->act0);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// X (+)= S(R) column block by column block (kSmBatch columns per pass)
+template <typename T>
+int sm_apply(pase_ctx* h, int m, const T* R, int64_t ldr, const T* dinv, T* X, int64_t ldx, bool add) {
+  PASE_TRY(sm_check(h));
+  Smoother* s = h->sm;
+  for (int c0 = 0; c0 < m; c0 += kSmBatch) {
+    const int bc = std::min(kSmBatch, m - c0);
+    PASE_TRY(normalise<T>(h, c0, bc, R, ldr, dinv));
+    if (s->dim == 2) PASE_TRY(forward<2>(h, bc));
+    else PASE_TRY(forward<3>(h, bc));
+    dim3 grid((unsigned)std::min<int64_t>((s->N + 255) / 256, 1024), (unsigned)bc);
+    k_sm_scatter<T><<<grid, 256, 0, h->stream>>>(s->N, c0, bc, s->y, s->sums + kSmBatch, X, ldx, add ? 1 : 0);
+    h->launches++;
+    PASE_CUDA(cudaGetLastError());
+  }
+  return PASE_OK;
+}
+template int sm_apply<double>(pase_ctx*, int, const double*, int64_t, const double*, double*, int64_t, bool);
+template int sm_apply<float>(pase_ctx*, int, const float*, int64_t, const float*, float*, int64_t, bool);
+
+template <int DIM, int CIN, int COUT>
+static int wgrad_launch(pase_ctx* h, int B, const float* X, int relu_in, const float* G, double* grad_out) {
+  Smoother* s = h->sm;
+  const int64_t nrows = s->N / s->n1;
+  int nblk = (int)std::min<int64_t>(nrows, kSmWgBlocks);
+  const int64_t rpb = (nrows + nblk - 1) / nblk;
+  nblk = (int)((nrows + rpb - 1) / rpb);
+  k_sm_wgrad<DIM, CIN, COUT><<<nblk, 256, 0, h->stream>>>(B, s->N, s->n1, X, relu_in, G, rpb, s->partial);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  constexpr int T = Taps<DIM>::T;
+  return launch_reduce_partials(h, nblk, COUT * CIN * T + COUT, s->partial, grad_out);
+}
+
+static int transpose_launch(pase_ctx* h, int cin, int cout, const float* W) {
+  const int T = h->sm->T;
+  const int n = cin * cout * T;
+  k_sm_transpose<<<(n + 255) / 256, 256, 0, h->stream>>>(cin, cout, T, W, h->sm->wt);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+template <int DIM>
+static int backward(pase_ctx* h, int B) {
+  Smoother* s = h->sm;
+  LayerOff L[4];
+  layer_offsets(s->T, L);
+  const float* p = s->peff;
+  // layer 4: input relu(z3); the output gradient gy sits in the first N*B floats of gb
+  float* gy = s->gb;
+  PASE_TRY((wgrad_launch<DIM, kSmC, 1>(h, B, s->z3, 1, gy, s->grad + L[3].W)));
+  PASE_TRY(transpose_launch(h, kSmC, 1, p + L[3].W));
+  PASE_TRY((conv_launch<DIM, 1, kSmC>(h, B, gy, 0, s->wt, nullptr, s->z3, s->ga)));
+  // layer 3
+  PASE_TRY((wgrad_launch<DIM, kSmC, kSmC>(h, B, s->z2, 1, s->ga, s->grad + L[2].W)));
+  PASE_TRY(transpose_launch(h, kSmC, kSmC, p + L[2].W));
+  PASE_TRY((conv_launch<DIM, kSmC, kSmC>(h, B, s->ga, 0, s->wt, nullptr, s->z2, s->gb)));
+  // layer 2
+  PASE_TRY((wgrad_launch<DIM, kSmC, kSmC>(h, B, s->z1, 1, s->gb, s->grad + L[1].W)));
+  PASE_TRY(transpose_launch(h, kSmC, kSmC, p + L[1].W));
+  PASE_TRY((conv_launch<DIM, kSmC, kSmC>(h, B, s->gb, 0, s->wt, nullptr, s->z1, s->ga)));
+  // layer 1 (input: the normalised residual and the feature)
+  PASE_TRY((wgrad_launch<DIM, 2, kSmC>(h, B, s->act0, 0, s->ga, s->grad + L[0].W)));
+  return PASE_OK;
+}
+
+// One training step on a batch of kSmBatch columns: e, r [N][B] device (r = A e).
+// Writes the per-column losses (host, B doubles) and, if update, one Adam step.
+int sm_step(pase_ctx* h, const double* e, const double* r, bool update, float lr, float b1, float b2, float eps,
+            double* loss_cols) {
+  PASE_TRY(sm_check(h));
+  Smoother* s = h->sm;
+  const int B = kSmBatch;
+  const int64_t N = s->N;
+  const DevCSR& A = h->lv[0].A;
+  PASE_TRY(normalise<double>(h, 0, B, r, B, h->lv[0].dinv));
+  if (s->dim == 2) PASE_TRY(forward<2>(h, B));
+  else PASE_TRY(forward<3>(h, B));
+  double* rho = s->sums + kSmBatch;
+  double* num = s->sums + 2 * kSmBatch;
+  double* den = s->sums + 3 * kSmBatch;
+  k_sm_err<<<sm_grid(N * B), 256, 0, h->stream>>>(N, B, e, s->y, rho, s->E);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_TRY(launch_csr<double>(h, CSR_MV, B, A, A.val, nullptr, s->E, nullptr, nullptr, nullptr, nullptr, 0.0, s->AE,
+                              nullptr, nullptr, nullptr));
+  PASE_TRY(launch_coldot(h, N, B, s->E, s->AE, num));
+  PASE_TRY(launch_coldot(h, N, B, e, r, den));
+  k_sm_outgrad<<<sm_grid(N * B), 256, 0, h->stream>>>(N, B, s->AE, rho, den, s->gb);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  if (s->dim == 2) PASE_TRY(backward<2>(h, B));
+  else PASE_TRY(backward<3>(h, B));
+  if (update) {
+    s->t += 1;
+    const float bc1 = (float)(1.0 - pow((double)b1, (double)s->t));
+    const float bc2 = (float)(1.0 - pow((double)b2, (double)s->t));
+    k_sm_adam<<<(s->P + 255) / 256, 256, 0, h->stream>>>(s->P, s->grad, s->params, s->adam_m, s->adam_v, lr, b1, b2,
+                                                          eps, bc1, bc2, s->peff);
+    h->launches++;
+    PASE_CUDA(cudaGetLastError());
+  }
+  PASE_CUDA(cudaMemcpyAsync(s->h_sums, num, sizeof(double) * 2 * kSmBatch, cudaMemcpyDeviceToHost, h->stream));
+  PASE_TRY(sync_stream(h));
+  for (int b = 0; b < B; ++b) loss_cols[b] = s->h_sums[b] / s->h_sums[kSmBatch + b];
+  return PASE_OK;
+}
+
+// Energy loss of the damped Jacobi correction omega D^-1 r on the same kind of batch
+int sm_jacobi_loss(pase_ctx* h, const double* e, const double* r, double* loss_cols) {
+  PASE_TRY(sm_check(h));
+  Smoother* s = h->sm;
+  const int B = kSmBatch;
+  const int64_t N = s->N;
+  const DevCSR& A = h->lv[0].A;
+  double* num = s->sums + 2 * kSmBatch;
+  double* den = s->sums + 3 * kSmBatch;
+  k_sm_jacobi_err<<<sm_grid(N * B), 256, 0, h->stream>>>(N, B, e, r, h->lv[0].dinv, h->opt.omega, s->E);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_TRY(launch_csr<double>(h, CSR_MV, B, A, A.val, nullptr, s->E, nullptr, nullptr, nullptr, nullptr, 0.0, s->AE,
+                              nullptr, nullptr, nullptr));
+  PASE_TRY(launch_coldot(h, N, B, s->E, s->AE, num));
+  PASE_TRY(launch_coldot(h, N, B, e, r, den));
+  PASE_CUDA(cudaMemcpyAsync(s->h_sums, num, sizeof(double) * 2 * kSmBatch, cudaMemcpyDeviceToHost, h->stream));
+  PASE_TRY(sync_stream(h));
+  for (int b = 0; b < B; ++b) loss_cols[b] = s->h_sums[b] / s->h_sums[kSmBatch + b];
+  return PASE_OK;
+}
+
+int sm_grad_to_host(pase_ctx* h, double* grad_host) {
+  PASE_TRY(sm_check(h));
+  PASE_CUDA(cudaMemcpyAsync(grad_host, h->sm->grad, sizeof(double) * h->sm->P, cudaMemcpyDeviceToHost, h->stream));
+  return sync_stream(h);
+}
+
+void sm_free(pase_ctx* h) {
+  if (h->sm) {
+    if (h->sm->h_sums) cudaFreeHost(h->sm->h_sums);
+    delete h->sm;
+    h->sm = nullptr;
+  }
+}
+
+}  // namespace pase

@@ -19,6 +19,8 @@ PASE_PREC_MIXED = 1
 PASE_SOLVER_VCYCLE = 0
 PASE_SOLVER_CG = 1
 PASE_SOLVER_MGCG = 2
+PASE_SMOOTHER_JACOBI = 0
+PASE_SMOOTHER_LEARNED = 1
 
 
 class PaseCSR(ctypes.Structure):
@@ -33,7 +35,14 @@ class PaseOptions(ctypes.Structure):
                 ("omega", ctypes.c_double), ("coarse_level", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
-                ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
+
+
+class PaseTrainOptions(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint),
+                ("max_cycles", ctypes.c_int)]
 
 
 class PaseStats(ctypes.Structure):
@@ -61,7 +70,9 @@ EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve",
             "pase_solve_batched", "pase_profile_kernel", "pase_profile_read",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
             "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_residual_noalloc",
-            "pase_time_kernel",
+            "pase_time_kernel", "pase_set_grid", "pase_smoother_nparams", "pase_smoother_state",
+            "pase_smoother_apply", "pase_smoother_step", "pase_default_train_options",
+            "pase_train_smoother",
             "pase_kernel_count",
             "pase_destroy", "pase_status_string", "pase_last_error"]
 
@@ -97,6 +108,15 @@ def load_library(path=LIB_PATH):
     L.pase_time_kernel.argtypes = [vp, i32, i32, i32, ctypes.POINTER(dbl)]
     L.pase_profile_kernel.argtypes = [vp, i32]
     L.pase_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+    L.pase_set_grid.argtypes = [vp, i32, i32, vp]
+    L.pase_smoother_nparams.argtypes = [i32]
+    L.pase_smoother_state.argtypes = [vp, vp, i64, i32]
+    L.pase_smoother_apply.argtypes = [vp, i32, vp, vp]
+    flt = ctypes.c_float
+    L.pase_smoother_step.argtypes = [vp, vp, vp, i32, flt, flt, flt, flt, vp, vp]
+    L.pase_default_train_options.argtypes = [ctypes.POINTER(PaseTrainOptions)]
+    L.pase_default_train_options.restype = None
+    L.pase_train_smoother.argtypes = [vp, ctypes.POINTER(PaseTrainOptions), vp]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
     L.pase_destroy.argtypes = [vp]
@@ -108,7 +128,8 @@ def load_library(path=LIB_PATH):
                  "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
                  "pase_iterate", "pase_spmm_am", "pase_residual_noalloc", "pase_time_kernel",
-                 "pase_profile_kernel", "pase_profile_read",
+                 "pase_profile_kernel", "pase_profile_read", "pase_set_grid", "pase_smoother_nparams",
+                 "pase_smoother_state", "pase_smoother_apply", "pase_smoother_step", "pase_train_smoother",
                  "pase_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
@@ -283,6 +304,62 @@ def pase_profile_read(h):
     ms = ctypes.c_double()
     _check(load_library().pase_profile_read(h, ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def pase_set_grid(h, dim, n, log_kappa=None):
+    """Fine level = interior grid of the uniform n^dim mesh; log_kappa per element (or None)."""
+    lk = None if log_kappa is None else np.ascontiguousarray(log_kappa, dtype=np.float64)
+    return _check(load_library().pase_set_grid(h, dim, n, _ptr(lk)))
+
+
+def pase_smoother_nparams(dim):
+    return int(load_library().pase_smoother_nparams(dim))
+
+
+def pase_smoother_state(h, dim, state=None):
+    """state None: returns the state (params, m, v, t); else sets it from a tuple
+    (params[, m, v, t]) of float arrays (missing moments are zero)."""
+    P = pase_smoother_nparams(dim)
+    L = load_library()
+    if state is None:
+        buf = np.empty(3 * P + 1, dtype=np.float32)
+        _check(L.pase_smoother_state(h, buf.ctypes.data, buf.size, 1))
+        return buf[:P].copy(), buf[P:2 * P].copy(), buf[2 * P:3 * P].copy(), int(buf[3 * P])
+    params = np.asarray(state[0], dtype=np.float32)
+    m = np.asarray(state[1], dtype=np.float32) if len(state) > 1 else np.zeros(P, np.float32)
+    v = np.asarray(state[2], dtype=np.float32) if len(state) > 2 else np.zeros(P, np.float32)
+    t = float(state[3]) if len(state) > 3 else 0.0
+    buf = np.concatenate([params, m, v, np.array([t], np.float32)]).astype(np.float32)
+    return _check(L.pase_smoother_state(h, buf.ctypes.data, buf.size, 0))
+
+
+def pase_smoother_apply(h, m, R, D):
+    return _check(load_library().pase_smoother_apply(h, m, _ptr(R), _ptr(D)))
+
+
+def pase_smoother_step(h, E, R, update=False, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, want_grad=False, P=None):
+    """One training step on 8 columns; returns (loss8, grad or None)."""
+    loss = np.empty(8)
+    grad = np.empty(P) if want_grad else None
+    _check(load_library().pase_smoother_step(h, _ptr(E), _ptr(R), int(update), lr, beta1, beta2, eps,
+                                             loss.ctypes.data, None if grad is None else grad.ctypes.data))
+    return loss, grad
+
+
+def pase_default_train_options():
+    o = PaseTrainOptions()
+    load_library().pase_default_train_options(ctypes.byref(o))
+    return o
+
+
+def pase_train_smoother(h, opt=None, **kw):
+    """Returns (loss over the first 10 steps, over the last 10, damped Jacobi's on the last 10)."""
+    o = opt or pase_default_train_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    out = np.empty(3)
+    _check(load_library().pase_train_smoother(h, ctypes.byref(o), out.ctypes.data))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def pase_kernel_count(h):
