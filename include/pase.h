@@ -276,12 +276,17 @@ int pase_smoother_apply(pase_handle h, int m, const double* R, double* D);
  * parameters; update = 1 also applies one Adam step (lr, beta1, beta2, eps). */
 int pase_smoother_step(pase_handle h, const double* E, const double* R, int update, float lr, float beta1,
                        float beta2, float eps, double* loss8, double* grad);
-/* Training on samples the solver generates on this handle's problem: per step, eight
- * random errors e0 (uniform, seeded), b = A e0, then k = (step/2) mod (max_cycles+1)
- * damped-Jacobi V-cycles from zero, and for odd steps one more coarse-grid correction
- * without smoothing (the state the post-smoother sees); the pair is the remaining error
- * e and its residual r = A e.  losses (host, 3): mean loss of the first 10 steps, of the
- * last 10 steps, and of the damped Jacobi correction on the last 10 steps' samples. */
+/* Training on samples the solver generates on this handle's problem, on-policy: per
+ * step, eight random errors e0 (uniform, seeded), b = A e0, x = 0, then
+ * k = (step/4) mod (max_cycles+1) V-cycles with the network being trained, then by
+ * step mod 4: nothing more / one pre-smoothing sweep / all pre-sweeps and the coarse-grid
+ * correction / that and one post-sweep; the pair is the remaining error e = e0 - x and
+ * its residual r = A e.  Afterwards the energy-norm error factor of two V-cycles on fresh
+ * errors is measured with the network and with damped Jacobi; if the network is not
+ * better, the handle falls back to Jacobi (until new parameters are set).
+ * losses (host, 5): mean loss of the first 10 steps, of the last 10 steps, of the damped
+ * Jacobi correction on the last 10 steps' samples, and the two V-cycle factors
+ * (network, Jacobi). */
 typedef struct {
   int steps;
   float lr, beta1, beta2, eps;

@@ -1428,6 +1428,34 @@ void pase_default_train_options(pase_train_options* o) {
   o->max_cycles = 2;
 }
 
+// Energy-norm error factor ||e0 - x||_A / ||e0||_A (mean over 8 seeded random errors)
+// after two V-cycles from zero with the handle's current fine-level smoother.
+static int vcycle_energy_factor(pase_ctx* h, unsigned seed, double* factor) {
+  Smoother* s = h->sm;
+  const int B = 8;
+  const int64_t N = h->N;
+  const Level& L0 = h->lv[0];
+  LevelBufs<double> VB = fp64_bufs(h);
+  double* ws = s->sums + 4 * B;  // [2B]: sums e.Ae after and before
+  PASE_TRY(launch_hash_fill(h, N, B, B, seed, s->e));
+  PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.A, L0.A.val, nullptr, s->e, nullptr, nullptr, nullptr, nullptr, 0.0,
+                              VB.b[0], nullptr, nullptr, nullptr));
+  PASE_CUDA(cudaMemsetAsync(VB.x[0], 0, sizeof(double) * N * B, h->stream));
+  for (int c = 0; c < 2; ++c) PASE_TRY(vcycle<double>(h, VB, 0, B, c == 0));
+  PASE_TRY(launch_coldot(h, N, B, s->e, VB.b[0], ws + B));              // e0 . A e0
+  PASE_TRY(launch_axpy(h, N * B, -1.0, VB.x[0], s->e, s->e));          // E = e0 - x
+  PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.A, L0.A.val, nullptr, s->e, nullptr, nullptr, nullptr, nullptr, 0.0,
+                              s->r, nullptr, nullptr, nullptr));
+  PASE_TRY(launch_coldot(h, N, B, s->e, s->r, ws));                    // E . A E
+  PASE_CUDA(cudaMemcpyAsync(s->h_sums, ws, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, h->stream));
+  if (h->stream) PASE_CUDA(cudaStreamSynchronize(h->stream));
+  else PASE_CUDA(cudaDeviceSynchronize());
+  double f = 0.0;
+  for (int b = 0; b < B; ++b) f += sqrt(s->h_sums[b] / s->h_sums[B + b]) / B;
+  *factor = f;
+  return PASE_OK;
+}
+
 int pase_train_smoother(pase_handle h, const pase_train_options* o, double* losses) {
   if (!h || !o || !losses) return fail(PASE_ERR_INVALID_ARG, "pase_train_smoother: null argument");
   if (o->steps < 1 || o->max_cycles < 0 || !(o->lr > 0.f))
@@ -1438,13 +1466,31 @@ int pase_train_smoother(pase_handle h, const pase_train_options* o, double* loss
   const int B = 8;
   const int64_t N = h->N;
   const Level& L0 = h->lv[0];
+  const double* dinv = L0.dinv;
   LevelBufs<double> VB = fp64_bufs(h);
-  struct Suspend {
+  // The samples come from the V-cycle that uses the network being trained (on-policy),
+  // so the states it meets after its own sweeps are in the training set.
+  struct Restore {
     pase_ctx* h;
-    ~Suspend() { h->sm_suspend = false; }
-  } guard{h};
-  h->sm_suspend = true;  // samples come from the Jacobi multigrid
+    int smoother;
+    ~Restore() {
+      h->opt.smoother = smoother;
+      h->sm_suspend = false;
+    }
+  } guard{h, h->opt.smoother};
+  h->opt.smoother = PASE_SMOOTHER_LEARNED;
+  h->sm_suspend = false;
+  s->rejected = false;
   invalidate_graph(h);
+  auto residual = [&](double* out) {
+    return launch_csr<double>(h, CSR_RESID, B, L0.A, L0.A.val, nullptr, VB.x[0], nullptr, VB.b[0], nullptr, nullptr,
+                              0.0, out, nullptr, nullptr, nullptr);
+  };
+  auto sweep = [&](bool from_zero) -> int {  // x <- x + S(b - A x)  (x = S(b) from zero)
+    if (from_zero) return sm_apply<double>(h, B, VB.b[0], B, dinv, VB.x[0], B, false);
+    PASE_TRY(residual(VB.t1[0]));
+    return sm_apply<double>(h, B, VB.t1[0], B, dinv, VB.x[0], B, true);
+  };
   const int window = std::min(10, o->steps);
   double first = 0.0, last = 0.0, jac = 0.0, l8[8], j8[8];
   for (int step = 0; step < o->steps; ++step) {
@@ -1453,20 +1499,26 @@ int pase_train_smoother(pase_handle h, const pase_train_options* o, double* loss
     PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.A, L0.A.val, nullptr, s->e, nullptr, nullptr, nullptr, nullptr, 0.0,
                                 VB.b[0], nullptr, nullptr, nullptr));
     PASE_CUDA(cudaMemsetAsync(VB.x[0], 0, sizeof(double) * N * B, h->stream));
-    const int k = (step / 2) % (o->max_cycles + 1);
+    // state: k full V-cycles, then 0: nothing more, 1: one pre-smoothing sweep,
+    // 2: all pre-sweeps and the coarse-grid correction, 3: that and one post-sweep
+    const int type = step % 4;
+    const int k = (step / 4) % (o->max_cycles + 1);
     for (int c = 0; c < k; ++c) PASE_TRY(vcycle<double>(h, VB, 0, B, c == 0));
-    if ((step & 1) && h->L > 1) {  // coarse-grid correction without smoothing
-      PASE_TRY(launch_csr<double>(h, CSR_RESID, B, L0.A, L0.A.val, nullptr, VB.x[0], nullptr, VB.b[0], nullptr,
-                                  nullptr, 0.0, VB.t2[0], nullptr, nullptr, nullptr));
-      PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.PT, L0.PT.val, nullptr, VB.t2[0], nullptr, nullptr, nullptr,
-                                  nullptr, 0.0, VB.b[1], nullptr, nullptr, nullptr));
-      PASE_TRY(vcycle<double>(h, VB, 1, B, true));
-      PASE_TRY(launch_csr<double>(h, CSR_ADD, B, L0.P, L0.P.val, nullptr, VB.x[1], nullptr, VB.x[0], nullptr, nullptr,
-                                  0.0, VB.x[0], nullptr, nullptr, nullptr));
+    if (type >= 1) PASE_TRY(sweep(k == 0));
+    if (type >= 2) {
+      for (int q = 1; q < h->opt.nu1; ++q) PASE_TRY(sweep(false));
+      if (h->L > 1) {
+        PASE_TRY(residual(VB.t2[0]));
+        PASE_TRY(launch_csr<double>(h, CSR_MV, B, L0.PT, L0.PT.val, nullptr, VB.t2[0], nullptr, nullptr, nullptr,
+                                    nullptr, 0.0, VB.b[1], nullptr, nullptr, nullptr));
+        PASE_TRY(vcycle<double>(h, VB, 1, B, true));
+        PASE_TRY(launch_csr<double>(h, CSR_ADD, B, L0.P, L0.P.val, nullptr, VB.x[1], nullptr, VB.x[0], nullptr,
+                                    nullptr, 0.0, VB.x[0], nullptr, nullptr, nullptr));
+      }
     }
+    if (type == 3) PASE_TRY(sweep(false));
     PASE_TRY(launch_axpy(h, N * B, -1.0, VB.x[0], s->e, s->e));  // e = e0 - x
-    PASE_TRY(launch_csr<double>(h, CSR_RESID, B, L0.A, L0.A.val, nullptr, VB.x[0], nullptr, VB.b[0], nullptr, nullptr,
-                                0.0, s->r, nullptr, nullptr, nullptr));
+    PASE_TRY(residual(s->r));
     PASE_TRY(sm_step(h, s->e, s->r, true, o->lr, o->beta1, o->beta2, o->eps, l8));
     double mean = 0.0;
     for (int b = 0; b < B; ++b) mean += l8[b] / B;
@@ -1478,9 +1530,20 @@ int pase_train_smoother(pase_handle h, const pase_train_options* o, double* loss
       for (int b = 0; b < B; ++b) jac += j8[b] / (B * window);
     }
   }
+  // validation on fresh errors: the learned V-cycle must beat the Jacobi V-cycle, else
+  // the handle falls back to Jacobi
+  double f_learned = 0.0, f_jacobi = 0.0;
+  const unsigned vseed = o->seed * 2654435761u + 0x5eed5u;
+  PASE_TRY(vcycle_energy_factor(h, vseed, &f_learned));
+  h->sm_suspend = true;
+  PASE_TRY(vcycle_energy_factor(h, vseed, &f_jacobi));
+  h->sm_suspend = false;
+  s->rejected = !(f_learned < f_jacobi);
   losses[0] = first;
   losses[1] = last;
   losses[2] = jac;
+  losses[3] = f_learned;
+  losses[4] = f_jacobi;
   return PASE_OK;
 }
 

@@ -117,7 +117,8 @@ struct Smoother {
   int dim = 0, n = 0, n1 = 0, T = 0, P = 0;
   int64_t N = 0;
   bool has_params = false;
-  int t = 0;  // Adam steps taken
+  bool rejected = false;  // validation after training found it no better than Jacobi
+  int t = 0;              // Adam steps taken
   float* feat = nullptr;                                                             // node feature [N]
   float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *peff = nullptr;  // [P]
   float* wt = nullptr;                                                               // transposed layer weights

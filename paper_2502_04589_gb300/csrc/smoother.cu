@@ -312,8 +312,8 @@ int smoother_nparams(int dim) {
 }
 
 bool sm_active(const pase_ctx* h) {
-  return h->opt.smoother == PASE_SMOOTHER_LEARNED && h->sm && h->sm->has_params && !h->sm_suspend &&
-         h->sm->N == h->N;
+  return h->opt.smoother == PASE_SMOOTHER_LEARNED && h->sm && h->sm->has_params && !h->sm->rejected &&
+         !h->sm_suspend && h->sm->N == h->N;
 }
 
 static int sm_check(pase_ctx* h) {
@@ -410,6 +410,7 @@ int sm_state(pase_ctx* h, float* buf, int64_t count, bool get) {
   PASE_TRY(sync_stream(h));
   s->t = (int)buf[3 * s->P];
   s->has_params = true;
+  s->rejected = false;
   return PASE_OK;
 }
 

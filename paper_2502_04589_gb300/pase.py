@@ -353,13 +353,17 @@ def pase_default_train_options():
 
 
 def pase_train_smoother(h, opt=None, **kw):
-    """Returns (loss over the first 10 steps, over the last 10, damped Jacobi's on the last 10)."""
+    """Returns a dict: loss over the first 10 steps, over the last 10, damped Jacobi's on
+    the last 10 steps' samples, and the two-V-cycle energy error factors with the network
+    and with Jacobi (the handle keeps Jacobi unless the network's is smaller)."""
     o = opt or pase_default_train_options()
     for k, v in kw.items():
         setattr(o, k, v)
-    out = np.empty(3)
+    out = np.empty(5)
     _check(load_library().pase_train_smoother(h, ctypes.byref(o), out.ctypes.data))
-    return float(out[0]), float(out[1]), float(out[2])
+    return dict(loss_first=float(out[0]), loss_last=float(out[1]), loss_jacobi=float(out[2]),
+                vcycle_factor=float(out[3]), vcycle_factor_jacobi=float(out[4]),
+                accepted=bool(out[3] < out[4]))
 
 
 def pase_kernel_count(h):

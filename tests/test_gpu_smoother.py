@@ -115,7 +115,7 @@ def test_learned_vcycle_matches_oracle():
         P.pase_destroy(h)
 
 
-def _vcycle_energy_factor(h, pb, m=8, seed=11):
+def _vcycle_energy_factor(h, pb, m=16, seed=11):
     """||e||_A / ||e0||_A after the handle's step (a) (two V-cycles) on A e = A e0 from 0."""
     e0 = pin.start_vectors(seed, pb.N, m)
     U = np.zeros_like(e0)
@@ -128,27 +128,33 @@ def _vcycle_energy_factor(h, pb, m=8, seed=11):
 
 def test_training_gains_over_jacobi():
     """Trained on one lognormal field and evaluated on a held-out one: the energy loss on
-    the training samples ends below damped Jacobi's, the two-V-cycle error factor on the
-    held-out field is smaller than with Jacobi, and the eigen-solve with the learned
-    smoother meets the same gates."""
+    the last training samples is below damped Jacobi's on the same samples, the library's
+    own validation accepts
+    the network, the two-V-cycle error factor on the held-out field is smaller than with
+    Jacobi, and the eigen-solve with the learned smoother meets the same gates."""
     d, n = 2, 64
     pb, lk = _problem(d, n, 21, sigma=1.0)
     params = pin.smoother_init(d, seed=1, noise=0.02)
     h = _handle(pb, d, lk, params, smoother=P.PASE_SMOOTHER_LEARNED)
     try:
-        first, last, jac = P.pase_train_smoother(h, steps=400, lr=2e-3, seed=3)
+        out = P.pase_train_smoother(h, steps=600, lr=1e-3, seed=3)
         trained = P.pase_smoother_state(h, d)
     finally:
         P.pase_destroy(h)
-    print(f"\ntraining loss: first {first:.4f}, last {last:.4f}, damped Jacobi {jac:.4f}")
-    assert last < first and last < jac, (first, last, jac)
+    print("\ntraining:", out)
+    # the samples come from the network's own V-cycle, so the loss of later steps is taken
+    # on harder states than the first; the comparison that holds is with Jacobi on the
+    # same samples
+    assert out["loss_last"] < out["loss_jacobi"], out
+    assert out["accepted"], out
     pbt, lkt = _problem(d, n, 77, sigma=1.0)
     hj = _handle(pbt, d, lkt, None)
     hl = _handle(pbt, d, lkt, trained[0], smoother=P.PASE_SMOOTHER_LEARNED)
     try:
         fj = _vcycle_energy_factor(hj, pbt)
         fl = _vcycle_energy_factor(hl, pbt)
-        print(f"two V-cycles, energy error factor: learned {np.mean(fl):.4f}, Jacobi {np.mean(fj):.4f}")
+        print(f"held-out field, two V-cycles, energy error factor: learned {np.mean(fl):.4f}, "
+              f"Jacobi {np.mean(fj):.4f}")
         assert np.mean(fl) < np.mean(fj), (fl, fj)
         nev, m = 6, 16
         U0 = pin.start_vectors(0, pbt.N, m)
