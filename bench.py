@@ -205,6 +205,87 @@ def run_batched(args, P, pin, torch, np, barrier):
             P.pase_destroy(h)
 
 
+def run_learned(args, P, pin, torch, np):
+    """Configuration 4, 2D: one smoother network trained on the solver's own samples from
+    64 seeded lognormal fields (sigma 1, seeds 1000-1063, 256^2 meshes, 20 steps of 8
+    pairs each: 10,240 pairs), evaluated on 16 held-out fields (seeds 2000-2015) by the
+    two-V-cycle energy error factor against damped Jacobi, and by a full FP64 solve of
+    the 1024^2 held-out field 2000 (coarse 128^2, nev 32, tol 1e-8) with each smoother."""
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def make(n, seed, params=None, smoother=0, m=None):
+        pb = pin.build_problem(2, n, n // 8, kappa_seed=seed, sigma=1.0, mg_min=4)
+        opt = P.pase_default_options()
+        opt.coarse_level = pb.coarse_level
+        opt.smoother = smoother
+        h = P.pase_create(opt, stream)
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        P.pase_set_grid(h, 2, n, np.log(pb.kappa))
+        if m:
+            P.pase_reserve(h, m)
+        if params is not None:
+            P.pase_smoother_state(h, 2, params)
+        return pb, h
+
+    t0 = time.perf_counter()
+    state = (pin.smoother_init(2, seed=1, noise=0.02),)
+    accepted = 0
+    for f in range(64):
+        pb, h = make(256, 1000 + f, state)
+        out = P.pase_train_smoother(h, steps=20, lr=1e-3, seed=f)
+        accepted += int(out["accepted"])
+        state = P.pase_smoother_state(h, 2)
+        P.pase_destroy(h)
+    train_s = time.perf_counter() - t0
+    params = (state[0],)
+
+    def factor(pb, h, m=8):
+        e0 = pin.start_vectors(11, pb.N, m)
+        W = np.empty_like(e0)
+        P.pase_linear_solve(h, m, np.zeros_like(e0), np.ones(m), np.ascontiguousarray(pb.A @ e0), W)
+        E = e0 - W
+        return float(np.mean(np.sqrt(np.einsum("ij,ij->j", E, pb.A @ E) / np.einsum("ij,ij->j", e0, pb.A @ e0))))
+
+    fl, fj = [], []
+    for f in range(16):
+        pb, hl = make(256, 2000 + f, params, smoother=P.PASE_SMOOTHER_LEARNED, m=8)
+        fl.append(factor(pb, hl))
+        P.pase_destroy(hl)
+        pb, hj = make(256, 2000 + f, None, m=8)
+        fj.append(factor(pb, hj))
+        P.pase_destroy(hj)
+    solves = {}
+    nev = 32
+    m = pin.guard_columns(nev)
+    lam_ref = None
+    for name, sm_ in (("jacobi", P.PASE_SMOOTHER_JACOBI), ("learned", P.PASE_SMOOTHER_LEARNED)):
+        pb, h = make(1024, 2000, params if sm_ else None, smoother=sm_, m=m)
+        U0 = torch.from_numpy(pin.start_vectors(SEED, pb.N, m)).cuda()
+        U = torch.empty_like(U0)
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rc, st = P.pase_solve(h, nev, 1e-8, m, U0, lam, U)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t1
+        lamh = lam[:nev].cpu().numpy()
+        solves[name] = {"status": rc, "iterations": st["iterations"], "seconds": sec,
+                        "ms_per_iteration": 1e3 * sec / max(1, st["iterations"]),
+                        "phase_ms": st["phase_ms"], "max_relres": st["max_residual"]}
+        if lam_ref is None:
+            lam_ref = lamh
+        else:
+            solves[name]["max_rel_eig_diff_vs_jacobi"] = float(np.max(np.abs(lamh - lam_ref) / lam_ref))
+        P.pase_destroy(h)
+    return {"workload": "2D Q1 lognormal kappa (sigma 1): train 64 fields at 256^2 (10,240 pairs), "
+                        "evaluate 16 held-out fields at 256^2 and a full solve at 1024^2, nev 32",
+            "train_seconds": train_s, "fields_accepted_by_validation": accepted,
+            "vcycle2_energy_factor_learned": float(np.mean(fl)), "vcycle2_energy_factor_jacobi": float(np.mean(fj)),
+            "heldout_fields_better": int(sum(a < b for a, b in zip(fl, fj))),
+            "solve_1024": solves,
+            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
+
+
 def run_profile_kernel(args):
     """One kernel of the path on the bench workload at --size, for ncu: two warm-up
     launches, then three timed ones (capture with -k <kernel> -s 2 -c 1).  The handle is
@@ -425,6 +506,7 @@ def run_ours(args):
             solves["mixed_vs_fp64_max_rel_eig_diff"] = float(np.max(np.abs(lam_mixed - lam_fp64) / lam_fp64))
 
     batched = run_batched(args, P, pin, torch, np, barrier) if args.batch > 0 else None
+    learned = run_learned(args, P, pin, torch, np) if (args.learned and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -443,7 +525,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (block 0.92 GB)"},
                 "roofline": roofline, "spmm_fp64": spmm_live, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "solve": solves, "batched": batched}
+                "clocks": clocks, "solve": solves, "batched": batched, "learned_smoother": learned}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -460,6 +542,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-kernel", default=None,
                     help="only launch this kernel (spmm_am_fp64, jacobi_fp64, jacobi_fp32, ...) for ncu")
+    ap.add_argument("--learned", type=int, default=1, help="1: run the learned-smoother section")
     ap.add_argument("--batch", type=int, default=64,
                     help="independent problems in the batched run (0 skips it)")
     ap.add_argument("--size", type=int, default=NFINE,
