@@ -934,116 +934,168 @@ __global__ void __launch_bounds__(1024) k_sygv_tridiag_s(int n, int k, double* w
 //    ctol = 1e-5 |T| form a cluster: its vectors are re-orthogonalised against each other
 //    (vectors of close eigenvalues computed independently lose orthogonality by
 //    ~eps |T| / gap) and rotated by a Rayleigh-Ritz step inside the cluster.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Largest number of vectors of one cluster iterated side by side (one lane each); each
+// lane keeps its tridiagonal-solve scratch (4n doubles, padded by one) in shared memory.
+__host__ __device__ inline int inviter_lanes(int n) {
+  const int budget = 160 * 1024;
+  int l = budget / ((4 * n + 1) * (int)sizeof(double));
+  return l < 1 ? 1 : (l > 32 ? 32 : l);
+}
+
+// One warp per cluster head: inverse iteration with Rayleigh-quotient shifts for the
+// eigenvalues of the cluster, run for up to inviter_lanes(n) vectors at once (lane j
+// solves with vector j's own shift), each sweep followed by modified Gram-Schmidt of the
+// block against the cluster's earlier vectors and within itself; then a Jacobi
+// Rayleigh-Ritz inside the cluster.  Dot products, updates, norms and Rayleigh quotients
+// are spread over the 32 lanes.
 __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work, double* __restrict__ lam,
                                                      const int* status) {
   if (status[0] != 0) return;
-  extern __shared__ double sw[];  // 4n
+  extern __shared__ double sw[];  // inviter_lanes(n) x (4n + 1)
+  __shared__ double H[kClusterRR * kClusterRR], R[kClusterRR * kClusterRR];
+  __shared__ double shifts[32];
+  __shared__ int perm[kClusterRR];
   SygvWork W = sygv_work(work, n, k);
-  const int i = blockIdx.x;
-  if (threadIdx.x != 0) return;
+  const int i = blockIdx.x, lane = threadIdx.x;
   const double tnorm = W.lamx[k];
   const double ctol = 1e-5 * tnorm;
   const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
   const double* lx = W.lamx;
-  if (i > 0 && lx[i] - lx[i - 1] <= ctol) return;  // not a cluster head
+  if (i > 0 && lx[i] - lx[i - 1] <= ctol) return;  // not a cluster head (uniform per block)
   int last = i;
   while (last + 1 < k && lx[last + 1] - lx[last] <= ctol) ++last;
   const double* d = W.d;
   const double* e = W.e;
   double* Z = W.Z;
-  double* u0 = sw;
-  double* u1 = u0 + n;
-  double* u2 = u1 + n;
-  double* bb = u2 + n;
-  for (int q = i; q <= last; ++q) {
-    for (int r = 0; r < n; ++r) bb[r] = hash_unit((unsigned)q, (unsigned)r) + 1e-3;
-    double shift = lx[q];
+  const int SP = inviter_lanes(n);
+  const int ld = 4 * n + 1;
+  auto vec = [&](int j) { return sw + (size_t)j * ld + 3 * n; };  // vector j of the block
+  for (int c0 = i; c0 <= last; c0 += SP) {
+    const int cs = min(SP, last + 1 - c0);
+    for (int j = 0; j < cs; ++j)
+      for (int r = lane; r < n; r += 32) vec(j)[r] = hash_unit((unsigned)(c0 + j), (unsigned)r) + 1e-3;
+    if (lane < cs) shifts[lane] = lx[c0 + lane];
     const int iters = (i == last) ? 3 : 4;
     for (int it = 0; it < iters; ++it) {
-      tri_solve(n, d, e, shift, bb, u0, u1, u2, tiny);
-      for (int pass = 0; pass < 2; ++pass)
-        for (int o = i; o < q; ++o) {
-          double dot = 0.0;
-          for (int r = 0; r < n; ++r) dot += bb[r] * Z[(int64_t)r * k + o];
-          for (int r = 0; r < n; ++r) bb[r] -= dot * Z[(int64_t)r * k + o];
+      __syncwarp();
+      if (lane < cs) {
+        double* base = sw + (size_t)lane * ld;
+        tri_solve(n, d, e, shifts[lane], base + 3 * n, base, base + n, base + 2 * n, tiny);
+      }
+      __syncwarp();
+      for (int j = 0; j < cs; ++j) {
+        double* b = vec(j);
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int o = i; o < c0; ++o) {  // earlier chunks of the cluster (in Z)
+            double dot = 0.0;
+            for (int r = lane; r < n; r += 32) dot = fma(b[r], Z[(int64_t)r * k + o], dot);
+            dot = warp_sum(dot);
+            for (int r = lane; r < n; r += 32) b[r] -= dot * Z[(int64_t)r * k + o];
+          }
+          for (int o = 0; o < j; ++o) {  // earlier vectors of this block
+            const double* bo = vec(o);
+            double dot = 0.0;
+            for (int r = lane; r < n; r += 32) dot = fma(b[r], bo[r], dot);
+            dot = warp_sum(dot);
+            for (int r = lane; r < n; r += 32) b[r] -= dot * bo[r];
+          }
         }
-      double nrm = 0.0;
-      for (int r = 0; r < n; ++r) nrm += bb[r] * bb[r];
-      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-      for (int r = 0; r < n; ++r) bb[r] *= inv;
-      if (it >= 1) {  // Rayleigh-quotient shift
-        double rq = 0.0;
-        for (int r = 0; r < n; ++r) {
-          double tq = d[r] * bb[r];
-          if (r > 0) tq += e[r - 1] * bb[r - 1];
-          if (r < n - 1) tq += e[r] * bb[r + 1];
-          rq += bb[r] * tq;
+        double nrm = 0.0;
+        for (int r = lane; r < n; r += 32) nrm = fma(b[r], b[r], nrm);
+        nrm = warp_sum(nrm);
+        const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+        for (int r = lane; r < n; r += 32) b[r] *= inv;
+        __syncwarp();
+        if (it >= 1) {  // Rayleigh-quotient shift
+          double rq = 0.0;
+          for (int r = lane; r < n; r += 32) {
+            double tq = d[r] * b[r];
+            if (r > 0) tq += e[r - 1] * b[r - 1];
+            if (r < n - 1) tq += e[r] * b[r + 1];
+            rq = fma(b[r], tq, rq);
+          }
+          rq = warp_sum(rq);
+          if (lane == 0) shifts[j] = rq;
         }
-        shift = rq;
+        __syncwarp();
       }
     }
-    lam[q] = shift;
-    for (int r = 0; r < n; ++r) Z[(int64_t)r * k + q] = bb[r];
+    if (lane < cs) lam[c0 + lane] = shifts[lane];
+    for (int j = 0; j < cs; ++j)
+      for (int r = lane; r < n; r += 32) Z[(int64_t)r * k + c0 + j] = vec(j)[r];
+    __syncwarp();
   }
   const int s = last - i + 1;
   if (s >= 2 && s <= kClusterRR) {
-    double H[kClusterRR * kClusterRR], R[kClusterRR * kClusterRR];
+    // projected tridiagonal matrix of the cluster's vectors
     for (int a = 0; a < s; ++a)
       for (int b = a; b < s; ++b) {
         double acc = 0.0;
-        for (int r = 0; r < n; ++r) {
+        for (int r = lane; r < n; r += 32) {
           double tq = d[r] * Z[(int64_t)r * k + i + b];
           if (r > 0) tq += e[r - 1] * Z[(int64_t)(r - 1) * k + i + b];
           if (r < n - 1) tq += e[r] * Z[(int64_t)(r + 1) * k + i + b];
-          acc += Z[(int64_t)r * k + i + a] * tq;
+          acc = fma(Z[(int64_t)r * k + i + a], tq, acc);
         }
-        H[a * s + b] = acc;
-        H[b * s + a] = acc;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+          H[a * s + b] = acc;
+          H[b * s + a] = acc;
+        }
       }
-    for (int a = 0; a < s; ++a)
-      for (int b = 0; b < s; ++b) R[a * s + b] = (a == b) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 12; ++sweep) {
-      double off = 0.0, diag = 0.0;
-      for (int a = 0; a < s; ++a) {
-        diag += H[a * s + a] * H[a * s + a];
-        for (int b = a + 1; b < s; ++b) off += H[a * s + b] * H[a * s + b];
-      }
-      if (off <= 1e-30 * (diag + DBL_MIN)) break;
+    __syncwarp();
+    if (lane == 0) {  // cyclic Jacobi on the s x s matrix (s <= 16)
       for (int a = 0; a < s; ++a)
-        for (int b = a + 1; b < s; ++b) {
-          const double hab = H[a * s + b];
-          if (hab == 0.0) continue;
-          const double th = 0.5 * (H[b * s + b] - H[a * s + a]) / hab;
-          const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
-          for (int l = 0; l < s; ++l) {
-            const double ha = H[l * s + a], hb = H[l * s + b];
-            H[l * s + a] = c * ha - sn * hb;
-            H[l * s + b] = sn * ha + c * hb;
-          }
-          for (int l = 0; l < s; ++l) {
-            const double ha = H[a * s + l], hb = H[b * s + l];
-            H[a * s + l] = c * ha - sn * hb;
-            H[b * s + l] = sn * ha + c * hb;
-          }
-          for (int l = 0; l < s; ++l) {
-            const double ra = R[l * s + a], rb = R[l * s + b];
-            R[l * s + a] = c * ra - sn * rb;
-            R[l * s + b] = sn * ra + c * rb;
-          }
+        for (int b = 0; b < s; ++b) R[a * s + b] = (a == b) ? 1.0 : 0.0;
+      for (int sweep = 0; sweep < 12; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int a = 0; a < s; ++a) {
+          diag += H[a * s + a] * H[a * s + a];
+          for (int b = a + 1; b < s; ++b) off += H[a * s + b] * H[a * s + b];
         }
+        if (off <= 1e-30 * (diag + DBL_MIN)) break;
+        for (int a = 0; a < s; ++a)
+          for (int b = a + 1; b < s; ++b) {
+            const double hab = H[a * s + b];
+            if (hab == 0.0) continue;
+            const double th = 0.5 * (H[b * s + b] - H[a * s + a]) / hab;
+            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+            for (int l = 0; l < s; ++l) {
+              const double ha = H[l * s + a], hb = H[l * s + b];
+              H[l * s + a] = c * ha - sn * hb;
+              H[l * s + b] = sn * ha + c * hb;
+            }
+            for (int l = 0; l < s; ++l) {
+              const double ha = H[a * s + l], hb = H[b * s + l];
+              H[a * s + l] = c * ha - sn * hb;
+              H[b * s + l] = sn * ha + c * hb;
+            }
+            for (int l = 0; l < s; ++l) {
+              const double ra = R[l * s + a], rb = R[l * s + b];
+              R[l * s + a] = c * ra - sn * rb;
+              R[l * s + b] = sn * ra + c * rb;
+            }
+          }
+      }
+      for (int a = 0; a < s; ++a) perm[a] = a;
+      for (int a = 0; a < s; ++a)
+        for (int b = a + 1; b < s; ++b)
+          if (H[perm[b] * s + perm[b]] < H[perm[a] * s + perm[a]]) {
+            const int t2 = perm[a];
+            perm[a] = perm[b];
+            perm[b] = t2;
+          }
     }
-    int perm[kClusterRR];
-    for (int a = 0; a < s; ++a) perm[a] = a;
-    for (int a = 0; a < s; ++a)
-      for (int b = a + 1; b < s; ++b)
-        if (H[perm[b] * s + perm[b]] < H[perm[a] * s + perm[a]]) {
-          const int t2 = perm[a];
-          perm[a] = perm[b];
-          perm[b] = t2;
-        }
-    double row[kClusterRR];
-    for (int r = 0; r < n; ++r) {
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) {  // rotate the cluster's rows (one row per lane)
+      double row[kClusterRR];
       for (int a = 0; a < s; ++a) {
         double acc = 0.0;
         for (int b = 0; b < s; ++b) acc += Z[(int64_t)r * k + i + b] * R[b * s + perm[a]];
@@ -1051,7 +1103,7 @@ __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work,
       }
       for (int a = 0; a < s; ++a) Z[(int64_t)r * k + i + a] = row[a];
     }
-    for (int a = 0; a < s; ++a) lam[i + a] = H[perm[a] * s + perm[a]];
+    if (lane < s) lam[i + lane] = H[perm[lane] * s + perm[lane]];
   }
 }
 
@@ -1163,7 +1215,7 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     k_sygv_tridiag_s<<<1, 1024, smem_tri_s, s>>>(n, k, w, status_dev);
   else
     k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
-  k_sygv_inviter<<<k, 32, (size_t)4 * n * sizeof(double), s>>>(n, k, w, lam, status_dev);
+  k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
   k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
   PASE_CUDA(cudaGetLastError());
