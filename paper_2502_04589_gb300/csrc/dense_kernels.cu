@@ -6,6 +6,7 @@
 // FP64 on this part runs at ~1.2 TFLOP/s against ~75 TFLOP/s FP32, so the FP64 kernels
 // are ALU-bound: they are laid out to keep the FP64 pipe busy (register tiles fed from
 // shared memory) rather than to minimise bytes.
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "pase_internal.h"
@@ -1107,6 +1108,227 @@ __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work,
   }
 }
 
+// 3b. Householder tridiagonalisation on a thread-block cluster of kTriC CTAs (one SM
+//     each): CTA c keeps the full rows r = c, c + kTriC, ... of the symmetric matrix in
+//     its shared memory.  Step j: the owner of row j forms the reflector (as kernel 3) and
+//     writes it into every CTA's shared memory; each CTA computes p = t A22 v for its own
+//     rows and writes those entries (and its share of p.v) into every CTA; every CTA then
+//     applies the rank-2 update to its own rows.  Reflector, p and partial sums are double
+//     buffered by step parity, so two hardware cluster barriers per step order the
+//     exchange.  d, e, tau and the reflectors go to the workspace exactly as in kernel 3;
+//     the eigenvalue brackets are computed afterwards by k_sygv_multisect.
+constexpr int kTriC = 8;
+constexpr int kTriClusterMin = 64;  // below this the single-CTA kernels are faster
+__host__ __device__ inline size_t tri_cluster_smem(int n) {
+  const int rows = (n + kTriC - 1) / kTriC;
+  return ((size_t)rows * n + 4 * (size_t)n + 4 * kTriC + 8) * sizeof(double);
+}
+
+__global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
+    k_sygv_tridiag_c(int n, int k, double* work, const int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  if (status[0] != 0) return;  // uniform over the cluster (written by an earlier kernel)
+  extern __shared__ double smc[];
+  __shared__ double red[40];
+  SygvWork W = sygv_work(work, n, k);
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  const int nrows = (n - rank + kTriC - 1) / kTriC;  // rows owned by this CTA
+  double* Arow = smc;                                           // [nrows][n]
+  double* vb = Arow + (size_t)((n + kTriC - 1) / kTriC) * n;    // [2][n] reflector
+  double* pb = vb + 2 * n;                                      // [2][n] p
+  double* part = pb + 2 * n;                                    // [2][kTriC] partial p.v
+  double* scal = part + 2 * kTriC;                              // [2][2] t, beta; [4..] max exchange
+  const double* K = W.K;
+  for (int lr = warp; lr < nrows; lr += nwarps) {
+    const int r = lr * kTriC + rank;
+    for (int c = lane; c < n; c += 32) Arow[(size_t)lr * n + c] = 0.5 * (K[(int64_t)r * n + c] + K[(int64_t)c * n + r]);
+  }
+  __syncthreads();
+  if (W.info[0] > 0) {  // dropped directions get a value above the kept spectrum
+    double rmax = 0.0;
+    for (int lr = tid; lr < nrows; lr += nt) {
+      const int r = lr * kTriC + rank;
+      if (W.tau[r] != 0.0) continue;
+      double a = 0.0;
+      for (int c = 0; c < n; ++c)
+        if (W.tau[c] == 0.0) a += fabs(Arow[(size_t)lr * n + c]);
+      rmax = fmax(rmax, a);
+    }
+    rmax = block_max(rmax, red);
+    if (tid < kTriC) *cluster.map_shared_rank(scal + 4 + rank, tid) = rmax;
+    cluster.sync();
+    double big = 0.0;
+    for (int q = 0; q < kTriC; ++q) big = fmax(big, scal[4 + q]);
+    big = 2.0 * big + 1.0;
+    for (int lr = warp; lr < nrows; lr += nwarps) {
+      const int r = lr * kTriC + rank;
+      for (int c = lane; c < n; c += 32)
+        if (W.tau[r] != 0.0 || W.tau[c] != 0.0) Arow[(size_t)lr * n + c] = (r == c) ? big : 0.0;
+    }
+  }
+  cluster.sync();  // the drop mask in tau is read above and overwritten below
+  for (int j = 0; j + 2 < n; ++j) {
+    const int par = j & 1;
+    const int len = n - j - 1, j1 = j + 1;
+    double* v = vb + par * n;
+    double* pp = pb + par * n;
+    double* pt = part + par * kTriC;
+    double* sc = scal + par * 2;
+    if (j % kTriC == rank) {  // owner of row j: the reflector
+      const double* x = Arow + (size_t)(j / kTriC) * n + j1;
+      double ps = 0.0;
+      for (int r = 1 + tid; r < len; r += nt) ps += x[r] * x[r];
+      const double sig = block_sum(ps, red);
+      __shared__ double s_hh[3];
+      if (tid == 0) {
+        const double x0 = x[0];
+        double beta = x0, t = 0.0, sl = 0.0;
+        if (sig != 0.0) {
+          const double nrm = sqrt(x0 * x0 + sig);
+          beta = (x0 >= 0.0) ? -nrm : nrm;
+          t = (beta - x0) / beta;
+          sl = 1.0 / (x0 - beta);
+        }
+        s_hh[0] = beta;
+        s_hh[1] = t;
+        s_hh[2] = sl;
+        W.d[j] = Arow[(size_t)(j / kTriC) * n + j];
+        W.e[j] = beta;
+        W.tau[j] = t;
+      }
+      __syncthreads();
+      const double t = s_hh[1], sl = s_hh[2];
+      for (int r = tid; r < len; r += nt) {
+        const double vr = (r == 0) ? 1.0 : x[r] * sl;
+        if (r >= 1) W.K[(int64_t)j * n + (j1 + r)] = vr;  // reflector store
+        for (int q = 0; q < kTriC; ++q) *cluster.map_shared_rank(v + r, q) = vr;
+      }
+      if (tid < kTriC) {
+        *cluster.map_shared_rank(sc, tid) = t;
+        *cluster.map_shared_rank(sc + 1, tid) = s_hh[0];
+      }
+    }
+    cluster.sync();
+    const double t = sc[0];
+    if (t != 0.0) {
+      // p = t A22 v for this CTA's rows R >= j1; share of p.v
+      double pvp = 0.0;
+      const int lr0 = (j1 - rank + kTriC - 1) / kTriC;  // first own local row with R >= j1
+      for (int lr = lr0 + warp; lr < nrows; lr += nwarps) {
+        const int R = lr * kTriC + rank;
+        const double* row = Arow + (size_t)lr * n + j1;
+        double acc = 0.0;
+        for (int c = lane; c < len; c += 32) acc = fma(row[c], v[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double pr = t * acc;
+        if (lane < kTriC) *cluster.map_shared_rank(pp + (R - j1), lane) = pr;
+        if (lane == 0) pvp += pr * v[R - j1];
+      }
+      const double pvs = block_sum(pvp, red);
+      if (tid < kTriC) *cluster.map_shared_rank(pt + rank, tid) = pvs;
+    }
+    cluster.sync();
+    if (t != 0.0) {
+      double pv = 0.0;
+      for (int q = 0; q < kTriC; ++q) pv += pt[q];
+      const double Kc = 0.5 * t * pv;
+      for (int r = tid; r < len; r += nt) pp[r] -= Kc * v[r];
+      __syncthreads();
+      const int lr0 = (j1 - rank + kTriC - 1) / kTriC;
+      for (int lr = lr0 + warp; lr < nrows; lr += nwarps) {
+        const int R = lr * kTriC + rank;
+        double* row = Arow + (size_t)lr * n + j1;
+        const double vR = v[R - j1], pR = pp[R - j1];
+        for (int c = lane; c < len; c += 32) row[c] -= vR * pp[c] + pR * v[c];
+      }
+    }
+    __syncthreads();
+  }
+  // the trailing 2 x 2 block
+  if (tid == 0) {
+    if (n >= 2 && (n - 2) % kTriC == rank) {
+      W.d[n - 2] = Arow[(size_t)((n - 2) / kTriC) * n + (n - 2)];
+      W.tau[n - 2] = 0.0;
+    }
+    if ((n - 1) % kTriC == rank) {
+      if (n >= 2) W.e[n - 2] = Arow[(size_t)((n - 1) / kTriC) * n + (n - 2)];
+      W.d[n - 1] = Arow[(size_t)((n - 1) / kTriC) * n + (n - 1)];
+      W.e[n - 1] = 0.0;
+      W.tau[n - 1] = 0.0;
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still address its shared memory
+}
+
+// 3c. Gershgorin bounds of the tridiagonal matrix and FP32 multisection for the k
+//     smallest eigenvalues (the tail of kernel 3, for the cluster variant).
+__global__ void __launch_bounds__(1024) k_sygv_multisect(int n, int k, double* work, const int* status) {
+  if (status[0] != 0) return;
+  extern __shared__ double shm[];
+  __shared__ double red[40];
+  __shared__ double s_lo, s_hi;
+  SygvWork W = sygv_work(work, n, k);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int* icnt = reinterpret_cast<int*>(shm);  // nt
+  float* df = reinterpret_cast<float*>(icnt + nt);
+  float* e2f = df + n;
+  float* flo = e2f + n;
+  float* fhi = flo + k;
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(W.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(W.e[i]) : 0.0);
+      lo = fmin(lo, W.d[i] - r);
+      hi = fmax(hi, W.d[i] + r);
+    }
+    s_lo = lo;
+    s_hi = hi;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    df[i] = (float)W.d[i];
+    e2f[i] = (float)(W.e[i] * W.e[i]);
+  }
+  for (int i = tid; i < k; i += nt) {
+    flo[i] = (float)s_lo - 1e-6f * (float)fabs(s_lo) - 1e-30f;
+    fhi[i] = (float)s_hi + 1e-6f * (float)fabs(s_hi) + 1e-30f;
+  }
+  __syncthreads();
+  const int G = max(1, min(32, nt / k));
+  for (int round = 0; round < 40; ++round) {
+    const int i = tid / G, g = tid % G;
+    if (i < k) {
+      const float a = flo[i], b = fhi[i];
+      const float x = a + (b - a) * (float)(g + 1) / (float)(G + 1);
+      icnt[tid] = (b - a > 4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) ? sturm_count_f32(n, df, e2f, x) : -1;
+    }
+    __syncthreads();
+    int moved = 0;
+    if (i < k && g == 0 && icnt[tid] >= 0) {
+      const float a = flo[i], b = fhi[i];
+      float na = a, nb = b;
+      for (int q = 0; q < G; ++q) {
+        const float x = a + (b - a) * (float)(q + 1) / (float)(G + 1);
+        if (icnt[i * G + q] > i) {
+          nb = x;
+          break;
+        }
+        na = x;
+      }
+      flo[i] = na;
+      fhi[i] = nb;
+      moved = 1;
+    }
+    if (block_sum((double)moved, red) == 0.0) break;
+  }
+  for (int i = tid; i < k; i += nt) W.lamx[i] = 0.5 * ((double)flo[i] + (double)fhi[i]);
+  if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));  // |T| bound
+}
+
 // 5. back-transform: each CTA takes kBtCols columns of Z through z <- H_0 ... H_{n-3} z,
 //    then c = D L^-T z.
 constexpr int kBtCols = 4;
@@ -1211,10 +1433,18 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     k_sygv_chol<<<1, 1024, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, status_dev);
   k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, status_dev);
-  if (packed)
+  const size_t smem_c = tri_cluster_smem(n);
+  const size_t smem_ms = (size_t)1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
+  if (n >= kTriClusterMin && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
+    PASE_TRY(ensure_max_smem((const void*)k_sygv_tridiag_c, 200 * 1024));
+    k_sygv_tridiag_c<<<kTriC, 256, smem_c, s>>>(n, k, w, status_dev);
+    k_sygv_multisect<<<1, 1024, smem_ms, s>>>(n, k, w, status_dev);
+    h->launches++;
+  } else if (packed) {
     k_sygv_tridiag_s<<<1, 1024, smem_tri_s, s>>>(n, k, w, status_dev);
-  else
+  } else {
     k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
+  }
   k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
   k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
