@@ -24,7 +24,10 @@
  *    width nev_w (nev plus guard columns) and must be a multiple of 8 and at most 256.
  *  - Pointers to multivectors, lambda and small matrices may be device or host
  *    memory; the library detects which (cudaPointerGetAttributes).  Host inputs are
- *    copied in and host outputs copied back inside the call, on the handle's stream.
+ *    copied in and host outputs copied back inside the call, on the handle's stream,
+ *    through device staging buffers that the handle keeps between calls (they grow to
+ *    the largest set of host arguments one call has staged and are freed by
+ *    pase_destroy).  A handle must not be used by two host threads at once.
  *  - All device work runs on the CUDA stream given to pase_create; calls return after
  *    the stream has been synchronised, so outputs are ready on return.
  *  - Borrowed inputs are only read during the call.  The handle owns all of its device

@@ -87,10 +87,29 @@ static bool is_device_ptr(const void* p) {
 struct Stage {
   pase_ctx* h;
   std::vector<std::pair<void*, std::pair<void*, size_t>>> outs;  // (dev, (host, bytes))
-  std::vector<void*> temps;
+  std::vector<size_t> taken;                                     // pool entries in use
   explicit Stage(pase_ctx* hh) : h(hh) {}
   ~Stage() {
-    for (void* t : temps) cudaFree(t);
+    for (size_t i : taken) h->stage_pool[i].busy = false;
+  }
+  // a device buffer of at least `bytes` from the handle's pool (allocated on first need)
+  int take(size_t bytes, void** out) {
+    bytes = std::max<size_t>(bytes, 16);
+    size_t best = SIZE_MAX;
+    for (size_t i = 0; i < h->stage_pool.size(); ++i) {
+      const auto& b = h->stage_pool[i];
+      if (!b.busy && b.bytes >= bytes && (best == SIZE_MAX || b.bytes < h->stage_pool[best].bytes)) best = i;
+    }
+    if (best == SIZE_MAX) {
+      void* p = nullptr;
+      PASE_TRY(dev_alloc(h, &p, bytes));
+      h->stage_pool.push_back({p, bytes, false});
+      best = h->stage_pool.size() - 1;
+    }
+    h->stage_pool[best].busy = true;
+    taken.push_back(best);
+    *out = h->stage_pool[best].p;
+    return PASE_OK;
   }
   // device view of an input
   int in(const void* p, size_t bytes, const void** dev) {
@@ -103,8 +122,7 @@ struct Stage {
       return PASE_OK;
     }
     void* t = nullptr;
-    PASE_CUDA(cudaMalloc(&t, std::max<size_t>(bytes, 16)));
-    temps.push_back(t);
+    PASE_TRY(take(bytes, &t));
     PASE_CUDA(cudaMemcpyAsync(t, p, bytes, cudaMemcpyHostToDevice, h->stream));
     *dev = t;
     return PASE_OK;
@@ -120,8 +138,7 @@ struct Stage {
       return PASE_OK;
     }
     void* t = nullptr;
-    PASE_CUDA(cudaMalloc(&t, std::max<size_t>(bytes, 16)));
-    temps.push_back(t);
+    PASE_TRY(take(bytes, &t));
     if (inout) PASE_CUDA(cudaMemcpyAsync(t, p, bytes, cudaMemcpyHostToDevice, h->stream));
     outs.push_back({t, {p, bytes}});
     *dev = t;

@@ -175,6 +175,14 @@ struct pase_ctx {
   const double* ls_last_W = nullptr;
   bool graphs_ok = true;
   int tuned_m = 0;
+  // device staging buffers for host-memory arguments, kept between calls (grow-only;
+  // a buffer is busy while the call that took it runs)
+  struct StageBuf {
+    void* p;
+    size_t bytes;
+    bool busy;
+  };
+  std::vector<StageBuf> stage_pool;
   pase::Smoother* sm = nullptr;  // learned smoother (pase_set_grid)
   bool sm_suspend = false;       // Jacobi while the trainer generates samples
   double aug_tol_now = 0;    // current inner tolerance
