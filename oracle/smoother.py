@@ -28,6 +28,9 @@ batch loss is the mean over columns.  Adam as in Kingma & Ba (2015).
 
 Use in the V-cycle: on level 0 each of the nu1 pre- and nu2 post-smoothing sweeps
 x <- x + omega D^-1 (b - A x) becomes x <- x + S(b - A x); coarser levels keep Jacobi.
+Inference (the V-cycle, `apply(..., act_bf16=True)`) stores the hidden activations in
+bfloat16 between layers; training differentiates the same network with FP32
+activations.
 
 Parity: pinned in tests/test_oracle_pins.py (convolution against scipy.ndimage,
 finite-difference gradients, positive homogeneity, the Jacobi-equivalent weights,
@@ -126,8 +129,10 @@ def node_features(d, n, log_kappa):
     return (acc / 2 ** d).reshape(-1)
 
 
-def forward(params, s, feat, d, n1, round_bf16=True):
-    """s [B][N] (normalised Jacobi-scaled residual), feat [N] -> y [B][N] and a cache."""
+def forward(params, s, feat, d, n1, round_bf16=True, act_bf16=False):
+    """s [B][N] (normalised Jacobi-scaled residual), feat [N] -> y [B][N] and a cache.
+    act_bf16: the hidden activations (outputs of the three ReLU layers) are rounded to
+    bfloat16, as the library's inference path stores them."""
     p = bf16_round(params) if round_bf16 else np.asarray(params, dtype=np.float64)
     B = s.shape[0]
     x = np.stack([s, np.broadcast_to(feat, s.shape)], axis=1)
@@ -136,6 +141,8 @@ def forward(params, s, feat, d, n1, round_bf16=True):
         z = conv(x, W, bb, d, n1)
         cache.append((x, z))
         x = np.maximum(z, 0.0) if relu else z
+        if relu and act_bf16:
+            x = bf16_round(x.astype(np.float32))
     return x[:, 0, :], (p, cache)
 
 
@@ -174,10 +181,11 @@ def normalise(r, dinv):
     return s, rho
 
 
-def apply(params, r, dinv, feat, d, n1, round_bf16=True):
-    """The correction delta = S(r) for a residual block r [N][B]; returns [N][B]."""
+def apply(params, r, dinv, feat, d, n1, round_bf16=True, act_bf16=False):
+    """The correction delta = S(r) for a residual block r [N][B]; returns [N][B].
+    act_bf16=True is the inference form (hidden activations stored in bfloat16)."""
     s, rho = normalise(r, dinv)
-    y, _ = forward(params, s, feat, d, n1, round_bf16)
+    y, _ = forward(params, s, feat, d, n1, round_bf16, act_bf16)
     return (y * rho[:, None]).T
 
 
@@ -205,6 +213,7 @@ def adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def fine_smoother(params, dinv, feat, d, n1, round_bf16=True):
-    """Callable x-correction S(r) for `mg.Hierarchy(..., fine_smoother=...)`."""
-    return lambda r: apply(params, r, dinv, feat, d, n1, round_bf16)
+def fine_smoother(params, dinv, feat, d, n1, round_bf16=True, act_bf16=True):
+    """Callable x-correction S(r) for `mg.Hierarchy(..., fine_smoother=...)` (inference
+    form by default)."""
+    return lambda r: apply(params, r, dinv, feat, d, n1, round_bf16, act_bf16)

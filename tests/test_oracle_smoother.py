@@ -126,7 +126,30 @@ def test_learned_vcycle_with_jacobi_weights_is_the_jacobi_vcycle():
     feat = sm.node_features(2, 16, np.log(pb.kappa))
     om = float(sm.bf16_round(np.float32(2.0 / 3.0)))
     pj = pin.smoother_init(2, omega=2.0 / 3.0, noise=0.0)
-    H_l = mg.Hierarchy(pb.A, pb.chain, omega=om, fine_smoother=sm.fine_smoother(pj, dinv, feat, 2, n1))
+    H_l = mg.Hierarchy(pb.A, pb.chain, omega=om,
+                       fine_smoother=sm.fine_smoother(pj, dinv, feat, 2, n1, act_bf16=False))
     H_j = mg.Hierarchy(pb.A, pb.chain, omega=om)
     b = np.random.default_rng(0).standard_normal((pb.N, 3))
     np.testing.assert_allclose(H_l.solve(b, 2), H_j.solve(b, 2), rtol=1e-11, atol=1e-13)
+
+
+def test_bf16_activations_exact_when_representable():
+    """Inference form: rounding the hidden activations to bfloat16 changes nothing when
+    every activation is a bfloat16 number already (Jacobi weights on a residual whose
+    Jacobi-scaled values are +-1, so that their RMS is 1 and the activations are 0 or 1),
+    and stays within bfloat16 precision otherwise."""
+    A, n, feat = _tiny(2)
+    n1 = n - 1
+    dinv = 1.0 / A.diagonal()
+    q = np.ones((A.shape[0], 1))
+    q[1::2, 0] = -1.0
+    r = q / dinv[:, None]   # D^-1 r = q
+    pj = pin.smoother_init(2, noise=0.0)
+    a = sm.apply(pj, r, dinv, feat, 2, n1, act_bf16=True)
+    b = sm.apply(pj, r, dinv, feat, 2, n1, act_bf16=False)
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-12)
+    p = pin.smoother_init(2, seed=3, noise=0.3)
+    r2 = np.random.default_rng(2).standard_normal((A.shape[0], 3))
+    a = sm.apply(p, r2, dinv, feat, 2, n1, act_bf16=True)
+    b = sm.apply(p, r2, dinv, feat, 2, n1, act_bf16=False)
+    assert np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)) < 3e-2
