@@ -1373,6 +1373,7 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_tol_now = 0;
   h->aug_nconv = 0;
   if (stp) *stp = st;
+  if (sm_active(h)) PASE_TRY(sm_check_timeout(h));
   return rc;
 }
 
@@ -1414,7 +1415,8 @@ int pase_smoother_apply(pase_handle h, int m, const double* R, double* D) {
   PASE_TRY(st.in(R, nm, &dR));
   PASE_TRY(st.out(D, nm, &dD));
   PASE_TRY(sm_apply<double>(h, m, (const double*)dR, m, h->lv[0].dinv, (double*)dD, m, false));
-  return st.finish();
+  PASE_TRY(st.finish());
+  return sm_check_timeout(h);
 }
 
 int pase_smoother_step(pase_handle h, const double* E, const double* R, int update, float lr, float beta1,
@@ -1556,6 +1558,7 @@ int pase_train_smoother(pase_handle h, const pase_train_options* o, double* loss
   PASE_TRY(vcycle_energy_factor(h, vseed, &f_jacobi));
   h->sm_suspend = false;
   s->rejected = !(f_learned < f_jacobi);
+  PASE_TRY(sm_check_timeout(h));
   losses[0] = first;
   losses[1] = last;
   losses[2] = jac;

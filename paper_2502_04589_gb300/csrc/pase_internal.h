@@ -126,6 +126,7 @@ struct Smoother {
   float *act0 = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr, *ga = nullptr, *gb = nullptr;
   double *E = nullptr, *AE = nullptr, *e = nullptr, *r = nullptr;  // [N][8] training blocks
   double* sums = nullptr;                                          // small device scalars
+  int* tc_err = nullptr;                                           // tensor-core wait timeout flag
   double* h_sums = nullptr;                                        // pinned mirror
 };
 int smoother_nparams(int dim);
@@ -138,6 +139,7 @@ int sm_step(pase_ctx* h, const double* e, const double* r, bool update, float lr
             double* loss_cols);
 int sm_jacobi_loss(pase_ctx* h, const double* e, const double* r, double* loss_cols);
 int sm_grad_to_host(pase_ctx* h, double* grad_host);
+int sm_check_timeout(pase_ctx* h);  // PASE_ERR_TIMEOUT if a tensor-core wait gave up (then clears it)
 void sm_free(pase_ctx* h);
 
 }  // namespace pase

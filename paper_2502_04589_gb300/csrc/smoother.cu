@@ -165,6 +165,219 @@ __global__ void __launch_bounds__(256) k_sm_conv(int64_t N, int n1, const float*
   }
 }
 
+// ------------------------------------------------------------------ inference path
+// The V-cycle applies the network with its hidden activations stored in bfloat16,
+// node-major [B][N][16] (32 bytes per node).  Layer 1 (2 -> 16) and layer 4 (16 -> 1) run
+// on the CUDA cores; the two 16 -> 16 layers are implicit GEMMs on the tensor cores
+// (tcgen05): per tile of 128 nodes, M = 128 nodes, N = 16 output channels, K = 16 input
+// channels per tap, one MMA per tap accumulating in tensor memory.
+
+// layer 1: Y[b][i][co] = bf16(ReLU(bias[co] + sum_ci sum_t W[co][ci][t] act0[b][ci][i + o_t]))
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const float* __restrict__ X,
+                                                     const float* __restrict__ W, const float* __restrict__ bias,
+                                                     __nv_bfloat16* __restrict__ Y) {
+  constexpr int T = Taps<DIM>::T;
+  __shared__ float ws[kSmC * 2 * T + kSmC];
+  for (int k = threadIdx.x; k < kSmC * 2 * T; k += blockDim.x) ws[k] = W[k];
+  for (int k = threadIdx.x; k < kSmC; k += blockDim.x) ws[kSmC * 2 * T + k] = bias[k];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int cx, cy, cz;
+  node_coords<DIM>(i, n1, cx, cy, cz);
+  float acc[kSmC];
+#pragma unroll
+  for (int co = 0; co < kSmC; ++co) acc[co] = ws[kSmC * 2 * T + co];
+  const int64_t n1l = n1;
+  for (int ci = 0; ci < 2; ++ci) {
+    const float* xb = X + ((int64_t)b * 2 + ci) * N;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+      const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+      const float v = ok ? xb[i + ox + oy * n1l + oz * n1l * n1l] : 0.f;
+#pragma unroll
+      for (int co = 0; co < kSmC; ++co) acc[co] = fmaf(ws[(co * 2 + ci) * T + t], v, acc[co]);
+    }
+  }
+  __align__(16) __nv_bfloat16 out[kSmC];
+#pragma unroll
+  for (int co = 0; co < kSmC; ++co) out[co] = __float2bfloat16(fmaxf(acc[co], 0.f));
+  uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + i) * kSmC);
+  dst[0] = reinterpret_cast<const uint4*>(out)[0];
+  dst[1] = reinterpret_cast<const uint4*>(out)[1];
+}
+
+// layer 4: y[b][i] = bias + sum_ci sum_t W[0][ci][t] X[b][i + o_t][ci]   (X bf16, ReLU'd)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sm_last_bf(int64_t N, int n1, const __nv_bfloat16* __restrict__ X,
+                                                    const float* __restrict__ W, const float* __restrict__ bias,
+                                                    float* __restrict__ y) {
+  constexpr int T = Taps<DIM>::T;
+  __shared__ float ws[kSmC * T + 1];
+  for (int k = threadIdx.x; k < kSmC * T; k += blockDim.x) ws[k] = W[k];
+  if (threadIdx.x == 0) ws[kSmC * T] = bias[0];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int cx, cy, cz;
+  node_coords<DIM>(i, n1, cx, cy, cz);
+  float acc = ws[kSmC * T];
+  const int64_t n1l = n1;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+    const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                    (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+    if (!ok) continue;
+    const uint4* src = reinterpret_cast<const uint4*>(X + ((int64_t)b * N + i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
+    __align__(16) uint4 v[2];
+    v[0] = __ldg(src);
+    v[1] = __ldg(src + 1);
+    const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(v);
+#pragma unroll
+    for (int ci = 0; ci < kSmC; ++ci) acc = fmaf(ws[ci * T + t], __bfloat162float(xv[ci]), acc);
+  }
+  y[(int64_t)b * N + i] = acc;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// UMMA shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core matrices,
+// lbo = byte distance between core matrices along K, sbo = along M (or N)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;                // base offset 0, no swizzle
+}
+
+constexpr int kTcTile = 128;                   // nodes per MMA tile (M)
+constexpr uint32_t kTcIdesc = (1u << 4)        // D: FP32
+                              | (1u << 7)      // A: BF16
+                              | (1u << 10)     // B: BF16
+                              | ((16u >> 3) << 17)         // N = 16
+                              | ((uint32_t)(kTcTile >> 4) << 24);  // M = 128
+
+__host__ __device__ inline size_t tc_smem_bytes(int T) { return (size_t)T * (4096 + 512) + 128; }
+
+// hidden layer 16 -> 16 on the tensor cores; Y = bf16(ReLU(bias + conv(X)))
+template <int DIM>
+__global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B, const __nv_bfloat16* __restrict__ X,
+                                                        const float* __restrict__ W, const float* __restrict__ bias,
+                                                        __nv_bfloat16* __restrict__ Y, int* __restrict__ err) {
+  constexpr int T = Taps<DIM>::T;
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem);                 // [T][128 x 16]
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(tc_smem + (size_t)T * 4096);  // [T][16 x 16]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sbias[kSmC];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights: B_t[co][ci] = W[co][ci][t], canonical K-major layout (core matrix (co/8, ci/8))
+  for (int k = tid; k < T * 256; k += kTcTile) {
+    const int t = k / 256, rem = k % 256, co = rem / 16, ci = rem % 16;
+    sB[t * 256 + (co / 8) * 128 + (ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] =
+        __float2bfloat16(W[(co * kSmC + ci) * T + t]);
+  }
+  if (tid < kSmC) sbias[tid] = bias[tid];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int64_t tiles_per_col = (N + kTcTile - 1) / kTcTile;
+  const int64_t ntiles = tiles_per_col * B;
+  const int64_t n1l = n1;
+  uint32_t phase = 0;
+  bool ok_run = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok_run; tile += gridDim.x) {
+    const int b = (int)(tile / tiles_per_col);
+    const int64_t i = (tile % tiles_per_col) * kTcTile + tid;  // this thread's row of A
+    int cx = 0, cy = 0, cz = 0;
+    if (i < N) node_coords<DIM>(i, n1, cx, cy, cz);
+    const __nv_bfloat16* Xb = X + (int64_t)b * N * kSmC;
+    __nv_bfloat16* rowA = sA + (tid / 8) * 128 + (tid % 8) * 8;
+#pragma unroll 3
+    for (int t = 0; t < T; ++t) {
+      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+      const bool ok = i < N && (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+      uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+      if (ok) {
+        const uint4* src = reinterpret_cast<const uint4*>(Xb + (i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
+        lo = __ldg(src);
+        hi = __ldg(src + 1);
+      }
+      *reinterpret_cast<uint4*>(rowA + t * 2048) = lo;        // channels 0-7  (core column 0)
+      *reinterpret_cast<uint4*>(rowA + t * 2048 + 64) = hi;   // channels 8-15 (core column 1)
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      for (int t = 0; t < T; ++t) {
+        const uint64_t da = umma_desc(smem_u32(sA + t * 2048), 128, 256);
+        const uint64_t db = umma_desc(smem_u32(sB + t * 256), 128, 256);
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                     "l"(da), "l"(db), "r"(kTcIdesc), "r"(t));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it)
+      asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                   : "=r"(done)
+                   : "r"(smem_u32(&mbar)), "r"(phase));
+    if (!__syncthreads_and((int)done)) {  // (uniform) give up: report, let the MMAs finish, stop
+      if (tid == 0) atomicExch(err, 1);
+      done = 0;
+      for (int it = 0; it < (1 << 22) && !done; ++it)
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_u32(&mbar)), "r"(phase));
+      ok_run = false;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t r[16];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (i < N) {
+      __align__(16) __nv_bfloat16 out[kSmC];
+#pragma unroll
+      for (int c = 0; c < kSmC; ++c) out[c] = __float2bfloat16(fmaxf(__uint_as_float(r[c]) + sbias[c], 0.f));
+      uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + i) * kSmC);
+      dst[0] = reinterpret_cast<const uint4*>(out)[0];
+      dst[1] = reinterpret_cast<const uint4*>(out)[1];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // A tiles and the accumulator are reused by the next tile
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
 // Weight gradient of one layer: partial[blk][(co*CIN + ci)*T + t] = sum over the block's
 // grid rows and all b of G[b][co][i] act(X[b][ci][i + o_t]); bias gradients after the
 // weights (partial[blk][COUT*CIN*T + co] = sum G[b][co][i]).  A grid row is a run of n1
@@ -368,6 +581,8 @@ int sm_set_grid(pase_ctx* h, int dim, int n, const double* logk_host) {
   PASE_TRY(dev_alloc_t(h, &s->e, NB));
   PASE_TRY(dev_alloc_t(h, &s->r, NB));
   PASE_TRY(dev_alloc_t(h, &s->sums, 8 * kSmBatch));
+  PASE_TRY(dev_alloc_t(h, &s->tc_err, 1));
+  PASE_CUDA(cudaMemsetAsync(s->tc_err, 0, sizeof(int), h->stream));
   PASE_CUDA(cudaMallocHost(&s->h_sums, sizeof(double) * 8 * kSmBatch));
   double* dl = nullptr;
   if (logk_host) {
@@ -438,6 +653,49 @@ static int forward(pase_ctx* h, int B) {
   return PASE_OK;
 }
 
+// inference forward pass (bf16 hidden activations, tensor-core hidden layers)
+template <int DIM>
+static int forward_fast(pase_ctx* h, int B) {
+  Smoother* s = h->sm;
+  LayerOff L[4];
+  layer_offsets(s->T, L);
+  const float* p = s->peff;
+  __nv_bfloat16* y1 = reinterpret_cast<__nv_bfloat16*>(s->z1);
+  __nv_bfloat16* y2 = reinterpret_cast<__nv_bfloat16*>(s->z2);
+  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)B);
+  k_sm_first_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, s->act0, p + L[0].W, p + L[0].b, y1);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  constexpr int T = Taps<DIM>::T;
+  const size_t smem = tc_smem_bytes(T);
+  PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM>, 200 * 1024));
+  const int64_t tiles = ((s->N + kTcTile - 1) / kTcTile) * B;
+  const int per_sm = std::max(1, (int)((220 * 1024) / (smem + 1024)));
+  const int tcgrid = (int)std::min<int64_t>(tiles, (int64_t)152 * per_sm);
+  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, B, y1, p + L[1].W, p + L[1].b, y2, s->tc_err);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, B, y2, p + L[2].W, p + L[2].b, y1, s->tc_err);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  k_sm_last_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, y1, p + L[3].W, p + L[3].b, s->y);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+int sm_check_timeout(pase_ctx* h) {
+  if (!h->sm || !h->sm->tc_err) return PASE_OK;
+  int e = 0;
+  PASE_CUDA(cudaMemcpyAsync(&e, h->sm->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PASE_TRY(sync_stream(h));
+  if (e) {
+    PASE_CUDA(cudaMemsetAsync(h->sm->tc_err, 0, sizeof(int), h->stream));
+    return fail(PASE_ERR_TIMEOUT, "learned smoother: a tensor-core wait ran out of its limit");
+  }
+  return PASE_OK;
+}
+
 template <typename T>
 static int normalise(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, const T* dinv) {
   Smoother* s = h->sm;
@@ -465,8 +723,8 @@ int sm_apply(pase_ctx* h, int m, const T* R, int64_t ldr, const T* dinv, T* X, i
   for (int c0 = 0; c0 < m; c0 += kSmBatch) {
     const int bc = std::min(kSmBatch, m - c0);
     PASE_TRY(normalise<T>(h, c0, bc, R, ldr, dinv));
-    if (s->dim == 2) PASE_TRY(forward<2>(h, bc));
-    else PASE_TRY(forward<3>(h, bc));
+    if (s->dim == 2) PASE_TRY(forward_fast<2>(h, bc));
+    else PASE_TRY(forward_fast<3>(h, bc));
     dim3 grid((unsigned)std::min<int64_t>((s->N + 255) / 256, 1024), (unsigned)bc);
     k_sm_scatter<T><<<grid, 256, 0, h->stream>>>(s->N, c0, bc, s->y, s->sums + kSmBatch, X, ldx, add ? 1 : 0);
     h->launches++;

@@ -1,10 +1,13 @@
-"""Learned fine-level smoother through the C ABI (needs a GPU): network forward, loss,
-gradients and Adam against the FP64 oracle, the V-cycle with the network against the
-oracle's V-cycle, and what training gains over damped Jacobi.
+"""Learned fine-level smoother through the C ABI (needs a GPU): the inference pass
+(tensor-core hidden layers) and the training pass (loss, gradients, Adam) against the
+FP64 oracle, the V-cycle with the network against the oracle's V-cycle, and what
+training gains over damped Jacobi.
 
-Tolerances: the GPU evaluates the network in FP32 (bf16 parameters, FP32 accumulation)
-and the oracle in FP64 with the same bf16 parameters, so outputs agree to about 1e-6
-relative; gradients (sums of many FP32 products) to 1e-4 relative in norm per layer.
+Tolerances: training runs the network in FP32 (bf16 parameters, FP32 accumulation) and
+the oracle in FP64 with the same bf16 parameters, so losses agree to about 1e-6 relative
+and gradients (sums of many FP32 products) to 1e-4 relative in norm per layer.  Inference
+stores hidden activations in bf16 as the oracle's inference form does; an activation that
+FP32 and FP64 round to neighbouring bf16 values moves a column by far less than 1e-3.
 """
 import numpy as np
 import pytest
@@ -52,8 +55,15 @@ def test_apply_matches_oracle(d, n):
         D = np.empty_like(R)
         P.pase_smoother_apply(h, m, R, D)
         dinv = 1.0 / pb.A.diagonal()
-        ref = sm.apply(params, R, dinv, sm.node_features(d, n, lk), d, n - 1)
-        assert _colrel(D, ref) < 1e-5
+        feat = sm.node_features(d, n, lk)
+        # inference form: hidden activations in bf16, hidden layers on the tensor cores
+        # (FP32 accumulation); a rare activation rounded to the neighbouring bf16 value
+        # moves a column by far less than 1e-3
+        ref = sm.apply(params, R, dinv, feat, d, n - 1, act_bf16=True)
+        assert _colrel(D, ref) < 1e-3
+        # and within bf16 precision of the FP32-activation network
+        ref32 = sm.apply(params, R, dinv, feat, d, n - 1, act_bf16=False)
+        assert _colrel(D, ref32) < 3e-2
     finally:
         P.pase_destroy(h)
 
@@ -110,7 +120,7 @@ def test_learned_vcycle_matches_oracle():
         hier = mg.Hierarchy(pb.A, pb.chain,
                             fine_smoother=sm.fine_smoother(params, dinv, sm.node_features(d, n, lk), d, n - 1))
         Wref = opase.linear_solve(pb.A, pb.M, U, lam, 2, hier)
-        assert _colrel(W - U, Wref - U) < 1e-5
+        assert _colrel(W - U, Wref - U) < 1e-3
     finally:
         P.pase_destroy(h)
 
