@@ -108,19 +108,6 @@ __global__ void k_sm_gather(int64_t N, int c0, int bc, const T* __restrict__ R, 
   }
 }
 
-// X[i][c0+b] (+)= rho_b y[b][i]
-template <typename T>
-__global__ void k_sm_scatter(int64_t N, int c0, int bc, const float* __restrict__ y, const double* __restrict__ rho,
-                             T* __restrict__ X, int64_t ldx, int add) {
-  const int b = blockIdx.y;
-  const double rb = rho[b];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = rb * (double)y[(int64_t)b * N + i];
-    T* p = X + i * ldx + c0 + b;
-    *p = add ? (T)((double)*p + d) : (T)d;
-  }
-}
-
 // ------------------------------------------------------------------ convolution
 // Z[b][co][i] = bias[co] + sum_ci sum_t W[co][ci][t] act(X[b][ci][i + o_t]) (zero outside
 // the grid); act = ReLU when relu_in, identity otherwise; the result is multiplied by
@@ -172,11 +159,25 @@ __global__ void __launch_bounds__(256) k_sm_conv(int64_t N, int n1, const float*
 // (tcgen05): per tile of 128 nodes, M = 128 nodes, N = 16 output channels, K = 16 input
 // channels per tap, one MMA per tap accumulating in tensor memory.
 
-// layer 1: Y[b][i][co] = bf16(ReLU(bias[co] + sum_ci sum_t W[co][ci][t] act0[b][ci][i + o_t]))
+// inference input: S[b][i] = dinv_i R[i][c0+b] / rho_b, one thread per node for all bc
+// columns (contiguous reads of the node's row of R)
+template <typename T>
+__global__ void k_sm_gather_s(int64_t N, int c0, int bc, const T* __restrict__ R, int64_t ldr,
+                              const T* __restrict__ dinv, const double* __restrict__ rho, float* __restrict__ S) {
+  __shared__ double inv[kSmBatch];
+  if (threadIdx.x < kSmBatch) inv[threadIdx.x] = (threadIdx.x < bc && rho[threadIdx.x] > 0.0) ? 1.0 / rho[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double dv = (double)dinv[i];
+    for (int b = 0; b < bc; ++b) S[(int64_t)b * N + i] = (float)(dv * (double)R[i * ldr + c0 + b] * inv[b]);
+  }
+}
+
+// layer 1: Y[b][i][co] = bf16(ReLU(bias[co] + sum_t (W[co][0][t] S[b][i + o_t] + W[co][1][t] f[i + o_t])))
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const float* __restrict__ X,
-                                                     const float* __restrict__ W, const float* __restrict__ bias,
-                                                     __nv_bfloat16* __restrict__ Y) {
+__global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const float* __restrict__ S,
+                                                     const float* __restrict__ feat, const float* __restrict__ W,
+                                                     const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y) {
   constexpr int T = Taps<DIM>::T;
   __shared__ float ws[kSmC * 2 * T + kSmC];
   for (int k = threadIdx.x; k < kSmC * 2 * T; k += blockDim.x) ws[k] = W[k];
@@ -191,17 +192,16 @@ __global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const fl
 #pragma unroll
   for (int co = 0; co < kSmC; ++co) acc[co] = ws[kSmC * 2 * T + co];
   const int64_t n1l = n1;
-  for (int ci = 0; ci < 2; ++ci) {
-    const float* xb = X + ((int64_t)b * 2 + ci) * N;
+  const float* sb = S + (int64_t)b * N;
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
-      const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
-                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
-      const float v = ok ? xb[i + ox + oy * n1l + oz * n1l * n1l] : 0.f;
+  for (int t = 0; t < T; ++t) {
+    const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+    const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                    (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+    const int64_t nb = i + ox + oy * n1l + oz * n1l * n1l;
+    const float v0 = ok ? sb[nb] : 0.f, v1 = ok ? feat[nb] : 0.f;
 #pragma unroll
-      for (int co = 0; co < kSmC; ++co) acc[co] = fmaf(ws[(co * 2 + ci) * T + t], v, acc[co]);
-    }
+    for (int co = 0; co < kSmC; ++co) acc[co] = fmaf(ws[(co * 2 + 1) * T + t], v1, fmaf(ws[(co * 2) * T + t], v0, acc[co]));
   }
   __align__(16) __nv_bfloat16 out[kSmC];
 #pragma unroll
@@ -211,38 +211,45 @@ __global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const fl
   dst[1] = reinterpret_cast<const uint4*>(out)[1];
 }
 
-// layer 4: y[b][i] = bias + sum_ci sum_t W[0][ci][t] X[b][i + o_t][ci]   (X bf16, ReLU'd)
-template <int DIM>
-__global__ void __launch_bounds__(256) k_sm_last_bf(int64_t N, int n1, const __nv_bfloat16* __restrict__ X,
-                                                    const float* __restrict__ W, const float* __restrict__ bias,
-                                                    float* __restrict__ y) {
-  constexpr int T = Taps<DIM>::T;
-  __shared__ float ws[kSmC * T + 1];
-  for (int k = threadIdx.x; k < kSmC * T; k += blockDim.x) ws[k] = W[k];
-  if (threadIdx.x == 0) ws[kSmC * T] = bias[0];
+// layer 4 and the update: Xo[i][c0+b] (+)= rho_b (bias + sum_ci sum_t W[0][ci][t] X[b][i + o_t][ci]),
+// one thread per node for all bc columns (contiguous writes of the node's row)
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_sm_last_scatter(int64_t N, int n1, int c0, int bc,
+                                                         const __nv_bfloat16* __restrict__ X,
+                                                         const float* __restrict__ W, const float* __restrict__ bias,
+                                                         const double* __restrict__ rho, T* __restrict__ Xo,
+                                                         int64_t ldx, int add) {
+  constexpr int TT = Taps<DIM>::T;
+  __shared__ float ws[kSmC * TT + 1];
+  for (int k = threadIdx.x; k < kSmC * TT; k += blockDim.x) ws[k] = W[k];
+  if (threadIdx.x == 0) ws[kSmC * TT] = bias[0];
   __syncthreads();
-  const int b = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int cx, cy, cz;
   node_coords<DIM>(i, n1, cx, cy, cz);
-  float acc = ws[kSmC * T];
   const int64_t n1l = n1;
+  for (int b = 0; b < bc; ++b) {
+    float acc = ws[kSmC * TT];
 #pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
-    const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
-                    (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
-    if (!ok) continue;
-    const uint4* src = reinterpret_cast<const uint4*>(X + ((int64_t)b * N + i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
-    __align__(16) uint4 v[2];
-    v[0] = __ldg(src);
-    v[1] = __ldg(src + 1);
-    const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(v);
+    for (int t = 0; t < TT; ++t) {
+      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+      const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
+                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+      if (!ok) continue;
+      const uint4* src =
+          reinterpret_cast<const uint4*>(X + ((int64_t)b * N + i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
+      __align__(16) uint4 v[2];
+      v[0] = __ldg(src);
+      v[1] = __ldg(src + 1);
+      const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(v);
 #pragma unroll
-    for (int ci = 0; ci < kSmC; ++ci) acc = fmaf(ws[ci * T + t], __bfloat162float(xv[ci]), acc);
+      for (int ci = 0; ci < kSmC; ++ci) acc = fmaf(ws[ci * TT + t], __bfloat162float(xv[ci]), acc);
+    }
+    const double d = rho[b] * (double)acc;
+    T* p = Xo + i * ldx + c0 + b;
+    *p = add ? (T)((double)*p + d) : (T)d;
   }
-  y[(int64_t)b * N + i] = acc;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -653,32 +660,56 @@ static int forward(pase_ctx* h, int B) {
   return PASE_OK;
 }
 
-// inference forward pass (bf16 hidden activations, tensor-core hidden layers)
-template <int DIM>
-static int forward_fast(pase_ctx* h, int B) {
+// inference pass for columns c0..c0+bc-1 of R: X (+)= S(R) (bf16 hidden activations,
+// tensor-core hidden layers); rho must already be in sums[kSmBatch..]
+template <int DIM, typename T>
+static int forward_fast(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, const T* dinv, T* X, int64_t ldx,
+                        bool add) {
   Smoother* s = h->sm;
   LayerOff L[4];
   layer_offsets(s->T, L);
   const float* p = s->peff;
+  const double* rho = s->sums + kSmBatch;
   __nv_bfloat16* y1 = reinterpret_cast<__nv_bfloat16*>(s->z1);
   __nv_bfloat16* y2 = reinterpret_cast<__nv_bfloat16*>(s->z2);
-  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)B);
-  k_sm_first_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, s->act0, p + L[0].W, p + L[0].b, y1);
+  const int gn = (int)std::min<int64_t>((s->N + 255) / 256, 4096);
+  k_sm_gather_s<T><<<gn, 256, 0, h->stream>>>(s->N, c0, bc, R, ldr, dinv, rho, s->act0);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  constexpr int T = Taps<DIM>::T;
-  const size_t smem = tc_smem_bytes(T);
+  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)bc);
+  k_sm_first_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, s->act0, s->feat, p + L[0].W, p + L[0].b, y1);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  constexpr int TT = Taps<DIM>::T;
+  const size_t smem = tc_smem_bytes(TT);
   PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM>, 200 * 1024));
-  const int64_t tiles = ((s->N + kTcTile - 1) / kTcTile) * B;
+  const int64_t tiles = ((s->N + kTcTile - 1) / kTcTile) * bc;
   const int per_sm = std::max(1, (int)((220 * 1024) / (smem + 1024)));
   const int tcgrid = (int)std::min<int64_t>(tiles, (int64_t)152 * per_sm);
-  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, B, y1, p + L[1].W, p + L[1].b, y2, s->tc_err);
+  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y1, p + L[1].W, p + L[1].b, y2, s->tc_err);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, B, y2, p + L[2].W, p + L[2].b, y1, s->tc_err);
+  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y2, p + L[2].W, p + L[2].b, y1, s->tc_err);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  k_sm_last_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, y1, p + L[3].W, p + L[3].b, s->y);
+  k_sm_last_scatter<DIM, T><<<(unsigned)((s->N + 255) / 256), 256, 0, h->stream>>>(
+      s->N, s->n1, c0, bc, y1, p + L[3].W, p + L[3].b, rho, X, ldx, add ? 1 : 0);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// column sums of (D^-1 R)^2 and rho for columns c0..c0+bc-1 (into sums[kSmBatch..])
+template <typename T>
+static int scale_only(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, const T* dinv) {
+  Smoother* s = h->sm;
+  int64_t g = (s->N + 31) / 32;
+  if (g > kReduceBlocksHost) g = kReduceBlocksHost;
+  k_sm_colsq<T><<<(unsigned)g, 256, 0, h->stream>>>(s->N, c0, bc, R, ldr, dinv, s->colpart);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  PASE_TRY(launch_reduce_partials(h, (int)g, kSmBatch, s->colpart, s->sums));
+  k_sm_rho<<<1, 32, 0, h->stream>>>(bc, s->N, s->sums, s->sums + kSmBatch);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
@@ -722,13 +753,9 @@ int sm_apply(pase_ctx* h, int m, const T* R, int64_t ldr, const T* dinv, T* X, i
   Smoother* s = h->sm;
   for (int c0 = 0; c0 < m; c0 += kSmBatch) {
     const int bc = std::min(kSmBatch, m - c0);
-    PASE_TRY(normalise<T>(h, c0, bc, R, ldr, dinv));
-    if (s->dim == 2) PASE_TRY(forward_fast<2>(h, bc));
-    else PASE_TRY(forward_fast<3>(h, bc));
-    dim3 grid((unsigned)std::min<int64_t>((s->N + 255) / 256, 1024), (unsigned)bc);
-    k_sm_scatter<T><<<grid, 256, 0, h->stream>>>(s->N, c0, bc, s->y, s->sums + kSmBatch, X, ldx, add ? 1 : 0);
-    h->launches++;
-    PASE_CUDA(cudaGetLastError());
+    PASE_TRY(scale_only<T>(h, c0, bc, R, ldr, dinv));
+    if (s->dim == 2) PASE_TRY((forward_fast<2, T>(h, c0, bc, R, ldr, dinv, X, ldx, add)));
+    else PASE_TRY((forward_fast<3, T>(h, c0, bc, R, ldr, dinv, X, ldx, add)));
   }
   return PASE_OK;
 }
