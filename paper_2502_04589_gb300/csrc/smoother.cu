@@ -272,7 +272,19 @@ constexpr uint32_t kTcIdesc = (1u << 4)        // D: FP32
                               | ((16u >> 3) << 17)         // N = 16
                               | ((uint32_t)(kTcTile >> 4) << 24);  // M = 128
 
-__host__ __device__ inline size_t tc_smem_bytes(int T) { return (size_t)T * (4096 + 512) + 128; }
+// Tiles of 8 (x) x 16 (y) nodes (one z plane in 3D).  The tile's input halo (10 x 18
+// nodes, times 3 z planes in 3D) is staged once in shared memory as two planes, channels
+// 0-7 and channels 8-15, 16 bytes per node.  In the canonical K-major layout a core
+// matrix is then 8 consecutive x nodes of one plane, the 16 groups of 8 rows are the 16
+// halo rows (SBO = the halo row pitch) and the two K halves are the two planes (LBO =
+// plane size), so the A operand of tap t is the same halo addressed from a start shifted
+// by the tap's offset: no per-tap copies.
+constexpr int kTcX = 8, kTcY = 16, kTcHX = kTcX + 2, kTcHY = kTcY + 2;
+__host__ __device__ inline int tc_halo_nodes(int dim) { return kTcHX * kTcHY * (dim == 3 ? 3 : 1); }
+__host__ __device__ inline size_t tc_smem_bytes(int dim) {
+  const int T = dim == 2 ? 9 : 27;
+  return (size_t)2 * tc_halo_nodes(dim) * 16 + (size_t)T * 512 + 256;
+}
 
 // hidden layer 16 -> 16 on the tensor cores; Y = bf16(ReLU(bias + conv(X)))
 template <int DIM>
@@ -280,14 +292,16 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
                                                         const float* __restrict__ W, const float* __restrict__ bias,
                                                         __nv_bfloat16* __restrict__ Y, int* __restrict__ err) {
   constexpr int T = Taps<DIM>::T;
+  constexpr int HZ = DIM == 3 ? 3 : 1;
+  constexpr int HN = kTcHX * kTcHY * HZ;  // halo nodes
   extern __shared__ __align__(1024) uint8_t tc_smem[];
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem);                 // [T][128 x 16]
-  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(tc_smem + (size_t)T * 4096);  // [T][16 x 16]
+  uint4* plane0 = reinterpret_cast<uint4*>(tc_smem);                 // channels 0-7, [HZ][HY][HX]
+  uint4* plane1 = plane0 + HN;                                        // channels 8-15
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(tc_smem + (size_t)2 * HN * 16);  // [T][16 x 16]
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float sbias[kSmC];
   const int tid = threadIdx.x, warp = tid >> 5;
-  // weights: B_t[co][ci] = W[co][ci][t], canonical K-major layout (core matrix (co/8, ci/8))
   for (int k = tid; k < T * 256; k += kTcTile) {
     const int t = k / 256, rem = k % 256, co = rem / 16, ci = rem % 16;
     sB[t * 256 + (co / 8) * 128 + (ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] =
@@ -305,38 +319,43 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int64_t tiles_per_col = (N + kTcTile - 1) / kTcTile;
+  const int ntx = (n1 + kTcX - 1) / kTcX, nty = (n1 + kTcY - 1) / kTcY, ntz = DIM == 3 ? n1 : 1;
+  const int64_t tiles_per_col = (int64_t)ntx * nty * ntz;
   const int64_t ntiles = tiles_per_col * B;
   const int64_t n1l = n1;
+  const uint32_t p0 = smem_u32(plane0);
+  const uint32_t lbo = (uint32_t)HN * 16, sbo = kTcHX * 16;
   uint32_t phase = 0;
-  bool ok_run = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok_run; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int b = (int)(tile / tiles_per_col);
-    const int64_t i = (tile % tiles_per_col) * kTcTile + tid;  // this thread's row of A
-    int cx = 0, cy = 0, cz = 0;
-    if (i < N) node_coords<DIM>(i, n1, cx, cy, cz);
+    int64_t rem = tile % tiles_per_col;
+    const int tx = (int)(rem % ntx);
+    rem /= ntx;
+    const int ty = (int)(rem % nty);
+    const int tz = (int)(rem / nty);
+    const int x0 = tx * kTcX, y0 = ty * kTcY, z0 = tz;
     const __nv_bfloat16* Xb = X + (int64_t)b * N * kSmC;
-    __nv_bfloat16* rowA = sA + (tid / 8) * 128 + (tid % 8) * 8;
-#pragma unroll 3
-    for (int t = 0; t < T; ++t) {
-      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
-      const bool ok = i < N && (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
-                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
+    // stage the halo (zero outside the grid)
+    for (int e = tid; e < HN; e += kTcTile) {
+      const int hx = e % kTcHX, hy = (e / kTcHX) % kTcHY, hz = e / (kTcHX * kTcHY);
+      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = DIM == 3 ? z0 - 1 + hz : 0;
       uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-      if (ok) {
-        const uint4* src = reinterpret_cast<const uint4*>(Xb + (i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
+      if ((unsigned)gx < (unsigned)n1 && (unsigned)gy < (unsigned)n1 && (DIM == 2 || (unsigned)gz < (unsigned)n1)) {
+        const uint4* src = reinterpret_cast<const uint4*>(Xb + (gx + gy * n1l + gz * n1l * n1l) * kSmC);
         lo = __ldg(src);
         hi = __ldg(src + 1);
       }
-      *reinterpret_cast<uint4*>(rowA + t * 2048) = lo;        // channels 0-7  (core column 0)
-      *reinterpret_cast<uint4*>(rowA + t * 2048 + 64) = hi;   // channels 8-15 (core column 1)
+      plane0[e] = lo;
+      plane1[e] = hi;
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
       for (int t = 0; t < T; ++t) {
-        const uint64_t da = umma_desc(smem_u32(sA + t * 2048), 128, 256);
+        const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
+        const int base = ((DIM == 3 ? (1 + oz) : 0) * kTcHY + (1 + oy)) * kTcHX + (1 + ox);
+        const uint64_t da = umma_desc(p0 + (uint32_t)base * 16, lbo, sbo);
         const uint64_t db = umma_desc(smem_u32(sB + t * 256), 128, 256);
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -357,7 +376,6 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
         asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
                      : "=r"(done)
                      : "r"(smem_u32(&mbar)), "r"(phase));
-      ok_run = false;
       break;
     }
     phase ^= 1u;
@@ -370,16 +388,18 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;");
-    if (i < N) {
+    // accumulator row = tid: node (x0 + tid % 8, y0 + tid / 8, z0)
+    const int gx = x0 + (tid % kTcX), gy = y0 + (tid / kTcX);
+    if (gx < n1 && gy < n1) {
       __align__(16) __nv_bfloat16 out[kSmC];
 #pragma unroll
       for (int c = 0; c < kSmC; ++c) out[c] = __float2bfloat16(fmaxf(__uint_as_float(r[c]) + sbias[c], 0.f));
-      uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + i) * kSmC);
+      uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + gx + gy * n1l + (int64_t)z0 * n1l * n1l) * kSmC);
       dst[0] = reinterpret_cast<const uint4*>(out)[0];
       dst[1] = reinterpret_cast<const uint4*>(out)[1];
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // A tiles and the accumulator are reused by the next tile
+    __syncthreads();  // the halo and the accumulator are reused by the next tile
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
@@ -680,10 +700,10 @@ static int forward_fast(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, co
   k_sm_first_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, s->act0, s->feat, p + L[0].W, p + L[0].b, y1);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  constexpr int TT = Taps<DIM>::T;
-  const size_t smem = tc_smem_bytes(TT);
+  const size_t smem = tc_smem_bytes(DIM);
   PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM>, 200 * 1024));
-  const int64_t tiles = ((s->N + kTcTile - 1) / kTcTile) * bc;
+  const int64_t tiles = (int64_t)((s->n1 + kTcX - 1) / kTcX) * ((s->n1 + kTcY - 1) / kTcY) *
+                        (DIM == 3 ? s->n1 : 1) * bc;
   const int per_sm = std::max(1, (int)((220 * 1024) / (smem + 1024)));
   const int tcgrid = (int)std::min<int64_t>(tiles, (int64_t)152 * per_sm);
   k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y1, p + L[1].W, p + L[1].b, y2, s->tc_err);
