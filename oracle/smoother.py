@@ -28,9 +28,9 @@ batch loss is the mean over columns.  Adam as in Kingma & Ba (2015).
 
 Use in the V-cycle: on level 0 each of the nu1 pre- and nu2 post-smoothing sweeps
 x <- x + omega D^-1 (b - A x) becomes x <- x + S(b - A x); coarser levels keep Jacobi.
-Inference (the V-cycle, `apply(..., act_bf16=True)`) stores the hidden activations in
-bfloat16 between layers; training differentiates the same network with FP32
-activations.
+Inference (the V-cycle, `apply(..., act_bf16=True)`) rounds the network input and stores
+the hidden activations in bfloat16 between layers; training differentiates the same
+network with FP32 inputs and activations.
 
 Parity: pinned in tests/test_oracle_pins.py (convolution against scipy.ndimage,
 finite-difference gradients, positive homogeneity, the Jacobi-equivalent weights,
@@ -131,11 +131,13 @@ def node_features(d, n, log_kappa):
 
 def forward(params, s, feat, d, n1, round_bf16=True, act_bf16=False):
     """s [B][N] (normalised Jacobi-scaled residual), feat [N] -> y [B][N] and a cache.
-    act_bf16: the hidden activations (outputs of the three ReLU layers) are rounded to
-    bfloat16, as the library's inference path stores them."""
+    act_bf16: the network input (s, f) and the hidden activations (outputs of the three
+    ReLU layers) are rounded to bfloat16, as the library's inference path stores them."""
     p = bf16_round(params) if round_bf16 else np.asarray(params, dtype=np.float64)
     B = s.shape[0]
     x = np.stack([s, np.broadcast_to(feat, s.shape)], axis=1)
+    if act_bf16:
+        x = bf16_round(x.astype(np.float32))
     cache = []
     for W, bb, relu in unpack(p, d):
         z = conv(x, W, bb, d, n1)
