@@ -173,85 +173,6 @@ __global__ void k_sm_gather_s(int64_t N, int c0, int bc, const T* __restrict__ R
   }
 }
 
-// layer 1: Y[b][i][co] = bf16(ReLU(bias[co] + sum_t (W[co][0][t] S[b][i + o_t] + W[co][1][t] f[i + o_t])))
-template <int DIM>
-__global__ void __launch_bounds__(256) k_sm_first_bf(int64_t N, int n1, const float* __restrict__ S,
-                                                     const float* __restrict__ feat, const float* __restrict__ W,
-                                                     const float* __restrict__ bias, __nv_bfloat16* __restrict__ Y) {
-  constexpr int T = Taps<DIM>::T;
-  __shared__ float ws[kSmC * 2 * T + kSmC];
-  for (int k = threadIdx.x; k < kSmC * 2 * T; k += blockDim.x) ws[k] = W[k];
-  for (int k = threadIdx.x; k < kSmC; k += blockDim.x) ws[kSmC * 2 * T + k] = bias[k];
-  __syncthreads();
-  const int b = blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int cx, cy, cz;
-  node_coords<DIM>(i, n1, cx, cy, cz);
-  float acc[kSmC];
-#pragma unroll
-  for (int co = 0; co < kSmC; ++co) acc[co] = ws[kSmC * 2 * T + co];
-  const int64_t n1l = n1;
-  const float* sb = S + (int64_t)b * N;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
-    const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
-                    (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
-    const int64_t nb = i + ox + oy * n1l + oz * n1l * n1l;
-    const float v0 = ok ? sb[nb] : 0.f, v1 = ok ? feat[nb] : 0.f;
-#pragma unroll
-    for (int co = 0; co < kSmC; ++co) acc[co] = fmaf(ws[(co * 2 + 1) * T + t], v1, fmaf(ws[(co * 2) * T + t], v0, acc[co]));
-  }
-  __align__(16) __nv_bfloat16 out[kSmC];
-#pragma unroll
-  for (int co = 0; co < kSmC; ++co) out[co] = __float2bfloat16(fmaxf(acc[co], 0.f));
-  uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + i) * kSmC);
-  dst[0] = reinterpret_cast<const uint4*>(out)[0];
-  dst[1] = reinterpret_cast<const uint4*>(out)[1];
-}
-
-// layer 4 and the update: Xo[i][c0+b] (+)= rho_b (bias + sum_ci sum_t W[0][ci][t] X[b][i + o_t][ci]),
-// one thread per node for all bc columns (contiguous writes of the node's row)
-template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_sm_last_scatter(int64_t N, int n1, int c0, int bc,
-                                                         const __nv_bfloat16* __restrict__ X,
-                                                         const float* __restrict__ W, const float* __restrict__ bias,
-                                                         const double* __restrict__ rho, T* __restrict__ Xo,
-                                                         int64_t ldx, int add) {
-  constexpr int TT = Taps<DIM>::T;
-  __shared__ float ws[kSmC * TT + 1];
-  for (int k = threadIdx.x; k < kSmC * TT; k += blockDim.x) ws[k] = W[k];
-  if (threadIdx.x == 0) ws[kSmC * TT] = bias[0];
-  __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int cx, cy, cz;
-  node_coords<DIM>(i, n1, cx, cy, cz);
-  const int64_t n1l = n1;
-  for (int b = 0; b < bc; ++b) {
-    float acc = ws[kSmC * TT];
-#pragma unroll
-    for (int t = 0; t < TT; ++t) {
-      const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = DIM == 3 ? t / 9 - 1 : 0;
-      const bool ok = (unsigned)(cx + ox) < (unsigned)n1 && (unsigned)(cy + oy) < (unsigned)n1 &&
-                      (DIM == 2 || (unsigned)(cz + oz) < (unsigned)n1);
-      if (!ok) continue;
-      const uint4* src =
-          reinterpret_cast<const uint4*>(X + ((int64_t)b * N + i + ox + oy * n1l + oz * n1l * n1l) * kSmC);
-      __align__(16) uint4 v[2];
-      v[0] = __ldg(src);
-      v[1] = __ldg(src + 1);
-      const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(v);
-#pragma unroll
-      for (int ci = 0; ci < kSmC; ++ci) acc = fmaf(ws[ci * TT + t], __bfloat162float(xv[ci]), acc);
-    }
-    const double d = rho[b] * (double)acc;
-    T* p = Xo + i * ldx + c0 + b;
-    *p = add ? (T)((double)*p + d) : (T)d;
-  }
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // UMMA shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core matrices,
@@ -286,11 +207,19 @@ __host__ __device__ inline size_t tc_smem_bytes(int dim) {
   return (size_t)2 * tc_halo_nodes(dim) * 16 + (size_t)T * 512 + 256;
 }
 
-// hidden layer 16 -> 16 on the tensor cores; Y = bf16(ReLU(bias + conv(X)))
-template <int DIM>
+// LAYER 0: the 2 -> 16 input layer from S[b][N] (scaled residual) and f[N] (node
+// feature), both rounded to bf16, the input channels padded to K = 16 with zeros;
+// LAYER 1: a 16 -> 16 hidden layer; both give Y = bf16(ReLU(bias + conv)).
+// LAYER 2: the 16 -> 1 output layer with the update fused, Xo[i][c0+b] (+)= rho_b
+// (bias + conv(X)); the output channel is padded to N = 16 with zero weights.
+template <int DIM, int LAYER, typename TO>
 __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B, const __nv_bfloat16* __restrict__ X,
+                                                        const float* __restrict__ S, const float* __restrict__ feat,
                                                         const float* __restrict__ W, const float* __restrict__ bias,
-                                                        __nv_bfloat16* __restrict__ Y, int* __restrict__ err) {
+                                                        __nv_bfloat16* __restrict__ Y, int* __restrict__ err,
+                                                        const double* __restrict__ rho, TO* __restrict__ Xo,
+                                                        int64_t ldx, int c0, int add) {
+  constexpr bool LAST = LAYER == 2;
   constexpr int T = Taps<DIM>::T;
   constexpr int HZ = DIM == 3 ? 3 : 1;
   constexpr int HN = kTcHX * kTcHY * HZ;  // halo nodes
@@ -304,10 +233,12 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < T * 256; k += kTcTile) {
     const int t = k / 256, rem = k % 256, co = rem / 16, ci = rem % 16;
-    sB[t * 256 + (co / 8) * 128 + (ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] =
-        __float2bfloat16(W[(co * kSmC + ci) * T + t]);
+    float wv;
+    if (LAYER == 0) wv = ci < 2 ? W[(co * 2 + ci) * T + t] : 0.f;
+    else wv = (LAST && co > 0) ? 0.f : W[(co * kSmC + ci) * T + t];
+    sB[t * 256 + (co / 8) * 128 + (ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] = __float2bfloat16(wv);
   }
-  if (tid < kSmC) sbias[tid] = bias[tid];
+  if (tid < kSmC) sbias[tid] = (LAST && tid > 0) ? 0.f : bias[tid];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -341,9 +272,15 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = DIM == 3 ? z0 - 1 + hz : 0;
       uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
       if ((unsigned)gx < (unsigned)n1 && (unsigned)gy < (unsigned)n1 && (DIM == 2 || (unsigned)gz < (unsigned)n1)) {
-        const uint4* src = reinterpret_cast<const uint4*>(Xb + (gx + gy * n1l + gz * n1l * n1l) * kSmC);
-        lo = __ldg(src);
-        hi = __ldg(src + 1);
+        const int64_t node = gx + gy * n1l + gz * n1l * n1l;
+        if (LAYER == 0) {
+          __nv_bfloat162 sf = __floats2bfloat162_rn(S[(int64_t)b * N + node], feat[node]);
+          lo.x = *reinterpret_cast<uint32_t*>(&sf);
+        } else {
+          const uint4* src = reinterpret_cast<const uint4*>(Xb + node * kSmC);
+          lo = __ldg(src);
+          hi = __ldg(src + 1);
+        }
       }
       plane0[e] = lo;
       plane1[e] = hi;
@@ -391,12 +328,19 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
     // accumulator row = tid: node (x0 + tid % 8, y0 + tid / 8, z0)
     const int gx = x0 + (tid % kTcX), gy = y0 + (tid / kTcX);
     if (gx < n1 && gy < n1) {
-      __align__(16) __nv_bfloat16 out[kSmC];
+      const int64_t node = gx + gy * n1l + (int64_t)z0 * n1l * n1l;
+      if (LAST) {
+        const double d = rho[b] * (double)(__uint_as_float(r[0]) + sbias[0]);
+        TO* p = Xo + node * ldx + c0 + b;
+        *p = add ? (TO)((double)*p + d) : (TO)d;
+      } else {
+        __align__(16) __nv_bfloat16 out[kSmC];
 #pragma unroll
-      for (int c = 0; c < kSmC; ++c) out[c] = __float2bfloat16(fmaxf(__uint_as_float(r[c]) + sbias[c], 0.f));
-      uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + gx + gy * n1l + (int64_t)z0 * n1l * n1l) * kSmC);
-      dst[0] = reinterpret_cast<const uint4*>(out)[0];
-      dst[1] = reinterpret_cast<const uint4*>(out)[1];
+        for (int c = 0; c < kSmC; ++c) out[c] = __float2bfloat16(fmaxf(__uint_as_float(r[c]) + sbias[c], 0.f));
+        uint4* dst = reinterpret_cast<uint4*>(Y + ((int64_t)b * N + node) * kSmC);
+        dst[0] = reinterpret_cast<const uint4*>(out)[0];
+        dst[1] = reinterpret_cast<const uint4*>(out)[1];
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();  // the halo and the accumulator are reused by the next tile
@@ -696,24 +640,29 @@ static int forward_fast(pase_ctx* h, int c0, int bc, const T* R, int64_t ldr, co
   k_sm_gather_s<T><<<gn, 256, 0, h->stream>>>(s->N, c0, bc, R, ldr, dinv, rho, s->act0);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  dim3 grid((unsigned)((s->N + 255) / 256), (unsigned)bc);
-  k_sm_first_bf<DIM><<<grid, 256, 0, h->stream>>>(s->N, s->n1, s->act0, s->feat, p + L[0].W, p + L[0].b, y1);
-  h->launches++;
-  PASE_CUDA(cudaGetLastError());
   const size_t smem = tc_smem_bytes(DIM);
-  PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM>, 200 * 1024));
+  PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM, 0, T>, 200 * 1024));
+  PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM, 1, T>, 200 * 1024));
+  PASE_TRY(ensure_max_smem((const void*)k_sm_conv_tc<DIM, 2, T>, 200 * 1024));
   const int64_t tiles = (int64_t)((s->n1 + kTcX - 1) / kTcX) * ((s->n1 + kTcY - 1) / kTcY) *
                         (DIM == 3 ? s->n1 : 1) * bc;
   const int per_sm = std::max(1, (int)((220 * 1024) / (smem + 1024)));
   const int tcgrid = (int)std::min<int64_t>(tiles, (int64_t)152 * per_sm);
-  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y1, p + L[1].W, p + L[1].b, y2, s->tc_err);
+  k_sm_conv_tc<DIM, 0, T><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, nullptr, s->act0, s->feat, p + L[0].W,
+                                                                p + L[0].b, y1, s->tc_err, nullptr, nullptr, 0, 0, 0);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  k_sm_conv_tc<DIM><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y2, p + L[2].W, p + L[2].b, y1, s->tc_err);
+  k_sm_conv_tc<DIM, 1, T><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y1, nullptr, nullptr, p + L[1].W,
+                                                                p + L[1].b, y2, s->tc_err, nullptr, nullptr, 0, 0, 0);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
-  k_sm_last_scatter<DIM, T><<<(unsigned)((s->N + 255) / 256), 256, 0, h->stream>>>(
-      s->N, s->n1, c0, bc, y1, p + L[3].W, p + L[3].b, rho, X, ldx, add ? 1 : 0);
+  k_sm_conv_tc<DIM, 1, T><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y2, nullptr, nullptr, p + L[2].W,
+                                                                p + L[2].b, y1, s->tc_err, nullptr, nullptr, 0, 0, 0);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  k_sm_conv_tc<DIM, 2, T><<<tcgrid, kTcTile, smem, h->stream>>>(s->N, s->n1, bc, y1, nullptr, nullptr, p + L[3].W,
+                                                                p + L[3].b, nullptr, s->tc_err, rho, X, ldx, c0,
+                                                                add ? 1 : 0);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
