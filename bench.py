@@ -286,10 +286,45 @@ def run_learned(args, P, pin, torch, np):
             "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
 
 
+def run_profile_smoother(args):
+    """The learned smoother's inference pass (tensor-core convolutions) on a 2D lognormal
+    field at --size (8 columns, Jacobi-equivalent weights plus noise), three applications,
+    for ncu (capture with -k regex:k_sm_conv_tc; per application the launches are the
+    input layer, two hidden layers and the output layer)."""
+    import numpy as np
+    import torch
+
+    import pase_inputs as pin
+    from paper_2502_04589_gb300 import pase as P
+    n = args.size
+    pb = pin.build_problem(2, n, n // 8, kappa_seed=2000, sigma=1.0, mg_min=4)
+    opt = P.pase_default_options()
+    opt.coarse_level = pb.coarse_level
+    opt.autotune = 0
+    h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+    try:
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        P.pase_reserve(h, 8)
+        P.pase_set_grid(h, 2, n, np.log(pb.kappa))
+        P.pase_smoother_state(h, 2, (pin.smoother_init(2, seed=1, noise=0.02),))
+        R = torch.from_numpy(pin.start_vectors(1, pb.N, 8)).cuda()
+        D = torch.empty_like(R)
+        for _ in range(3):
+            P.pase_smoother_apply(h, 8, R, D)
+        torch.cuda.synchronize()
+    finally:
+        P.pase_destroy(h)
+    print(json.dumps({"profile_kernel": "smoother", "size": n, "N_h": pb.N, "columns": 8}), flush=True)
+    return 0
+
+
 def run_profile_kernel(args):
     """One kernel of the path on the bench workload at --size, for ncu: two warm-up
     launches, then three timed ones (capture with -k <kernel> -s 2 -c 1).  The handle is
-    created without the autotuner, so the sparse kernels run at 256 threads per block."""
+    created without the autotuner, so the sparse kernels run at 256 threads per block.
+    --profile-kernel smoother profiles the learned smoother instead (2D, --size^2)."""
+    if args.profile_kernel == "smoother":
+        return run_profile_smoother(args)
     import torch
 
     from paper_2502_04589_gb300 import pase as P
