@@ -286,6 +286,86 @@ def run_learned(args, P, pin, torch, np):
             "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
 
 
+def run_learned3d(args, P, pin, torch, np):
+    """Configuration 4, 3D: one smoother network (27 taps) trained on 16 seeded lognormal
+    fields (sigma 1, seeds 1000-1015) at 32^3, evaluated by the two-V-cycle energy error
+    factor on 4 held-out 64^3 fields (seeds 2000-2003) and by a full FP64 solve of the
+    128^3 held-out field 2000 (coarse 16^3, nev 32, tol 1e-8) with each smoother."""
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def make(n, seed, params=None, smoother=0, m=None):
+        pb = pin.build_problem(3, n, n // 8, kappa_seed=seed, sigma=1.0, mg_min=4)
+        opt = P.pase_default_options()
+        opt.coarse_level = pb.coarse_level
+        opt.smoother = smoother
+        h = P.pase_create(opt, stream)
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        P.pase_set_grid(h, 3, n, np.log(pb.kappa))
+        if m:
+            P.pase_reserve(h, m)
+        if params is not None:
+            P.pase_smoother_state(h, 3, params)
+        return pb, h
+
+    t0 = time.perf_counter()
+    state = (pin.smoother_init(3, seed=1, noise=0.02),)
+    accepted = 0
+    for f in range(16):
+        pb, h = make(32, 1000 + f, state)
+        out = P.pase_train_smoother(h, steps=40, lr=1e-3, seed=f)
+        accepted += int(out["accepted"])
+        state = P.pase_smoother_state(h, 3)
+        P.pase_destroy(h)
+    train_s = time.perf_counter() - t0
+    params = (state[0],)
+
+    def factor(pb, h, m=8):
+        e0 = pin.start_vectors(11, pb.N, m)
+        W = np.empty_like(e0)
+        P.pase_linear_solve(h, m, np.zeros_like(e0), np.ones(m), np.ascontiguousarray(pb.A @ e0), W)
+        E = e0 - W
+        return float(np.mean(np.sqrt(np.einsum("ij,ij->j", E, pb.A @ E) / np.einsum("ij,ij->j", e0, pb.A @ e0))))
+
+    fl, fj = [], []
+    for f in range(4):
+        pb, hl = make(64, 2000 + f, params, smoother=P.PASE_SMOOTHER_LEARNED, m=8)
+        fl.append(factor(pb, hl))
+        P.pase_destroy(hl)
+        pb, hj = make(64, 2000 + f, None, m=8)
+        fj.append(factor(pb, hj))
+        P.pase_destroy(hj)
+    solves = {}
+    nev = 32
+    m = pin.guard_columns(nev)
+    lam_ref = None
+    for name, sm_ in (("jacobi", P.PASE_SMOOTHER_JACOBI), ("learned", P.PASE_SMOOTHER_LEARNED)):
+        pb, h = make(128, 2000, params if sm_ else None, smoother=sm_, m=m)
+        U0 = torch.from_numpy(pin.start_vectors(SEED, pb.N, m)).cuda()
+        U = torch.empty_like(U0)
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rc, st = P.pase_solve(h, nev, 1e-8, m, U0, lam, U)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t1
+        lamh = lam[:nev].cpu().numpy()
+        solves[name] = {"status": rc, "iterations": st["iterations"], "seconds": sec,
+                        "ms_per_iteration": 1e3 * sec / max(1, st["iterations"]),
+                        "phase_ms": st["phase_ms"], "max_relres": st["max_residual"]}
+        if lam_ref is None:
+            lam_ref = lamh
+        else:
+            solves[name]["max_rel_eig_diff_vs_jacobi"] = float(np.max(np.abs(lamh - lam_ref) / lam_ref))
+        P.pase_destroy(h)
+    return {"workload": "3D Q1 lognormal kappa (sigma 1): train 16 fields at 32^3, evaluate 4 held-out fields "
+                        "at 64^3 and a full solve at 128^3 (coarse 16^3), nev 32",
+            "train_seconds": train_s, "fields_accepted_by_validation": accepted,
+            "vcycle2_energy_factor_learned": float(np.mean(fl)), "vcycle2_energy_factor_jacobi": float(np.mean(fj)),
+            "heldout_fields_better": int(sum(a < b for a, b in zip(fl, fj))),
+            "solve_128": solves,
+            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
+
+
 def run_profile_smoother(args):
     """The learned smoother's inference pass (tensor-core convolutions) on a 2D lognormal
     field at --size (8 columns, Jacobi-equivalent weights plus noise), three applications,
@@ -542,6 +622,7 @@ def run_ours(args):
 
     batched = run_batched(args, P, pin, torch, np, barrier) if args.batch > 0 else None
     learned = run_learned(args, P, pin, torch, np) if (args.learned and rank == 0) else None
+    learned3d = run_learned3d(args, P, pin, torch, np) if (args.learned and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -560,7 +641,8 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (block 0.92 GB)"},
                 "roofline": roofline, "spmm_fp64": spmm_live, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "solve": solves, "batched": batched, "learned_smoother": learned}
+                "clocks": clocks, "solve": solves, "batched": batched, "learned_smoother": learned,
+                "learned_smoother_3d": learned3d}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
