@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpase.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["sparse_kernels.cu", "dense_kernels.cu", "pase.cu", "noalloc.cu", "smoother.cu"]
+CU = ["sparse_kernels.cu", "dense_kernels.cu", "pase.cu", "noalloc.cu", "smoother.cu", "split_gemm.cu"]
 CPP = ["host_setup.cpp"]
 
 
@@ -29,7 +29,8 @@ def _run(cmd):
 
 def sources():
     return [os.path.join(CSRC, f) for f in CU + CPP] + [
-        os.path.join(CSRC, "pase_internal.h"), os.path.join(HERE, "..", "include", "pase.h")]
+        os.path.join(CSRC, "pase_internal.h"), os.path.join(CSRC, "tc_util.h"),
+        os.path.join(HERE, "..", "include", "pase.h")]
 
 
 def up_to_date():

@@ -313,6 +313,8 @@ static int reserve(pase_ctx* h, int m) {
   PASE_TRY(dev_alloc_t(h, &w.eigwork, w.eigwork_doubles));
   PASE_TRY(dev_alloc_t(h, &w.smallvec, (size_t)16 * m));
   PASE_TRY(dev_alloc_t(h, &w.status, 8));
+  PASE_TRY(dev_alloc_t(h, &h->tc_err, 1));
+  PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
   PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
   PASE_CUDA(cudaMallocHost(&w.h_status, sizeof(int) * 8));
   if (h->opt.autotune) PASE_TRY(autotune(h));
@@ -644,9 +646,24 @@ static int step_project(pase_ctx* h, const double* W, double* aH, double* bH, do
 // Step (d): U = W C_W + P C_H.
 static int step_prolongate(pase_ctx* h, const double* W, const double* CH, const double* CW, double* U) {
   const int m = h->w.m;
-  PASE_TRY(ts_gemm(h, h->N, m, m, 1.0, W, m, CW, m, 0.0, U, m));
+  if (h->opt.split_gemm && ts_gemm_split_ok(m, m, W, m, U, m))
+    PASE_TRY(ts_gemm_split(h, h->N, m, m, W, m, CW, m, U, m, h->tc_err));
+  else
+    PASE_TRY(ts_gemm(h, h->N, m, m, 1.0, W, m, CW, m, 0.0, U, m));
   PASE_TRY(launch_csr<double>(h, CSR_ADD, m, h->Pd, h->Pd.val, nullptr, CH, nullptr, U, nullptr, nullptr, 0.0,
                               U, nullptr, nullptr, nullptr));
+  return PASE_OK;
+}
+
+// Read (and clear) the flag of a tensor-core wait that ran out of its limit.
+static int tc_check(pase_ctx* h) {
+  if (!h->tc_err) return PASE_OK;
+  PASE_CUDA(cudaMemcpyAsync(h->w.h_status + 7, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PASE_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->w.h_status[7]) {
+    PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+    return fail(PASE_ERR_TIMEOUT, "split GEMM: a tensor-core wait ran out of its limit");
+  }
   return PASE_OK;
 }
 
@@ -902,6 +919,7 @@ void pase_default_options(pase_options* o) {
   o->use_graphs = 1;
   o->autotune = 1;
   o->smoother = PASE_SMOOTHER_JACOBI;
+  o->split_gemm = 1;
 }
 
 const char* pase_status_string(int code) {
@@ -946,6 +964,9 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
     delete h;
     return fail(PASE_ERR_CUDA, "pase_create: no CUDA device");
   }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && sms > 0)
+    h->num_sms = sms;
   *out = h;
   return PASE_OK;
 }
@@ -1156,7 +1177,8 @@ int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H, co
   PASE_TRY(st.out(U, nm, &dU));
   if (dU == dW) return fail(PASE_ERR_INVALID_ARG, "pase_prolongate: U must not alias W");
   PASE_TRY(step_prolongate(h, (const double*)dW, (const double*)dch, (const double*)dcw, (double*)dU));
-  return st.finish();
+  PASE_TRY(st.finish());
+  return tc_check(h);
 }
 
 int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int do_linear_solve,
@@ -1187,7 +1209,8 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
   h->aug_tol_now = 0;
   h->aug_nconv = 0;
   PASE_TRY(rc);
-  return st.finish();
+  PASE_TRY(st.finish());
+  return tc_check(h);
 }
 
 int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX) {
@@ -1210,7 +1233,10 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
   if (kernel == PASE_KERNEL_JACOBI_FP32 && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_SYGV3) return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
+  if (kernel < 0 || kernel > PASE_KERNEL_PROLONG_SPLIT)
+    return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
+  if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
+    return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 64");
   // deterministic operands
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 8u, w.R));
@@ -1247,6 +1273,8 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
         return ts_gram(h, h->N, m, m, w.W, m, w.R, m, w.GA, m, true);
       case PASE_KERNEL_PROLONG_FP64:
         return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
+      case PASE_KERNEL_PROLONG_SPLIT:
+        return ts_gemm_split(h, h->N, m, m, w.W, m, w.CW, m, w.T1, m, h->tc_err);
       case PASE_KERNEL_SYGV:
         return small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
       case PASE_KERNEL_SYGV3:
@@ -1267,7 +1295,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms_per_launch = (double)ms / reps;
-  return PASE_OK;
+  return tc_check(h);
 }
 
 int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, double* lambda, double* U,
@@ -1374,6 +1402,7 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_nconv = 0;
   if (stp) *stp = st;
   if (sm_active(h)) PASE_TRY(sm_check_timeout(h));
+  PASE_TRY(tc_check(h));
   return rc;
 }
 

@@ -148,6 +148,8 @@ struct pase_ctx {
   pase_options opt;
   cudaStream_t stream = nullptr;
   int device = 0;
+  int num_sms = 152;         // multiprocessors of the device (queried at create)
+  int* tc_err = nullptr;     // device flag: a tensor-core wait of the split GEMM ran out
   bool ready = false;
   int L = 0;             // number of levels (chain length + 1)
   int coarse_level = 0;  // which level is V_H
@@ -248,6 +250,11 @@ int launch_relres(pase_ctx* h, int m, const double* norms, const double* lam, do
 // dense tall-skinny
 int ts_gram(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int ldx, const double* Y,
             int ldy, double* G, int ldg, bool sym);  // G = X^T Y (k1 x k2)
+// Y = X C on the BF16 tensor cores with FP64 accuracy (split_gemm.cu); k1 even <= 64,
+// k2 <= 64, 16-byte aligned rows.  err: device flag set if a tensor-core wait runs out.
+bool ts_gemm_split_ok(int k1, int k2, const void* X, int64_t ldx, const void* Y, int64_t ldy);
+int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C, int ldc,
+                  double* Y, int64_t ldy, int* err);
 int ts_gemm(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const double* X, int ldx,
             const double* C, int ldc, double beta, double* Y, int ldy);  // Y = a X C + b Y
 template <typename T>

@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "pase_internal.h"
+#include "tc_util.h"
 
 namespace pase {
 
@@ -173,25 +174,8 @@ __global__ void k_sm_gather_s(int64_t N, int c0, int bc, const T* __restrict__ R
   }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// UMMA shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core matrices,
-// lbo = byte distance between core matrices along K, sbo = along M (or N)
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
-  return d;                // base offset 0, no swizzle
-}
-
-constexpr int kTcTile = 128;                   // nodes per MMA tile (M)
-constexpr uint32_t kTcIdesc = (1u << 4)        // D: FP32
-                              | (1u << 7)      // A: BF16
-                              | (1u << 10)     // B: BF16
-                              | ((16u >> 3) << 17)         // N = 16
-                              | ((uint32_t)(kTcTile >> 4) << 24);  // M = 128
+constexpr int kTcTile = 128;                                      // nodes per MMA tile (M)
+constexpr uint32_t kTcIdesc = umma_idesc_bf16(kTcTile, 16);       // M = 128, N = 16
 
 // Tiles of 8 (x) x 16 (y) nodes (one z plane in 3D).  The tile's input halo (10 x 18
 // nodes, times 3 z planes in 3D) is staged once in shared memory as two planes, channels
@@ -301,18 +285,10 @@ __global__ void __launch_bounds__(kTcTile) k_sm_conv_tc(int64_t N, int n1, int B
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar)));
     }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-      asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-                   : "=r"(done)
-                   : "r"(smem_u32(&mbar)), "r"(phase));
+    const uint32_t done = mbar_wait_bounded(smem_u32(&mbar), phase, 1 << 22);
     if (!__syncthreads_and((int)done)) {  // (uniform) give up: report, let the MMAs finish, stop
       if (tid == 0) atomicExch(err, 1);
-      done = 0;
-      for (int it = 0; it < (1 << 22) && !done; ++it)
-        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(done)
-                     : "r"(smem_u32(&mbar)), "r"(phase));
+      mbar_wait_bounded(smem_u32(&mbar), phase, 1 << 22);
       break;
     }
     phase ^= 1u;

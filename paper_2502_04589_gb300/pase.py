@@ -36,7 +36,7 @@ class PaseOptions(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):
@@ -282,7 +282,7 @@ def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres,
 
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
-           "prolong_fp64": 4, "sygv": 5, "sygv3": 6}
+           "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7}
 
 
 def pase_time_kernel(h, kernel, m, reps=10):

@@ -430,3 +430,29 @@ def test_full_size_laplace_3d_128_nev50(p3d_128, precision):
     assert np.all(res <= 1e-8), res.max()
     MU = pb.M @ U
     np.testing.assert_allclose(U.T @ MU, np.eye(m), atol=1e-10)
+
+
+def test_full_size_split_prolongation_sampled(p3d_128):
+    """Step (d) on the tensor cores at the benchmark size (N_h = 2,048,383, m = 56, the
+    launch bench.py times): sampled rows of U = W C_W against exact rational products."""
+    from fractions import Fraction
+    pb = p3d_128
+    m = pin.guard_columns(50)
+    c = Ctx(pb)
+    try:
+        W = pin.start_vectors(21, pb.N, m)
+        CW = pin.start_vectors(22, m, m)
+        U = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        CH = torch.zeros(pb.N_H, m, dtype=torch.float64, device="cuda")
+        P.pase_prolongate(c.h, m, dev(W), CH, dev(CW), U)
+        Uh = host(U)
+    finally:
+        c.close()
+    u = 2.0 ** -53
+    rows = list(range(0, pb.N, 40961)) + [pb.N - 1]
+    for r in rows:
+        smax = np.abs(W[r]).max() * np.abs(CW).max(axis=0)
+        for j in range(m):
+            ex = sum(Fraction(float(W[r, k])) * Fraction(float(CW[k, j])) for k in range(m))
+            assert abs(Fraction(float(Uh[r, j])) - ex) <= Fraction(8 * u) * Fraction(float(smax[j])) + Fraction(u) * abs(ex)
+    assert _colrel(Uh, W @ CW) < 1e-14

@@ -1,0 +1,174 @@
+"""The step-(d) product W C_W on the tensor cores (split digits, `split_gemm = 1`) against
+the oracle, through the C ABI (needs a GPU).
+
+With C_H = 0, pase_prolongate returns U = W C_W.  Bound checked on every entry (the
+error analysis of the split product: dropped digit diagonals, floor shifts, digit
+rounding, final rounding):
+    |U - W C_W| <= 8 u max_k |w_rk| max_k |c_kj| + u |W C_W| + K 2^-1074,   u = 2^-53,
+where W C_W is exact: rational arithmetic on sampled entries, and elsewhere the FP64
+oracle product with its own error bound K u sum_k |w_rk||c_kj| added.  Inputs stress the
+scaling: rows at 2^-40..2^40, entries spread over 2^60 inside a row, zero rows,
+subnormal entries, a ragged last tile (N = 31^3 is not a multiple of 128), every padded
+width K, N in {16, 32, 48, 64} and a width above 64 (the FP64 kernel).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import pase_inputs as pin
+from oracle import pase as opase
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2502_04589_gb300.pase")
+
+pytestmark = pytest.mark.gpu
+
+U53 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def p3d():
+    return pin.build_problem(3, 32, 8, kappa_seed=5, mg_min=4)
+
+
+def _handle(pb, split):
+    opt = P.pase_default_options()
+    opt.coarse_level = pb.coarse_level
+    opt.split_gemm = split
+    h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+    try:
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+    except Exception:
+        P.pase_destroy(h)
+        raise
+    return h
+
+
+def _operands(N, m, seed):
+    rng = np.random.default_rng(seed)
+    W = pin.start_vectors(seed, N, m)
+    W *= np.exp2(rng.integers(-40, 41, size=(N, 1)))           # row scales
+    wide = rng.choice(N, size=N // 16, replace=False)           # entries spread inside a row
+    W[wide] *= np.exp2(rng.integers(-60, 1, size=(len(wide), m)))
+    W[rng.choice(N, size=8, replace=False)] = 0.0               # zero rows
+    sub = rng.choice(N, size=4, replace=False)
+    W[sub[:2], : m // 2] = 1e-310                               # subnormal entries
+    W[sub[2:]] = 1e-310 * pin.start_vectors(seed + 2, 2, m)     # whole rows subnormal
+    W[N - 1] *= 3.0                                             # last (ragged-tile) row
+    C = pin.start_vectors(seed + 1, m, m) * np.exp2(rng.integers(-20, 21, size=(1, m)))
+    return W, C
+
+
+def _prolong(h, pb, m, W, C):
+    U = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+    CH = torch.zeros(pb.N_H, m, dtype=torch.float64, device="cuda")
+    P.pase_prolongate(h, m, torch.from_numpy(W).cuda(), CH, torch.from_numpy(C).cuda(), U)
+    return U.cpu().numpy()
+
+
+def _check_bound(pb, W, C, U, sample_rows):
+    """The split bound for K <= 64; wider blocks run the FP64 kernel, whose error bound
+    is the usual K u sum_k |w_rk||c_kj| (kept in `scale`)."""
+    K = W.shape[1]
+    if K <= 64:
+        scale = np.abs(W).max(axis=1)[:, None] * np.abs(C).max(axis=0)[None, :]
+    else:
+        scale = (K / 8.0) * (np.abs(W) @ np.abs(C))
+    ref = opase.prolongate(pb.P, W, np.zeros((pb.N_H, K)), C)
+    refbound = K * U53 * (np.abs(W) @ np.abs(C))                # the oracle's own rounding
+    err = np.abs(U - ref)
+    tiny = K * 2.0 ** -1074                                        # subnormal results
+    assert np.all(err <= 8 * U53 * scale + U53 * np.abs(ref) + refbound + tiny), (err / np.maximum(scale, 1e-300)).max()
+    for r in sample_rows:                                      # exact products, no oracle rounding
+        for j in range(C.shape[1]):
+            ex = sum(Fraction(float(W[r, k])) * Fraction(float(C[k, j])) for k in range(K))
+            e = abs(Fraction(float(U[r, j])) - ex)
+            assert e <= Fraction(8 * U53) * Fraction(float(scale[r, j])) + Fraction(U53) * abs(ex) + Fraction(tiny), (r, j)
+
+
+@pytest.mark.parametrize("m", [8, 16, 24, 40, 56, 64, 72])
+def test_split_product_error_bound(p3d, m):
+    pb = p3d
+    h = _handle(pb, 1)
+    try:
+        W, C = _operands(pb.N, m, 40 + m)
+        U = _prolong(h, pb, m, W, C)
+    finally:
+        P.pase_destroy(h)
+    rng = np.random.default_rng(m)
+    rows = list(rng.choice(pb.N, size=6, replace=False)) + [pb.N - 1, 0] + list(np.flatnonzero(np.abs(W).max(axis=1) < 1e-300))
+    _check_bound(pb, W, C, U, rows)
+
+
+def test_split_and_fp64_kernels_agree(p3d):
+    """The two kernels behind split_gemm = 1 and 0 give the same product to the bound."""
+    pb, m = p3d, 56
+    W, C = _operands(pb.N, m, 7)
+    out = {}
+    for split in (1, 0):
+        h = _handle(pb, split)
+        try:
+            out[split] = _prolong(h, pb, m, W, C)
+        finally:
+            P.pase_destroy(h)
+    scale = np.abs(W).max(axis=1)[:, None] * np.abs(C).max(axis=0)[None, :]
+    K = m
+    tol = (8 + 2 * K) * U53 * scale + 2 * U53 * np.abs(out[0]) + 2 * K * 2.0 ** -1074
+    assert np.all(np.abs(out[1] - out[0]) <= tol)
+    # on O(1) random blocks the split product is at least as close to exact as FP64
+    Wr, Cr = pin.start_vectors(3, pb.N, m), pin.start_vectors(4, m, m)
+    res = {}
+    for split in (1, 0):
+        h = _handle(pb, split)
+        try:
+            res[split] = _prolong(h, pb, m, Wr, Cr)
+        finally:
+            P.pase_destroy(h)
+    rows = range(0, pb.N, 997)
+    exact = np.array([[float(sum(Fraction(float(Wr[r, k])) * Fraction(float(Cr[k, j])) for k in range(K)))
+                       for j in range(m)] for r in rows])
+    e_split = np.abs(res[1][list(rows)] - exact).max()
+    e_fp64 = np.abs(res[0][list(rows)] - exact).max()
+    assert e_split <= 2 * e_fp64 + 1e-300, (e_split, e_fp64)
+
+
+def test_split_nonfinite_rows_and_columns(p3d):
+    """Inf/NaN in a row of W or a column of C_W come out as in an FP64 product."""
+    pb, m = p3d, 24
+    W, C = _operands(pb.N, m, 11)
+    W[5, 3] = np.nan
+    W[200, 0] = np.inf
+    C[2, 7] = -np.inf
+    h = _handle(pb, 1)
+    try:
+        U = _prolong(h, pb, m, W, C)
+    finally:
+        P.pase_destroy(h)
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = W @ C
+    assert np.array_equal(np.isnan(U), np.isnan(ref))
+    assert np.array_equal(np.isposinf(U), np.isposinf(ref))
+    assert np.array_equal(np.isneginf(U), np.isneginf(ref))
+    fin = np.isfinite(ref)
+    scale = np.abs(np.where(np.isfinite(W), W, 0)).max(axis=1)[:, None] * \
+        np.abs(np.where(np.isfinite(C), C, 0)).max(axis=0)[None, :]
+    assert np.all(np.abs(U - ref)[fin] <= ((8 + 2 * m) * U53 * scale + 2 * U53 * np.abs(ref) + 2 * m * 2.0 ** -1074)[fin])
+
+
+def test_split_kernel_timing_entry(p3d):
+    """pase_time_kernel runs the split kernel for m <= 64 and refuses wider blocks."""
+    pb = p3d
+    h = _handle(pb, 1)
+    try:
+        P.pase_reserve(h, 56)
+        assert P.pase_time_kernel(h, "prolong_split", 56, 2) > 0.0
+    finally:
+        P.pase_destroy(h)
+    h = _handle(pb, 1)
+    try:
+        P.pase_reserve(h, 72)
+        with pytest.raises(P.PaseError):
+            P.pase_time_kernel(h, "prolong_split", 72, 2)
+    finally:
+        P.pase_destroy(h)
