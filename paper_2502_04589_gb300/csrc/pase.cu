@@ -1236,7 +1236,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   if (kernel < 0 || kernel > PASE_KERNEL_PROLONG_SPLIT)
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
-    return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 64");
+    return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
   // deterministic operands
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 8u, w.R));

@@ -250,8 +250,8 @@ int launch_relres(pase_ctx* h, int m, const double* norms, const double* lam, do
 // dense tall-skinny
 int ts_gram(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int ldx, const double* Y,
             int ldy, double* G, int ldg, bool sym);  // G = X^T Y (k1 x k2)
-// Y = X C on the BF16 tensor cores with FP64 accuracy (split_gemm.cu); k1 even <= 64,
-// k2 <= 64, 16-byte aligned rows.  err: device flag set if a tensor-core wait runs out.
+// Y = X C on the BF16 tensor cores with FP64 accuracy (split_gemm.cu); k1, k2 even <= 128,
+// 16-byte aligned rows.  err: device flag set if a tensor-core wait runs out.
 bool ts_gemm_split_ok(int k1, int k2, const void* X, int64_t ldx, const void* Y, int64_t ldy);
 int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C, int ldc,
                   double* Y, int64_t ldy, int* err);

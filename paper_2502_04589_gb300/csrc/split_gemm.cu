@@ -1,5 +1,6 @@
-// Y = X C for a tall block X [n][k1] and a small C [k1][k2] (k1, k2 <= 64) on the BF16
-// tensor cores with FP64 accuracy: the prolongation W C_W of Alg. 3 step 6.
+// Y = X C for a tall block X [n][k1] and a small C [k1][k2] (k1, k2 <= 128, even) on the
+// BF16 tensor cores with FP64 accuracy: the prolongation W C_W of Alg. 3 step 6.  One
+// launch covers k1, k2 <= 64; wider products run as 64-wide blocks.
 //
 // Error-free splitting (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication", Numer.
@@ -125,8 +126,8 @@ __device__ __forceinline__ double sg_to_double(int64_t T, int X) {
 template <int KP>
 __global__ void __launch_bounds__(kSgThreads, 1)
     k_ts_gemm_split(int64_t n, int k1, int k2, int np, const double* __restrict__ X, int64_t ldx,
-                    const double* __restrict__ C, int ldc, double* __restrict__ Y, int64_t ldy, uint32_t tmem_cols,
-                    int* __restrict__ err) {
+                    const double* __restrict__ C, int ldc, double* __restrict__ Y, int64_t ldy, int beta,
+                    uint32_t tmem_cols, int* __restrict__ err) {
   static_assert(KP % 16 == 0 && KP <= 64, "K tile");
   constexpr int KH = KP / 2;  // K values per thread in the load phase
   extern __shared__ __align__(1024) uint8_t sg_smem[];
@@ -282,6 +283,11 @@ __global__ void __launch_bounds__(kSgThreads, 1)
           }
         }
         double* yr = Y + row * ldy + c0;
+        if (beta) {  // Y += X C (a second K block of a wider product)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c0 + c < k2) out[c] += yr[c];
+        }
         if (c0 + 8 <= k2) {
 #pragma unroll
           for (int c = 0; c < 8; c += 2) *reinterpret_cast<double2*>(yr + c) = make_double2(out[c], out[c + 1]);
@@ -300,14 +306,13 @@ __global__ void __launch_bounds__(kSgThreads, 1)
 }
 
 bool ts_gemm_split_ok(int k1, int k2, const void* X, int64_t ldx, const void* Y, int64_t ldy) {
-  return k1 >= 2 && k1 <= 64 && k2 >= 1 && k2 <= 64 && (k1 % 2) == 0 && (ldx % 2) == 0 && (ldy % 2) == 0 &&
-         ((uintptr_t)X % 16) == 0 && ((uintptr_t)Y % 16) == 0;
+  return k1 >= 2 && k1 <= 128 && k2 >= 1 && k2 <= 128 && (k1 % 2) == 0 && (k2 % 2) == 0 && (ldx % 2) == 0 &&
+         (ldy % 2) == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)Y % 16) == 0;
 }
 
-int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C, int ldc,
-                  double* Y, int64_t ldy, int* err) {
-  if (n == 0 || k2 == 0) return PASE_OK;
-  if (!ts_gemm_split_ok(k1, k2, X, ldx, Y, ldy)) return fail(PASE_ERR_INVALID_ARG, "ts_gemm_split: unsupported shape");
+// one launch: k1, k2 <= 64
+static int split_launch(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C,
+                        int ldc, double* Y, int64_t ldy, int beta, int* err) {
   const int kp = (k1 + 15) / 16 * 16, np = (k2 + 15) / 16 * 16;
   uint32_t cols = 32;
   while (cols < (uint32_t)(8 * np)) cols <<= 1;
@@ -324,22 +329,41 @@ int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64
     default: fn = (const void*)k_ts_gemm_split<64>; break;
   }
   PASE_TRY(ensure_max_smem(fn, 200 * 1024));  // the largest request of any shape (192 KB)
+#define PASE_SG_LAUNCH(KP)                                                                                      \
+  k_ts_gemm_split<KP><<<grid, kSgThreads, smem, h->stream>>>(n, k1, k2, np, X, ldx, C, ldc, Y, ldy, beta, cols, \
+                                                              err)
   switch (kp) {
-    case 16:
-      k_ts_gemm_split<16><<<grid, kSgThreads, smem, h->stream>>>(n, k1, k2, np, X, ldx, C, ldc, Y, ldy, cols, err);
-      break;
-    case 32:
-      k_ts_gemm_split<32><<<grid, kSgThreads, smem, h->stream>>>(n, k1, k2, np, X, ldx, C, ldc, Y, ldy, cols, err);
-      break;
-    case 48:
-      k_ts_gemm_split<48><<<grid, kSgThreads, smem, h->stream>>>(n, k1, k2, np, X, ldx, C, ldc, Y, ldy, cols, err);
-      break;
-    default:
-      k_ts_gemm_split<64><<<grid, kSgThreads, smem, h->stream>>>(n, k1, k2, np, X, ldx, C, ldc, Y, ldy, cols, err);
-      break;
+    case 16: PASE_SG_LAUNCH(16); break;
+    case 32: PASE_SG_LAUNCH(32); break;
+    case 48: PASE_SG_LAUNCH(48); break;
+    default: PASE_SG_LAUNCH(64); break;
   }
+#undef PASE_SG_LAUNCH
   h->launches++;
   PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// Widths above 64 in blocks of at most 64 (even sizes): Y[:, nb] = sum over K blocks kb of
+// X[:, kb] C[kb, nb], the K blocks after the first added to Y in FP64 (one more rounding).
+int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C, int ldc,
+                  double* Y, int64_t ldy, int* err) {
+  if (n == 0 || k2 == 0) return PASE_OK;
+  if (!ts_gemm_split_ok(k1, k2, X, ldx, Y, ldy)) return fail(PASE_ERR_INVALID_ARG, "ts_gemm_split: unsupported shape");
+  auto blocks = [](int k) {  // 1 or 2 blocks of even size <= 64
+    if (k <= 64) return std::make_pair(k, 0);
+    const int a = ((k / 2) + 1) & ~1;
+    return std::make_pair(a, k - a);
+  };
+  const auto kb = blocks(k1), nb = blocks(k2);
+  const int ks[2] = {kb.first, kb.second}, ns[2] = {nb.first, nb.second};
+  int n0 = 0;
+  for (int j = 0; j < 2 && ns[j] > 0; n0 += ns[j], ++j) {
+    int k0 = 0;
+    for (int i = 0; i < 2 && ks[i] > 0; k0 += ks[i], ++i)
+      PASE_TRY(split_launch(h, n, ks[i], ns[j], X + k0, ldx, C + (int64_t)k0 * ldc + n0, ldc, Y + n0, ldy,
+                            i > 0 ? 1 : 0, err));
+  }
   return PASE_OK;
 }
 

@@ -9,7 +9,8 @@ where W C_W is exact: rational arithmetic on sampled entries, and elsewhere the 
 oracle product with its own error bound K u sum_k |w_rk||c_kj| added.  Inputs stress the
 scaling: rows at 2^-40..2^40, entries spread over 2^60 inside a row, zero rows,
 subnormal entries, a ragged last tile (N = 31^3 is not a multiple of 128), every padded
-width K, N in {16, 32, 48, 64} and a width above 64 (the FP64 kernel).
+width K, N in {16, 32, 48, 64}, widths 72-128 (two K and N blocks) and 136 (the FP64
+kernel).
 """
 from fractions import Fraction
 
@@ -68,13 +69,14 @@ def _prolong(h, pb, m, W, C):
 
 
 def _check_bound(pb, W, C, U, sample_rows):
-    """The split bound for K <= 64; wider blocks run the FP64 kernel, whose error bound
-    is the usual K u sum_k |w_rk||c_kj| (kept in `scale`)."""
+    """The split bound; widths above 64 add two K blocks in FP64 (twice the bound plus one
+    rounding); above 128 the FP64 kernel runs, with the usual K u sum_k |w_rk||c_kj|."""
     K = W.shape[1]
-    if K <= 64:
-        scale = np.abs(W).max(axis=1)[:, None] * np.abs(C).max(axis=0)[None, :]
-    else:
+    scale = np.abs(W).max(axis=1)[:, None] * np.abs(C).max(axis=0)[None, :]
+    if K > 128:
         scale = (K / 8.0) * (np.abs(W) @ np.abs(C))
+    elif K > 64:
+        scale = 2.0 * scale + np.abs(W) @ np.abs(C) / 8.0
     ref = opase.prolongate(pb.P, W, np.zeros((pb.N_H, K)), C)
     refbound = K * U53 * (np.abs(W) @ np.abs(C))                # the oracle's own rounding
     err = np.abs(U - ref)
@@ -87,7 +89,7 @@ def _check_bound(pb, W, C, U, sample_rows):
             assert e <= Fraction(8 * U53) * Fraction(float(scale[r, j])) + Fraction(U53) * abs(ex) + Fraction(tiny), (r, j)
 
 
-@pytest.mark.parametrize("m", [8, 16, 24, 40, 56, 64, 72])
+@pytest.mark.parametrize("m", [8, 16, 24, 40, 56, 64, 72, 112, 128, 136])
 def test_split_product_error_bound(p3d, m):
     pb = p3d
     h = _handle(pb, 1)
@@ -157,7 +159,7 @@ def test_split_nonfinite_rows_and_columns(p3d):
 
 
 def test_split_kernel_timing_entry(p3d):
-    """pase_time_kernel runs the split kernel for m <= 64 and refuses wider blocks."""
+    """pase_time_kernel runs the split kernel for m <= 128 and refuses wider blocks."""
     pb = p3d
     h = _handle(pb, 1)
     try:
@@ -167,8 +169,8 @@ def test_split_kernel_timing_entry(p3d):
         P.pase_destroy(h)
     h = _handle(pb, 1)
     try:
-        P.pase_reserve(h, 72)
+        P.pase_reserve(h, 136)
         with pytest.raises(P.PaseError):
-            P.pase_time_kernel(h, "prolong_split", 72, 2)
+            P.pase_time_kernel(h, "prolong_split", 136, 2)
     finally:
         P.pase_destroy(h)
