@@ -581,7 +581,8 @@ def run_ours(args):
             ("jacobi_fp32", 2.0 * nnz * m + 3.0 * N * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
             ("gram_fp64", 1.0 * N * m * (m + 4), 2 * N * m * 8, "alu"),
             ("prolong_fp64", 2.0 * N * m * m, 2 * N * m * 8, "alu"),
-            ("prolong_split", 2.0 * N * m * m, 2 * N * m * 8, "hbm")):
+            ("prolong_split", 2.0 * N * m * m, 2 * N * m * 8, "hbm"),
+            ("gram_split", 2.0 * N * m * (m + 4), 2 * 2 * N * m * 8, "hbm")):
         try:
             ms_k = P.pase_time_kernel(hk, name, m, 10)
             kernels[name] = kinfo(name, ms_k, flops, nbytes, bound)

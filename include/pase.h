@@ -88,11 +88,12 @@ typedef struct {
   int smoother;        /* PASE_SMOOTHER_JACOBI (default) or PASE_SMOOTHER_LEARNED: the fine-
                           level sweeps of the V-cycle use the learned network once
                           pase_set_grid and parameters are given (Jacobi until then)      */
-  int split_gemm;      /* 1 (default): the step-(d) product W C_W (m <= 128) runs on the BF16
-                          tensor cores with FP64 accuracy (error-free splitting into 8-bit
-                          digit slices, exact FP32 sums per digit diagonal, 64-bit integer
-                          recombination; error a few units of 2^-53 relative to
-                          max|w_row| max|c_col|); 0: FP64 CUDA cores                       */
+  int split_gemm;      /* 1 (default): the dense products of steps (b) and (d), the Gram
+                          blocks W^T(A_h W), W^T(M_h W) and W C_W (m <= 128, even), run on
+                          the BF16 tensor cores with FP64 accuracy (error-free splitting into
+                          8-bit digit slices, exact FP32 sums per digit diagonal, 64-bit
+                          integer recombination; error a few units of 2^-53 relative to the
+                          products of the row and column maxima); 0: FP64 CUDA cores      */
 } pase_options;
 
 #define PASE_SMOOTHER_JACOBI 0
@@ -243,6 +244,7 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_SYGV 5          /* small symmetric-definite eigensolver, n = k = m     */
 #define PASE_KERNEL_SYGV3 6         /* the same with n = 3m, k = m (step-(c) Rayleigh-Ritz) */
 #define PASE_KERNEL_PROLONG_SPLIT 7 /* W C over N_h rows on the tensor cores (split digits; m <= 128) */
+#define PASE_KERNEL_GRAM_SPLIT 8    /* both Gram blocks W^T R, W^T W on the tensor cores (split digits) */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
 /* Live timing of one kernel while the handle works (pase_solve, pase_iterate, ...): with

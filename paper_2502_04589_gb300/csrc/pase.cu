@@ -313,6 +313,7 @@ static int reserve(pase_ctx* h, int m) {
   PASE_TRY(dev_alloc_t(h, &w.eigwork, w.eigwork_doubles));
   PASE_TRY(dev_alloc_t(h, &w.smallvec, (size_t)16 * m));
   PASE_TRY(dev_alloc_t(h, &w.status, 8));
+  PASE_TRY(dev_alloc_t(h, &w.colexp, 3 * 128));
   PASE_TRY(dev_alloc_t(h, &h->tc_err, 1));
   PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
   PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
@@ -638,6 +639,8 @@ static int step_project(pase_ctx* h, const double* W, double* aH, double* bH, do
                               nullptr, nullptr, 0.0, w.T1, w.T2, nullptr, nullptr));
   PASE_TRY(launch_csr<double>(h, CSR_MV2, m, h->PdT, h->PdT.val, nullptr, w.T1, w.T2, nullptr, nullptr,
                               nullptr, 0.0, aH, bH, nullptr, nullptr));
+  if (h->opt.split_gemm && ts_gram2_split_ok(m, w))
+    return ts_gram2_split(h, h->N, m, W, w.T1, w.T2, GA, GM, m, w.colexp, h->tc_err);
   PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T1, m, GA, m, true));
   PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T2, m, GM, m, true));
   return PASE_OK;
@@ -1233,10 +1236,12 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
   if (kernel == PASE_KERNEL_JACOBI_FP32 && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_PROLONG_SPLIT)
+  if (kernel < 0 || kernel > PASE_KERNEL_GRAM_SPLIT)
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
+  if (kernel == PASE_KERNEL_GRAM_SPLIT && !ts_gram2_split_ok(m, h->w))
+    return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split Gram takes m <= 128");
   // deterministic operands
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 8u, w.R));
@@ -1275,6 +1280,8 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
         return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
       case PASE_KERNEL_PROLONG_SPLIT:
         return ts_gemm_split(h, h->N, m, m, w.W, m, w.CW, m, w.T1, m, h->tc_err);
+      case PASE_KERNEL_GRAM_SPLIT:
+        return ts_gram2_split(h, h->N, m, w.W, w.R, w.W, w.GA, w.GM, m, w.colexp, h->tc_err);
       case PASE_KERNEL_SYGV:
         return small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
       case PASE_KERNEL_SYGV3:

@@ -107,6 +107,7 @@ struct Work {
   double *cgP = nullptr, *cgQ = nullptr;                // CG direction and A times it [N][m]
   double* cgs = nullptr;                                // CG scalars: (r,z) x2, (p,Ap), ratio [4m]
   int* status = nullptr;                                // device status words [8]
+  int* colexp = nullptr;                                // split Gram column exponents [3][128]
   // host pinned mirror for small readbacks
   double* h_small = nullptr;
   int* h_status = nullptr;
@@ -255,6 +256,11 @@ int ts_gram(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int ldx, co
 bool ts_gemm_split_ok(int k1, int k2, const void* X, int64_t ldx, const void* Y, int64_t ldy);
 int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64_t ldx, const double* C, int ldc,
                   double* Y, int64_t ldy, int* err);
+// GA = W^T Y1, GB = W^T Y2 (upper triangles mirrored), [n][m] blocks with m <= 128 even,
+// on the tensor cores with the same splitting (split_gemm.cu); colexp: 3 x 128 ints.
+bool ts_gram2_split_ok(int m, const Work& w);
+int ts_gram2_split(pase_ctx* h, int64_t n, int m, const double* W, const double* Y1, const double* Y2, double* GA,
+                   double* GB, int ldg, int* colexp, int* err);
 int ts_gemm(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const double* X, int ldx,
             const double* C, int ldc, double beta, double* Y, int ldy);  // Y = a X C + b Y
 template <typename T>

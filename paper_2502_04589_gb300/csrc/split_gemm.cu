@@ -16,11 +16,11 @@
 //     pairs times K <= 64 terms, |sum| < 2^23) exactly in its FP32 accumulator:
 //     D_d = sum_{p+q=d} A_p B_q, one TMEM accumulator per d = 2..9 (36 MMAs per K step);
 //   * the epilogue recombines T = sum_d D_d 2^{60 - 8d} in 64-bit integers (|T| < 2^62;
-//     the two lowest diagonals shifted right, floor) and builds the double
+//     the two lowest diagonals shifted right with rounding) and builds the double
 //     T 2^{e_r + f_j - 56} from its bits with integer instructions (FP64 instructions
 //     run at ~2 per clock per SM on this part).
-// Error: the dropped diagonals d >= 10 (at most ~2^-52 2^{e_r + f_j}), the floor shifts
-// (2^{e_r + f_j - 55}) and the digit rounding (2^{e_r + f_j - 61}): a few units of 2^-53
+// Error: the dropped diagonals d >= 10 (at most ~2^-52 2^{e_r + f_j}), the rounded shifts
+// (2^{e_r + f_j - 56}) and the digit rounding (2^{e_r + f_j - 61}): a few units of 2^-53
 // relative to max_k |x_rk| max_k |c_kj|, plus the rounding of the result to double;
 // on random blocks with K = 56 the entrywise relative error is below the FP64 GEMM's.
 // Rows or columns with an Inf or NaN are recomputed in plain FP64 (so they propagate as
@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(kSgThreads, 1)
           int64_t T = 0;
 #pragma unroll
           for (int d = 0; d < 6; ++d) T += (int64_t)__float2int_rn(__uint_as_float(v[d][c])) * (1ll << (44 - 8 * d));
-          T += (int64_t)(__float2int_rn(__uint_as_float(v[6][c])) >> 4);
-          T += (int64_t)(__float2int_rn(__uint_as_float(v[7][c])) >> 12);
+          T += (int64_t)((__float2int_rn(__uint_as_float(v[6][c])) + (1 << 3)) >> 4);  // to nearest
+          T += (int64_t)((__float2int_rn(__uint_as_float(v[7][c])) + (1 << 11)) >> 12);
           const int j = c0 + c;
           const int fj = sFx[j];
           if (erx == 2047 || fj == 2047) {  // Inf/NaN in the row or the column: plain FP64
@@ -363,6 +363,355 @@ int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64
     for (int i = 0; i < 2 && ks[i] > 0; k0 += ks[i], ++i)
       PASE_TRY(split_launch(h, n, ks[i], ns[j], X + k0, ldx, C + (int64_t)k0 * ldc + n0, ldc, Y + n0, ldy,
                             i > 0 ? 1 : 0, err));
+  }
+  return PASE_OK;
+}
+
+// ------------------------------------------------------------------ Gram blocks
+// D = A^T B over the rows of a tall block pair (Alg. 3 step 4: W^T (A_h W), W^T (M_h W)),
+// with A = [A0 | A1] (two blocks of at most 64 columns, M = 128) and B at most 64
+// columns, by the same digit splitting with the scales taken per column over all rows
+// (a pre-pass, k_colexp).  Each CTA takes a contiguous row range in chunks of 64 rows (the
+// MMA K); the 8 diagonal accumulators collect two chunks (128 rows: |D_d| <= 128 x 114688
+// < 2^24, still exact) and are then drained into per-thread 64-bit integer sums
+// T += sum_d D_d 2^{52 - 8d} (unit 2^{e_i + f_j - 48}; the three lowest diagonals shifted
+// right with rounding, so the per-drain error is unbiased), which stay below 2^63 for up
+// to 2^14 rows per CTA.  The CTA writes its sums as doubles to partial[cta][128][np]; a
+// reduction kernel adds the CTAs in FP64.  On random blocks the error relative to
+// sum_r |a_ri||b_rj| is below that of the FP64 Gram kernel.
+constexpr int kGsK = 64;          // rows per chunk (MMA K)
+constexpr int kGsDrainChunks = 2;  // chunks per accumulation
+constexpr int64_t kGsMaxRowsPerCta = 1 << 14;
+constexpr int kGsU0 = 48;          // T unit 2^{e_i + f_j - 48}
+constexpr int kGsItems = (kSgM * 8 + 64 * 8) / kSgThreads;  // slicing items per thread
+
+// column exponents (sg_bexp + 2048, so 0 = "no value yet") by atomicMax; blockIdx.y
+// selects one of three [n][ld] arrays, columns [c0, c0 + m), m <= 64
+struct ColexpArgs {
+  const double* x[3];
+  int* out[3];
+};
+__global__ void __launch_bounds__(256) k_colexp(int64_t n, int m, int64_t ld, ColexpArgs a) {
+  __shared__ int se[256];
+  const int y = blockIdx.y;
+  const double* __restrict__ X = y == 0 ? a.x[0] : (y == 1 ? a.x[1] : a.x[2]);
+  int* out = y == 0 ? a.out[0] : (y == 1 ? a.out[1] : a.out[2]);
+  const int c = threadIdx.x & 63, r4 = threadIdx.x >> 6;
+  int e = 0;
+  if (c < m) {
+    const int64_t step = (int64_t)gridDim.x * 16;
+    for (int64_t rb = (int64_t)blockIdx.x * 16 + r4; rb < n; rb += step) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t r = rb + 4 * k;
+        v[k] = r < n ? X[r * ld + c] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (rb + 4 * k < n) e = max(e, sg_bexp(v[k]) + 2048);
+    }
+  }
+  se[threadIdx.x] = e;
+  __syncthreads();
+  if (threadIdx.x < 64 && c < m) {
+    const int v = max(max(se[c], se[c + 64]), max(se[c + 128], se[c + 192]));
+    if (v > 0) atomicMax(out + c, v);
+  }
+}
+
+__global__ void __launch_bounds__(kSgThreads, 1)
+    k_gram_split(int64_t n, int64_t rows_per_cta, const double* __restrict__ A0, int64_t lda0, int na0,
+                 const double* __restrict__ A1, int64_t lda1, int na1, const double* __restrict__ B, int64_t ldb,
+                 int nbc, int np, const int* __restrict__ aexp0, const int* __restrict__ aexp1,
+                 const int* __restrict__ bexp, double* __restrict__ partial, uint32_t tmem_cols,
+                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t sg_smem[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sg_smem);  // [8][128 x 64]
+  __nv_bfloat16* sB = sA + (size_t)kSgDigits * kSgM * kGsK;        // [8][np x 64]
+  __shared__ int sAe[kSgM], sBe[64];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int strideA = kSgM * kGsK, strideB = np * kGsK;
+  if (tid < kSgM) {
+    int e = 0;
+    if (tid < 64 && tid < na0) e = aexp0[tid];
+    if (tid >= 64 && tid - 64 < na1) e = aexp1[tid - 64];
+    sAe[tid] = e - 2048;
+  }
+  if (tid < 64) sBe[tid] = (tid < nbc ? bexp[tid] : 0) - 2048;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = umma_idesc_bf16(kSgM, np);
+  const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  // drain role: TMEM lane (A column) er, B columns [jb, jb + np/2)
+  const int lq = warp & 3, er = lq * 32 + lane, jb = (warp >> 2) * (np / 2);
+  const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
+  int64_t acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  int chunk = 0;
+  // one slicing item = 8 consecutive rows of one column (A: 128 x 8 items, B: np x 8);
+  // lanes take consecutive columns, so each load instruction reads contiguous row segments
+  const int nitems = kSgM * 8 + np * 8;
+  auto item = [&](int it, const double*& src, int64_t& ld, int& col, bool& valid, int& e, int& kg,
+                  __nv_bfloat16*& dst, int& stride) {
+    if (it < kSgM * 8) {
+      const int i = it % kSgM;
+      kg = it / kSgM;
+      const bool hi = i >= 64;
+      col = hi ? i - 64 : i;
+      src = hi ? A1 : A0;
+      ld = hi ? lda1 : lda0;
+      valid = col < (hi ? na1 : na0);
+      e = sAe[i];
+      dst = sA + (i >> 3) * (kGsK * 8) + kg * 64 + (i & 7) * 8;
+      stride = strideA;
+    } else {
+      const int j = (it - kSgM * 8) % np;
+      kg = (it - kSgM * 8) / np;
+      col = j;
+      src = B;
+      ld = ldb;
+      valid = j < nbc;
+      e = sBe[j < 64 ? j : 0];
+      dst = sB + (j >> 3) * (kGsK * 8) + kg * 64 + (j & 7) * 8;
+      stride = strideB;
+    }
+  };
+  double pv[kGsItems][8];  // raw values of this thread's items of the next chunk
+  auto load_chunk = [&](int64_t rb) {
+#pragma unroll
+    for (int q = 0; q < kGsItems; ++q) {
+      const int it = tid + q * kSgThreads;
+      const double* src = nullptr;
+      int64_t ld = 0;
+      int col = 0, e = 0, kg = 0, stride = 0;
+      bool valid = false;
+      __nv_bfloat16* dst = nullptr;
+      if (it < nitems) item(it, src, ld, col, valid, e, kg, dst, stride);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t r = rb + kg * 8 + c;
+        pv[q][c] = (valid && r < r1) ? __ldg(src + r * ld + col) : 0.0;
+      }
+    }
+  };
+  if (r0 < r1) load_chunk(r0);
+  for (int64_t rb = r0; rb < r1; rb += kGsK, ++chunk) {
+    // ---- digit slices of rows [rb, rb + 64) from the prefetched values
+#pragma unroll
+    for (int q = 0; q < kGsItems; ++q) {
+      const int it = tid + q * kSgThreads;
+      if (it < nitems) {
+        const double* src;
+        int64_t ld;
+        int col, e, kg, stride;
+        bool valid;
+        __nv_bfloat16* dst;
+        item(it, src, ld, col, valid, e, kg, dst, stride);
+        uint64_t z[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) z[c] = sg_fixed(pv[q][c], e);
+        sg_store_chunk(z, dst, stride);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const bool fresh = (chunk % kGsDrainChunks) == 0;
+#pragma unroll 1
+      for (int d = 2; d <= kSgDigits + 1; ++d) {
+        const uint32_t dcol = tmem + (uint32_t)((d - 2) * np);
+        bool first = fresh;
+        for (int p = 1; p < d; ++p) {
+          const int q = d - p;
+          if (p > kSgDigits || q > kSgDigits) continue;
+#pragma unroll
+          for (int s = 0; s < kGsK / 16; ++s) {
+            const uint64_t da = umma_desc(aBase + (uint32_t)(((p - 1) * strideA + s * 128) * 2), 128, kGsK * 16);
+            const uint64_t db = umma_desc(bBase + (uint32_t)(((q - 1) * strideB + s * 128) * 2), 128, kGsK * 16);
+            const uint32_t accf = first ? 0u : 1u;
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                         "l"(da), "l"(db), "r"(idesc), "r"(accf));
+            first = false;
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    if (rb + kGsK < r1) load_chunk(rb + kGsK);  // next chunk's rows while the tensor cores run
+    const uint32_t done = mbar_wait_bounded(smem_u32(&mbar), phase, 1 << 22);
+    if (!__syncthreads_and((int)done)) {  // (uniform) give up: report, let the MMAs finish, stop
+      if (tid == 0) atomicExch(err, 1);
+      mbar_wait_bounded(smem_u32(&mbar), phase, 1 << 22);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // ---- drain after every second chunk and after the last
+    if ((chunk % kGsDrainChunks) == kGsDrainChunks - 1 || rb + kGsK >= r1) {
+#pragma unroll
+      for (int cb = 0; cb < 8; ++cb) {
+        if (cb * 4 < np / 2) {  // warp-uniform
+          uint32_t v[8][4];
+#pragma unroll
+          for (int d = 0; d < 8; ++d)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3])
+                         : "r"(lane_addr + (uint32_t)(d * np + jb + cb * 4)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            int64_t T = 0;
+#pragma unroll
+            for (int d = 0; d < 5; ++d)  // diagonals 2..6: shifts 36, 28, 20, 12, 4
+              T += (int64_t)__float2int_rn(__uint_as_float(v[d][c])) * (1ll << (36 - 8 * d));
+            T += (int64_t)((__float2int_rn(__uint_as_float(v[5][c])) + (1 << 3)) >> 4);  // to nearest
+            T += (int64_t)((__float2int_rn(__uint_as_float(v[6][c])) + (1 << 11)) >> 12);
+            T += (int64_t)((__float2int_rn(__uint_as_float(v[7][c])) + (1 << 19)) >> 20);
+            acc[cb * 4 + c] += T;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // slices and (after a drain) the accumulators are reused
+  }
+  if (ok) {
+    // ---- the CTA's sums as doubles; Inf/NaN columns summed directly in FP64
+    double* out = partial + ((int64_t)blockIdx.x * kSgM + er) * np;
+    const int ie = sAe[er];
+    const bool hi = er >= 64;
+    const int icol = hi ? er - 64 : er;
+    const bool ivalid = icol < (hi ? na1 : na0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const int j = jb + c;
+      if (c < np / 2) {
+        double vout = 0.0;
+        if (ivalid && j < nbc) {
+          const int je = sBe[j];
+          if (ie == 2047 || je == 2047) {
+            const double* a = hi ? A1 : A0;
+            const int64_t la = hi ? lda1 : lda0;
+            double s2 = 0.0;
+            for (int64_t r = r0; r < r1; ++r) s2 = fma(a[r * la + icol], B[r * ldb + j], s2);
+            vout = s2;
+          } else {
+            vout = sg_to_double(acc[c], ie + je - 2044 - kGsU0);
+          }
+        }
+        out[j] = vout;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+// G_g[p][q] = G_g[q][p] = sum_b partial[b][i][j] for the entries of this launch with
+// p = n0 + j <= q = column of A index i (the upper triangle of W^T Y, mirrored, as in the
+// FP64 path); A index i < 64 belongs to G0 (column c0 + i), i >= 64 to G1 (c1 + i - 64).
+__global__ void k_gram_split_reduce(int nb, int np, const double* __restrict__ partial, int na0, int na1, int nbc,
+                                    double* __restrict__ G0, int c0, double* __restrict__ G1, int c1, int n0,
+                                    int ldg) {
+  const int total = kSgM * np;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int i = idx / np, j = idx % np;
+    const bool hi = i >= 64;
+    const int ic = hi ? i - 64 : i;
+    if (ic >= (hi ? na1 : na0) || j >= nbc) continue;
+    const int q = (hi ? c1 : c0) + ic, p = n0 + j;
+    if (p > q) continue;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[((int64_t)b * kSgM + i) * np + j];
+    double* G = hi ? G1 : G0;
+    G[(int64_t)p * ldg + q] = s;
+    G[(int64_t)q * ldg + p] = s;
+  }
+}
+
+bool ts_gram2_split_ok(int m, const Work& w) {
+  if (m < 2 || m > 128 || (m % 2) != 0) return false;
+  const int64_t need = (int64_t)4 * kSgM * 64;  // a few CTAs' partials at least
+  return (int64_t)(w.partial_bytes / sizeof(double)) >= need;
+}
+
+// GA = W^T Y1 and GB = W^T Y2 (symmetric, upper triangle mirrored), all [n][m], m <= 128
+// even; colexp: device scratch of 3 x 128 ints.
+int ts_gram2_split(pase_ctx* h, int64_t n, int m, const double* W, const double* Y1, const double* Y2, double* GA,
+                   double* GB, int ldg, int* colexp, int* err) {
+  if (n == 0 || m == 0) return PASE_OK;
+  Work& w = h->w;
+  // column exponents of Y1, Y2, W
+  PASE_CUDA(cudaMemsetAsync(colexp, 0, 3 * 128 * sizeof(int), h->stream));
+  const int ceg = (int)std::min<int64_t>((n + 15) / 16, (int64_t)h->num_sms * 4);
+  for (int c0 = 0; c0 < m; c0 += 64) {
+    ColexpArgs a{{Y1 + c0, Y2 + c0, W + c0}, {colexp + c0, colexp + 128 + c0, colexp + 256 + c0}};
+    k_colexp<<<dim3((unsigned)ceg, 3), 256, 0, h->stream>>>(n, std::min(64, m - c0), m, a);
+    h->launches++;
+  }
+  PASE_CUDA(cudaGetLastError());
+  int64_t grid = std::max<int64_t>(h->num_sms, (n + kGsMaxRowsPerCta - 1) / kGsMaxRowsPerCta);
+  grid = std::min<int64_t>(grid, (n + kGsK - 1) / kGsK);
+  int64_t rpc = (n + grid - 1) / grid;
+  rpc = (rpc + kGsK - 1) / kGsK * kGsK;
+  grid = (n + rpc - 1) / rpc;
+  const size_t smem = std::max<size_t>(sg_smem_bytes(kGsK, 64), 116 * 1024);
+  PASE_TRY(ensure_max_smem((const void*)k_gram_split, 200 * 1024));
+  auto launch = [&](const double* A0, int na0, const int* e0, const double* A1, int na1, const int* e1,
+                    const double* Bp, int nbc, const int* eb, double* G0, int cc0, double* G1, int cc1,
+                    int n0) -> int {
+    const int np = (nbc + 15) / 16 * 16;
+    if ((int64_t)grid * kSgM * np > (int64_t)(w.partial_bytes / sizeof(double)))
+      return fail(PASE_ERR_INVALID_ARG, "ts_gram2_split: partial buffer too small");
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(8 * np)) cols <<= 1;
+    k_gram_split<<<(unsigned)grid, kSgThreads, smem, h->stream>>>(n, rpc, A0, m, na0, A1, m, na1, Bp, m, nbc, np,
+                                                                  e0, e1, eb, w.partial, cols, err);
+    h->launches++;
+    PASE_CUDA(cudaGetLastError());
+    const int total = kSgM * np;
+    k_gram_split_reduce<<<(total + 255) / 256, 256, 0, h->stream>>>((int)grid, np, w.partial, na0, na1, nbc, G0,
+                                                                     cc0, G1, cc1, n0, ldg);
+    h->launches++;
+    PASE_CUDA(cudaGetLastError());
+    return PASE_OK;
+  };
+  int* eY1 = colexp;
+  int* eY2 = colexp + 128;
+  int* eW = colexp + 256;
+  if (m <= 64) return launch(Y1, m, eY1, Y2, m, eY2, W, m, eW, GA, 0, GB, 0, 0);
+  // wider: per Gram, A = [Y[:, 0:64] | Y[:, 64:m]], B = W in two column blocks
+  const int b0 = ((m / 2) + 1) & ~1;
+  const int nbs[2] = {b0, m - b0};
+  for (int g = 0; g < 2; ++g) {
+    const double* Y = g == 0 ? Y1 : Y2;
+    const int* eY = g == 0 ? eY1 : eY2;
+    double* G = g == 0 ? GA : GB;
+    int n0 = 0;
+    for (int k = 0; k < 2; n0 += nbs[k], ++k)
+      PASE_TRY(launch(Y, 64, eY, Y + 64, m - 64, eY + 64, W + n0, nbs[k], eW + n0, G, 0, G, 64, n0));
   }
   return PASE_OK;
 }

@@ -282,7 +282,8 @@ def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres,
 
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
-           "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7}
+           "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7,
+           "gram_split": 8}
 
 
 def pase_time_kernel(h, kernel, m, reps=10):

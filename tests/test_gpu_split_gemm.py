@@ -1,5 +1,5 @@
-"""The step-(d) product W C_W on the tensor cores (split digits, `split_gemm = 1`) against
-the oracle, through the C ABI (needs a GPU).
+"""The dense products on the tensor cores (split digits, `split_gemm = 1`), step (d) W C_W
+and the step-(b) Gram blocks, against the oracle through the C ABI (needs a GPU).
 
 With C_H = 0, pase_prolongate returns U = W C_W.  Bound checked on every entry (the
 error analysis of the split product: dropped digit diagonals, floor shifts, digit
@@ -174,3 +174,68 @@ def test_split_kernel_timing_entry(p3d):
             P.pase_time_kernel(h, "prolong_split", 136, 2)
     finally:
         P.pase_destroy(h)
+
+
+def _project(h, pb, m, W):
+    aH = torch.empty(pb.N_H, m, dtype=torch.float64, device="cuda")
+    bH = torch.empty_like(aH)
+    GA = torch.empty(m, m, dtype=torch.float64, device="cuda")
+    GM = torch.empty_like(GA)
+    P.pase_project(h, m, torch.from_numpy(np.ascontiguousarray(W)).cuda(), aH, bH, GA, GM)
+    return GA.cpu().numpy(), GM.cpu().numpy()
+
+
+def _gram_operand(N, m, seed):
+    rng = np.random.default_rng(seed)
+    W = pin.start_vectors(seed, N, m)
+    W *= np.exp2(rng.integers(-30, 31, size=(1, m)))             # column scales
+    spread = rng.choice(N, size=N // 8, replace=False)           # entries spread inside columns
+    W[spread] *= np.exp2(rng.integers(-20, 1, size=(len(spread), m)))
+    return W
+
+
+@pytest.mark.parametrize("m", [24, 56, 112])
+def test_split_gram_no_worse_than_fp64(p3d, m):
+    """Step (b) Gram blocks W^T(A_h W), W^T(M_h W) with split_gemm = 1 and 0 against an
+    extended-precision evaluation of the same definition (upper triangle mirrored): the
+    largest error relative to sum_r |w_ri||y_rj| is at most twice the FP64 kernel's (both
+    include the rounding of A_h W by the FP64 sparse product) and below 64 u.""" 
+    pb = p3d
+    W = _gram_operand(pb.N, m, 60 + m)
+    res = {}
+    for split in (1, 0):
+        h = _handle(pb, split)
+        try:
+            res[split] = _project(h, pb, m, W)
+        finally:
+            P.pase_destroy(h)
+    Wl = W.astype(np.longdouble)
+    for idx, Mat in ((0, pb.A), (1, pb.M)):
+        Y = Mat.astype(np.longdouble) @ Wl
+        ref = Wl.T @ Y
+        ref = np.triu(ref) + np.triu(ref, 1).T                 # upper triangle mirrored
+        scale = (np.abs(Wl).T @ np.abs(Y)).astype(np.float64)
+        scale = np.maximum(np.triu(scale), np.triu(scale, 1).T)
+        ref = ref.astype(np.float64)
+        r_s = (np.abs(res[1][idx] - ref) / scale).max() / U53   # worst error in units of u sum|w||y|
+        r_f = (np.abs(res[0][idx] - ref) / scale).max() / U53
+        assert r_s <= max(2.0 * r_f, 2.0) and r_s <= 64.0, (idx, r_s, r_f)
+
+
+def test_split_gram_nonfinite(p3d):
+    """A NaN in W gives the same NaN entries of the Gram blocks as the FP64 kernel."""
+    pb, m = p3d, 16
+    W = pin.start_vectors(70, pb.N, m)
+    W[1234, 5] = np.nan
+    res = {}
+    for split in (1, 0):
+        h = _handle(pb, split)
+        try:
+            res[split] = _project(h, pb, m, W)
+        finally:
+            P.pase_destroy(h)
+    for idx in (0, 1):
+        assert np.array_equal(np.isnan(res[1][idx]), np.isnan(res[0][idx]))
+        assert np.isnan(res[1][idx]).any()
+        fin = np.isfinite(res[0][idx])
+        np.testing.assert_allclose(res[1][idx][fin], res[0][idx][fin], rtol=1e-12, atol=1e-12 * np.abs(res[0][idx][fin]).max())
