@@ -1329,75 +1329,70 @@ __global__ void __launch_bounds__(1024) k_sygv_multisect(int n, int k, double* w
   if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));  // |T| bound
 }
 
-// 5. back-transform: each CTA takes kBtCols columns of Z through z <- H_0 ... H_{n-3} z,
+// 5. back-transform: each warp takes one column of Z through z <- H_0 ... H_{n-3} z,
 //    then c = D L^-T z.
-constexpr int kBtCols = 4;
-__global__ void __launch_bounds__(128) k_sygv_back(int n, int k, double* work, double* __restrict__ C, int ldc,
-                                                   int stage, const int* status) {
+constexpr int kBtWarps = 8;  // columns (one warp each) per CTA of the back-transform
+__global__ void __launch_bounds__(kBtWarps * 32) k_sygv_back(int n, int k, double* work, double* __restrict__ C,
+                                                             int ldc, int stage, const int* status) {
+  // one warp per eigenvector column: the reflector sweep and the triangular solve are
+  // sequences of n dependent steps, each a dot product and an update over one column, so
+  // a warp runs them with shuffles and no block barrier
   if (status[0] != 0) return;
-  extern __shared__ double zc[];  // kBtCols * n, then [packed reflectors | packed L]
-  __shared__ double red[4 * kBtCols];
-  __shared__ double coef[kBtCols];
+  extern __shared__ double zc[];  // kBtWarps * n, then [packed reflectors | packed L]
   SygvWork W = sygv_work(work, n, k);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
-  double* pk = zc + kBtCols * n;
-  const int c0 = blockIdx.x * kBtCols;
-  const int nc = min(kBtCols, k - c0);
-  for (int q = 0; q < nc; ++q)
-    for (int r = tid; r < n; r += blockDim.x) zc[q * n + r] = W.Z[(int64_t)r * k + c0 + q];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* pk = zc + kBtWarps * n;
+  const int col = blockIdx.x * kBtWarps + warp;
+  const bool have = col < k;
+  double* z = zc + warp * n;
+  if (have)
+    for (int r = lane; r < n; r += 32) z[r] = W.Z[(int64_t)r * k + col];
   // reflector j (rows j+1..n-1): v[0] = 1, v[r] = K[j][j+1+r] for r >= 1, packed at
   // pk + off(j), off(j) = j(n-2) - j(j-1)/2, n-j-2 entries
   if (stage) {
-    for (int j = warp; j + 2 < n; j += nw) {
+    for (int j = warp; j + 2 < n; j += kBtWarps) {
       const int off = j * (n - 2) - j * (j - 1) / 2;
       for (int r = lane; r < n - j - 2; r += 32) pk[off + r] = W.K[(int64_t)j * n + (j + 2 + r)];
     }
   }
   __syncthreads();
-  for (int j = n - 3; j >= 0; --j) {
-    const double t = W.tau[j];
-    if (t == 0.0) continue;
-    const int len = n - j - 1;
-    const double* vr = stage ? pk + (j * (n - 2) - j * (j - 1) / 2) - 1 : W.K + (int64_t)j * n + (j + 1);
-    for (int q = 0; q < nc; ++q) {
+  if (have) {
+    for (int j = n - 3; j >= 0; --j) {
+      const double t = W.tau[j];
+      if (t == 0.0) continue;
+      const int len = n - j - 1;
+      const double* vr = stage ? pk + (j * (n - 2) - j * (j - 1) / 2) - 1 : W.K + (int64_t)j * n + (j + 1);
       double acc = 0.0;
-      for (int r = tid; r < len; r += blockDim.x) acc = fma(r == 0 ? 1.0 : vr[r], zc[q * n + j + 1 + r], acc);
+      for (int r = lane; r < len; r += 32) acc = fma(r == 0 ? 1.0 : vr[r], z[j + 1 + r], acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) red[q * 4 + warp] = acc;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const double c = t * acc;
+      for (int r = lane; r < len; r += 32) z[j + 1 + r] -= c * (r == 0 ? 1.0 : vr[r]);
+      __syncwarp();
     }
-    __syncthreads();
-    if (tid < nc) coef[tid] = t * (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3]);
-    __syncthreads();
-    for (int q = 0; q < nc; ++q)
-      for (int r = tid; r < len; r += blockDim.x) zc[q * n + j + 1 + r] -= coef[q] * (r == 0 ? 1.0 : vr[r]);
-    __syncthreads();
   }
   // L^T x = z, rows from the bottom (column i of L = L[l][i], l > i); L packed by rows,
   // row l at off(l) = l(l+1)/2, when staged
   if (stage) {
-    for (int l = warp; l < n; l += nw)
+    __syncthreads();  // every warp is done with the reflectors
+    for (int l = warp; l < n; l += kBtWarps)
       for (int c = lane; c <= l; c += 32) pk[l * (l + 1) / 2 + c] = W.L[(int64_t)l * n + c];
     __syncthreads();
   }
+  if (!have) return;
   for (int i = n - 1; i >= 0; --i) {
-    for (int q = 0; q < nc; ++q) {
-      double acc = 0.0;
-      for (int l = i + 1 + tid; l < n; l += blockDim.x)
-        acc = fma(stage ? pk[l * (l + 1) / 2 + i] : W.L[(int64_t)l * n + i], zc[q * n + l], acc);
+    double acc = 0.0;
+    for (int l = i + 1 + lane; l < n; l += 32)
+      acc = fma(stage ? pk[l * (l + 1) / 2 + i] : W.L[(int64_t)l * n + i], z[l], acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) red[q * 4 + warp] = acc;
-    }
-    __syncthreads();
-    if (tid < nc) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
       const double lii = stage ? pk[i * (i + 1) / 2 + i] : W.L[(int64_t)i * n + i];
-      zc[tid * n + i] = (zc[tid * n + i] - (red[tid * 4] + red[tid * 4 + 1] + red[tid * 4 + 2] + red[tid * 4 + 3])) / lii;
+      z[i] = (z[i] - acc) / lii;
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int q = 0; q < nc; ++q)
-    for (int r = tid; r < n; r += blockDim.x) C[(int64_t)r * ldc + c0 + q] = W.sc[r] * zc[q * n + r];
+  for (int r = lane; r < n; r += 32) C[(int64_t)r * ldc + col] = W.sc[r] * z[r];
 }
 
 size_t small_sygv_work_doubles(int n, int k) {
@@ -1421,9 +1416,9 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   const size_t smem_trsm_st = (size_t)(n + 8 + tri) * sizeof(double);
   const int stage_l = smem_trsm_st <= 200 * 1024 ? 1 : 0;
   const size_t smem_trsm = stage_l ? smem_trsm_st : (size_t)(n + 8) * sizeof(double);
-  const size_t smem_back_st = (size_t)(kBtCols * n + tri) * sizeof(double);
+  const size_t smem_back_st = (size_t)(kBtWarps * n + tri) * sizeof(double);
   const int stage_b = smem_back_st <= 200 * 1024 ? 1 : 0;
-  const size_t smem_back = stage_b ? smem_back_st : (size_t)kBtCols * n * sizeof(double);
+  const size_t smem_back = stage_b ? smem_back_st : (size_t)kBtWarps * n * sizeof(double);
   const size_t smem_chol_s = (tri + n) * sizeof(double);
   const size_t smem_tri_s = (tri + 2 * n) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   const bool packed = smem_tri_s <= 200 * 1024 && smem_chol_s <= 200 * 1024;
@@ -1446,7 +1441,7 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
   }
   k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
-  k_sygv_back<<<(k + kBtCols - 1) / kBtCols, 128, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
+  k_sygv_back<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
