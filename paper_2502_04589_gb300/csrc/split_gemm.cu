@@ -28,9 +28,9 @@
 //
 // Layout: tiles of 128 rows (M = 128), K and N padded to multiples of 16 with zeros.
 // Shared memory holds the 8 A slices [128 x K] and 8 B slices [N x K] in the canonical
-// K-major core-matrix layout (8 rows x 16 bytes): 192 KB at K = N = 64, one CTA per SM,
-// persistent over tiles; the next tile's X rows are loaded into registers while the
-// tensor cores work on the current one.
+// K-major core-matrix layout (8 rows x 16 bytes): 192 KB at K = N = 64, one CTA of 16
+// warps per SM, persistent over tiles; the next tile's X rows are loaded into registers
+// while the tensor cores work on the current one.
 #include <cuda_bf16.h>
 
 #include "pase_internal.h"
@@ -39,7 +39,7 @@
 namespace pase {
 
 constexpr int kSgM = 128;       // rows per tile
-constexpr int kSgThreads = 256;
+constexpr int kSgThreads = 512;  // 16 warps: the slicing and the epilogue are latency-bound
 constexpr int kSgDigits = 8;
 
 __host__ __device__ inline size_t sg_smem_bytes(int kp, int np) {
@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(kSgThreads, 1)
                     const double* __restrict__ C, int ldc, double* __restrict__ Y, int64_t ldy, int beta,
                     uint32_t tmem_cols, int* __restrict__ err) {
   static_assert(KP % 16 == 0 && KP <= 64, "K tile");
-  constexpr int KH = KP / 2;  // K values per thread in the load phase
+  // threads per row in the load phase: the largest divisor of KP / 8 up to 4
+  constexpr int RP = (KP / 8) % 4 == 0 ? 4 : ((KP / 8) % 3 == 0 ? 3 : ((KP / 8) % 2 == 0 ? 2 : 1));
+  constexpr int KH = KP / RP;  // K values per loading thread (a multiple of 8)
+  static_assert(KH % 8 == 0, "load chunks of 8");
   extern __shared__ __align__(1024) uint8_t sg_smem[];
   __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sg_smem);  // [8][128 x KP]
   __nv_bfloat16* sB = sA + (size_t)kSgDigits * kSgM * KP;          // [8][np x KP]
@@ -174,13 +177,14 @@ __global__ void __launch_bounds__(kSgThreads, 1)
   const uint32_t idesc = umma_idesc_bf16(kSgM, np);
   const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
 
-  // load-phase role: row lr of the tile, K half lh
+  // load-phase role: row lr of the tile, K part lh (threads with lh >= RP only wait)
   const int lr = tid & (kSgM - 1), lh = tid >> 7;
+  const bool loader = lh < RP;
   const int64_t ntiles = (n + kSgM - 1) / kSgM;
   double xv[KH];
   auto load_tile = [&](int64_t tile) {
     const int64_t row = tile * kSgM + lr;
-    const bool ok = row < n;
+    const bool ok = loader && row < n;
     const double* src = X + (ok ? row : 0) * ldx + lh * KH;
 #pragma unroll
     for (int c = 0; c < KH; c += 2) {
@@ -200,9 +204,11 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     for (int c = 0; c < KH; ++c) e = max(e, sg_bexp(xv[c]));
     sEx[tid] = e;
     __syncthreads();
-    e = max(sEx[lr], sEx[lr + kSgM]);
+    e = sEx[lr];
 #pragma unroll
-    for (int c8 = 0; c8 < KH / 8; ++c8) {
+    for (int q = 1; q < RP; ++q) e = max(e, sEx[lr + q * kSgM]);
+#pragma unroll
+    for (int c8 = 0; c8 < (loader ? KH / 8 : 0); ++c8) {
       uint64_t z[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) z[c] = sg_fixed(xv[c8 * 8 + c], e);
@@ -247,25 +253,26 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // ---- epilogue: warp -> 32 TMEM lanes (rows) x half of the columns
-    const int lq = warp & 3, chh = warp >> 2;
+    // ---- epilogue: warp -> 32 TMEM lanes (rows) x a quarter of the columns
+    const int lq = warp & 3, part = warp >> 2, npart = np / 4;  // npart: a multiple of 4
     const int er = lq * 32 + lane;
     const int64_t row = tile * kSgM + er;
-    const int erx = max(sEx[er], sEx[er + kSgM]);
+    int erx = sEx[er];
+#pragma unroll
+    for (int q = 1; q < RP; ++q) erx = max(erx, sEx[er + q * kSgM]);
     const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
-    for (int c0 = chh * (np / 2); c0 < (chh + 1) * (np / 2); c0 += 8) {
-      uint32_t v[8][8];
+    for (int c0 = part * npart; c0 < (part + 1) * npart; c0 += 4) {
+      uint32_t v[8][4];
 #pragma unroll
       for (int d = 0; d < 8; ++d)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
-                       "=r"(v[d][6]), "=r"(v[d][7])
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3])
                      : "r"(lane_addr + (uint32_t)(d * np + c0)));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row < n) {
-        double out[8];
+        double out[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 4; ++c) {
           int64_t T = 0;
 #pragma unroll
           for (int d = 0; d < 6; ++d) T += (int64_t)__float2int_rn(__uint_as_float(v[d][c])) * (1ll << (44 - 8 * d));
@@ -285,15 +292,15 @@ __global__ void __launch_bounds__(kSgThreads, 1)
         double* yr = Y + row * ldy + c0;
         if (beta) {  // Y += X C (a second K block of a wider product)
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
+          for (int c = 0; c < 4; ++c)
             if (c0 + c < k2) out[c] += yr[c];
         }
-        if (c0 + 8 <= k2) {
-#pragma unroll
-          for (int c = 0; c < 8; c += 2) *reinterpret_cast<double2*>(yr + c) = make_double2(out[c], out[c + 1]);
+        if (c0 + 4 <= k2) {
+          *reinterpret_cast<double2*>(yr) = make_double2(out[0], out[1]);
+          *reinterpret_cast<double2*>(yr + 2) = make_double2(out[2], out[3]);
         } else {
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
+          for (int c = 0; c < 4; ++c)
             if (c0 + c < k2) yr[c] = out[c];
         }
       }
@@ -383,7 +390,10 @@ constexpr int kGsK = 64;          // rows per chunk (MMA K)
 constexpr int kGsDrainChunks = 2;  // chunks per accumulation
 constexpr int64_t kGsMaxRowsPerCta = 1 << 14;
 constexpr int kGsU0 = 48;          // T unit 2^{e_i + f_j - 48}
-constexpr int kGsItems = (kSgM * 8 + 64 * 8) / kSgThreads;  // slicing items per thread
+constexpr int kGsThreads = 512;     // 16 warps: the slicing is latency-bound
+constexpr int kGsWarpParts = kGsThreads / 128;  // warps sharing one TMEM lane quarter
+constexpr int kGsOut = 64 / kGsWarpParts;       // accumulator columns per thread (np <= 64)
+constexpr int kGsItems = (kSgM * 8 + 64 * 8) / kGsThreads;  // slicing items per thread
 
 // column exponents (sg_bexp + 2048, so 0 = "no value yet") by atomicMax; blockIdx.y
 // selects one of three [n][ld] arrays, columns [c0, c0 + m), m <= 64
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(256) k_colexp(int64_t n, int m, int64_t ld, Co
   }
 }
 
-__global__ void __launch_bounds__(kSgThreads, 1)
+__global__ void __launch_bounds__(kGsThreads, 1)
     k_gram_split(int64_t n, int64_t rows_per_cta, const double* __restrict__ A0, int64_t lda0, int na0,
                  const double* __restrict__ A1, int64_t lda1, int na1, const double* __restrict__ B, int64_t ldb,
                  int nbc, int np, const int* __restrict__ aexp0, const int* __restrict__ aexp1,
@@ -458,11 +468,12 @@ __global__ void __launch_bounds__(kSgThreads, 1)
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = min(n, r0 + rows_per_cta);
   // drain role: TMEM lane (A column) er, B columns [jb, jb + np/2)
-  const int lq = warp & 3, er = lq * 32 + lane, jb = (warp >> 2) * (np / 2);
+  const int npart = np / kGsWarpParts;  // columns per warp (a multiple of 4)
+  const int lq = warp & 3, er = lq * 32 + lane, jb = (warp >> 2) * npart;
   const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
-  int64_t acc[32];
+  int64_t acc[kGsOut];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0;
+  for (int c = 0; c < kGsOut; ++c) acc[c] = 0;
   uint32_t phase = 0;
   bool ok = true;
   int chunk = 0;
@@ -498,7 +509,7 @@ __global__ void __launch_bounds__(kSgThreads, 1)
   auto load_chunk = [&](int64_t rb) {
 #pragma unroll
     for (int q = 0; q < kGsItems; ++q) {
-      const int it = tid + q * kSgThreads;
+      const int it = tid + q * kGsThreads;
       const double* src = nullptr;
       int64_t ld = 0;
       int col = 0, e = 0, kg = 0, stride = 0;
@@ -517,7 +528,7 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     // ---- digit slices of rows [rb, rb + 64) from the prefetched values
 #pragma unroll
     for (int q = 0; q < kGsItems; ++q) {
-      const int it = tid + q * kSgThreads;
+      const int it = tid + q * kGsThreads;
       if (it < nitems) {
         const double* src;
         int64_t ld;
@@ -571,8 +582,8 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     // ---- drain after every second chunk and after the last
     if ((chunk % kGsDrainChunks) == kGsDrainChunks - 1 || rb + kGsK >= r1) {
 #pragma unroll
-      for (int cb = 0; cb < 8; ++cb) {
-        if (cb * 4 < np / 2) {  // warp-uniform
+      for (int cb = 0; cb < kGsOut / 4; ++cb) {
+        if (cb * 4 < npart) {  // warp-uniform
           uint32_t v[8][4];
 #pragma unroll
           for (int d = 0; d < 8; ++d)
@@ -605,9 +616,9 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     const int icol = hi ? er - 64 : er;
     const bool ivalid = icol < (hi ? na1 : na0);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int c = 0; c < kGsOut; ++c) {
       const int j = jb + c;
-      if (c < np / 2) {
+      if (c < npart) {
         double vout = 0.0;
         if (ivalid && j < nbc) {
           const int je = sBe[j];
@@ -687,7 +698,7 @@ int ts_gram2_split(pase_ctx* h, int64_t n, int m, const double* W, const double*
       return fail(PASE_ERR_INVALID_ARG, "ts_gram2_split: partial buffer too small");
     uint32_t cols = 32;
     while (cols < (uint32_t)(8 * np)) cols <<= 1;
-    k_gram_split<<<(unsigned)grid, kSgThreads, smem, h->stream>>>(n, rpc, A0, m, na0, A1, m, na1, Bp, m, nbc, np,
+    k_gram_split<<<(unsigned)grid, kGsThreads, smem, h->stream>>>(n, rpc, A0, m, na0, A1, m, na1, Bp, m, nbc, np,
                                                                   e0, e1, eb, w.partial, cols, err);
     h->launches++;
     PASE_CUDA(cudaGetLastError());
