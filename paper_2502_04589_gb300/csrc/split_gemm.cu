@@ -123,6 +123,36 @@ __device__ __forceinline__ double sg_to_double(int64_t T, int X) {
   return ldexp((double)T, X);
 }
 
+// The 36 slice products of one K block into the 8 diagonal accumulators (TMEM columns
+// (d - 2) np ...): fully unrolled, descriptors formed by adding compile-time offsets to
+// the two base descriptors (the 14-bit address field cannot carry: shared memory is
+// below 256 KB).  strideA16 / strideB16: slice strides in 16-byte units.  fresh: the
+// first product of each diagonal overwrites the accumulator.
+template <int KSTEPS>
+__device__ __forceinline__ void sg_issue_products(uint32_t tmem, int np, uint64_t descA0, uint64_t descB0,
+                                                  uint32_t strideA16, uint32_t strideB16, uint32_t idesc,
+                                                  bool fresh) {
+#pragma unroll
+  for (int d = 2; d <= kSgDigits + 1; ++d) {
+    const uint32_t dcol = tmem + (uint32_t)((d - 2) * np);
+#pragma unroll
+    for (int p = 1; p <= kSgDigits; ++p) {
+      const int q = d - p;
+      if (q < 1 || q > kSgDigits) continue;
+#pragma unroll
+      for (int s = 0; s < KSTEPS; ++s) {
+        const bool first = p == (d - kSgDigits > 1 ? d - kSgDigits : 1) && s == 0;
+        const uint64_t da = descA0 + (uint64_t)((p - 1) * strideA16 + s * 16);
+        const uint64_t db = descB0 + (uint64_t)((q - 1) * strideB16 + s * 16);
+        const uint32_t accf = (first && fresh) ? 0u : 1u;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                     "l"(da), "l"(db), "r"(idesc), "r"(accf));
+      }
+    }
+  }
+}
+
 template <int KP>
 __global__ void __launch_bounds__(kSgThreads, 1)
     k_ts_gemm_split(int64_t n, int k1, int k2, int np, const double* __restrict__ X, int64_t ldx,
@@ -143,6 +173,9 @@ __global__ void __launch_bounds__(kSgThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int strideA = kSgM * KP, strideB = np * KP;
 
+  // A-slice chunks that only hold K padding (k >= k1) stay zero: clear them once
+  for (int i = tid; i < kSgDigits * kSgM * KP / 8; i += kSgThreads)
+    reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
   // ---- B slices from C (every CTA; C is at most 64 x 64)
   if (tid < 64) {
     int f = kSgZeroExp;
@@ -209,10 +242,11 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     for (int q = 1; q < RP; ++q) e = max(e, sEx[lr + q * kSgM]);
 #pragma unroll
     for (int c8 = 0; c8 < (loader ? KH / 8 : 0); ++c8) {
+      const int kc = lh * (KH / 8) + c8;
+      if (kc * 8 >= k1) continue;  // padding only: still zero
       uint64_t z[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) z[c] = sg_fixed(xv[c8 * 8 + c], e);
-      const int kc = lh * (KH / 8) + c8;
       sg_store_chunk(z, sA + (lr >> 3) * (KP * 8) + kc * 64 + (lr & 7) * 8, strideA);
     }
     asm volatile("fence.proxy.async.shared::cta;");
@@ -220,26 +254,8 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     // ---- 36 slice products per K step into the 8 diagonal accumulators
     if (tid == 0) {
-#pragma unroll 1
-      for (int d = 2; d <= 2 * kSgDigits; ++d) {
-        if (d > kSgDigits + 1) break;
-        const uint32_t dcol = tmem + (uint32_t)((d - 2) * np);
-        bool first = true;
-        for (int p = 1; p < d; ++p) {
-          const int q = d - p;
-          if (p > kSgDigits || q > kSgDigits) continue;
-#pragma unroll
-          for (int s = 0; s < KP / 16; ++s) {
-            const uint64_t da = umma_desc(aBase + (uint32_t)(((p - 1) * strideA + s * 128) * 2), 128, KP * 16);
-            const uint64_t db = umma_desc(bBase + (uint32_t)(((q - 1) * strideB + s * 128) * 2), 128, KP * 16);
-            const uint32_t acc = first ? 0u : 1u;
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-                         "l"(da), "l"(db), "r"(idesc), "r"(acc));
-            first = false;
-          }
-        }
-      }
+      sg_issue_products<KP / 16>(tmem, np, umma_desc(aBase, 128, KP * 16), umma_desc(bBase, 128, KP * 16),
+                                 (uint32_t)(strideA / 8), (uint32_t)(strideB / 8), idesc, true);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar)));
     }
@@ -451,6 +467,9 @@ __global__ void __launch_bounds__(kGsThreads, 1)
     sAe[tid] = e - 2048;
   }
   if (tid < 64) sBe[tid] = (tid < nbc ? bexp[tid] : 0) - 2048;
+  // slices of padding columns (beyond na0, na1, nbc) stay zero: clear both buffers once
+  for (int i = tid; i < (kSgDigits * kSgM * kGsK + kSgDigits * np * kGsK) / 8; i += kGsThreads)
+    reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(tmem_cols));
@@ -536,6 +555,7 @@ __global__ void __launch_bounds__(kGsThreads, 1)
         bool valid;
         __nv_bfloat16* dst;
         item(it, src, ld, col, valid, e, kg, dst, stride);
+        if (!valid) continue;  // padding column: its slices stay zero
         uint64_t z[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) z[c] = sg_fixed(pv[q][c], e);
@@ -546,26 +566,9 @@ __global__ void __launch_bounds__(kGsThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
-      const bool fresh = (chunk % kGsDrainChunks) == 0;
-#pragma unroll 1
-      for (int d = 2; d <= kSgDigits + 1; ++d) {
-        const uint32_t dcol = tmem + (uint32_t)((d - 2) * np);
-        bool first = fresh;
-        for (int p = 1; p < d; ++p) {
-          const int q = d - p;
-          if (p > kSgDigits || q > kSgDigits) continue;
-#pragma unroll
-          for (int s = 0; s < kGsK / 16; ++s) {
-            const uint64_t da = umma_desc(aBase + (uint32_t)(((p - 1) * strideA + s * 128) * 2), 128, kGsK * 16);
-            const uint64_t db = umma_desc(bBase + (uint32_t)(((q - 1) * strideB + s * 128) * 2), 128, kGsK * 16);
-            const uint32_t accf = first ? 0u : 1u;
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-                         "l"(da), "l"(db), "r"(idesc), "r"(accf));
-            first = false;
-          }
-        }
-      }
+      sg_issue_products<kGsK / 16>(tmem, np, umma_desc(aBase, 128, kGsK * 16), umma_desc(bBase, 128, kGsK * 16),
+                                   (uint32_t)(strideA / 8), (uint32_t)(strideB / 8), idesc,
+                                   (chunk % kGsDrainChunks) == 0);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar)));
     }
