@@ -63,3 +63,52 @@ def test_missing_library_fails_loudly(tmp_path):
             P.load_library(str(tmp_path / "nope.so"))
     finally:
         P._lib = saved
+
+
+_CTYPES = {"int": "c_int", "double": "c_double", "float": "c_float", "unsigned": "c_uint",
+           "int64_t": "c_int64"}
+
+
+def _header_struct(name):
+    """(field, C type, array length) of `typedef struct {...} name;` in include/pase.h."""
+    src = open(os.path.join(ROOT, "include", "pase.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(const\s+)?([A-Za-z_0-9]+\s*\**)\s*(.*)", decl)
+        ctype = m.group(2).replace(" ", "")
+        for var in m.group(3).split(","):
+            var = var.strip()
+            if var.startswith("*"):
+                ctype, var = ctype + "*", var[1:].strip()
+            am = re.match(r"([A-Za-z_0-9]+)\s*(?:\[(\d+)\])?", var)
+            out.append((am.group(1), ctype, int(am.group(2)) if am.group(2) else 0))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("pase_options", "PaseOptions"), ("pase_stats", "PaseStats"),
+                                          ("pase_train_options", "PaseTrainOptions"), ("pase_csr", "PaseCSR")])
+def test_binding_structs_match_header(cname, pyname):
+    """Field names, order and types of the ctypes mirrors equal the header's structs."""
+    import ctypes
+    from paper_2502_04589_gb300 import pase as P
+    fields = getattr(P, pyname)._fields_
+    decl = _header_struct(cname)
+    assert [f[0] for f in fields] == [d[0] for d in decl]
+    for (fname, ftype), (_, ctype, n) in zip(fields, decl):
+        if ctype.endswith("*"):
+            assert ftype is ctypes.c_void_p, fname
+        elif n:
+            assert ftype._length_ == n and ftype._type_ is getattr(ctypes, _CTYPES[ctype]), fname
+        else:
+            assert ftype is getattr(ctypes, _CTYPES[ctype]), fname
+
+
+def test_default_options_of_the_later_fields(lib):
+    from paper_2502_04589_gb300 import pase as P
+    o = P.pase_default_options()
+    assert (o.use_graphs, o.autotune, o.smoother, o.split_gemm, o.aug_adaptive) == (1, 1, P.PASE_SMOOTHER_JACOBI, 1, 1)
