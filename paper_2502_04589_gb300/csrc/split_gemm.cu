@@ -1,6 +1,9 @@
-// Y = X C for a tall block X [n][k1] and a small C [k1][k2] (k1, k2 <= 128, even) on the
-// BF16 tensor cores with FP64 accuracy: the prolongation W C_W of Alg. 3 step 6.  One
-// launch covers k1, k2 <= 64; wider products run as 64-wide blocks.
+// The two dense FP64 contractions of the path on the BF16 tensor cores, with FP64
+// accuracy:
+//   * Y = X C for a tall block X [n][k1] and a small C [k1][k2] (k1, k2 <= 128, even):
+//     the prolongation W C_W of Alg. 3 step 6.  One launch covers k1, k2 <= 64; wider
+//     products run as 64-wide blocks.
+//   * the Gram blocks W^T (A_h W), W^T (M_h W) of Alg. 3 step 4 (second part of the file).
 //
 // Error-free splitting (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication", Numer.
