@@ -545,6 +545,8 @@ def run_ours(args):
     Uh = torch.from_numpy(U.cpu().numpy()).pin_memory()
     lh = torch.from_numpy(lam.cpu().numpy()).pin_memory()
     rh = torch.zeros(m, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):  # untimed: the first host-buffer call allocates the staging buffers
+        P.pase_iterate(h, NEV, m, Uh.numpy(), lh.numpy(), True, rh.numpy())
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
