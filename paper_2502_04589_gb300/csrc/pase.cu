@@ -639,7 +639,7 @@ static int step_project(pase_ctx* h, const double* W, double* aH, double* bH, do
                               nullptr, nullptr, 0.0, w.T1, w.T2, nullptr, nullptr));
   PASE_TRY(launch_csr<double>(h, CSR_MV2, m, h->PdT, h->PdT.val, nullptr, w.T1, w.T2, nullptr, nullptr,
                               nullptr, 0.0, aH, bH, nullptr, nullptr));
-  if (h->opt.split_gemm && ts_gram2_split_ok(m, w))
+  if (h->opt.split_gemm && ts_gram2_split_ok(h->N, m, h->num_sms, w))
     return ts_gram2_split(h, h->N, m, W, w.T1, w.T2, GA, GM, m, w.colexp, h->tc_err);
   PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T1, m, GA, m, true));
   PASE_TRY(ts_gram(h, h->N, m, m, W, m, w.T2, m, GM, m, true));
@@ -1240,7 +1240,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
-  if (kernel == PASE_KERNEL_GRAM_SPLIT && !ts_gram2_split_ok(m, h->w))
+  if (kernel == PASE_KERNEL_GRAM_SPLIT && !ts_gram2_split_ok(h->N, m, h->num_sms, h->w))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split Gram takes m <= 128");
   // deterministic operands
   PASE_TRY(launch_hash_fill(h, h->N, m, m, 7u, w.W));

@@ -258,7 +258,7 @@ int ts_gemm_split(pase_ctx* h, int64_t n, int k1, int k2, const double* X, int64
                   double* Y, int64_t ldy, int* err);
 // GA = W^T Y1, GB = W^T Y2 (upper triangles mirrored), [n][m] blocks with m <= 128 even,
 // on the tensor cores with the same splitting (split_gemm.cu); colexp: 3 x 128 ints.
-bool ts_gram2_split_ok(int m, const Work& w);
+bool ts_gram2_split_ok(int64_t n, int m, int num_sms, const Work& w);  // shape and scratch fit
 int ts_gram2_split(pase_ctx* h, int64_t n, int m, const double* W, const double* Y1, const double* Y2, double* GA,
                    double* GB, int ldg, int* colexp, int* err);
 int ts_gemm(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const double* X, int ldx,

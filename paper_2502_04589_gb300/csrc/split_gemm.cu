@@ -668,10 +668,22 @@ __global__ void k_gram_split_reduce(int nb, int np, const double* __restrict__ p
   }
 }
 
-bool ts_gram2_split_ok(int m, const Work& w) {
+// CTAs of the split Gram over n rows: at least one per SM, at most 2^14 rows each, whole
+// 64-row chunks; *rows_per_cta receives the rows of each.
+static int64_t gram_split_grid(int64_t n, int num_sms, int64_t* rows_per_cta) {
+  int64_t grid = std::max<int64_t>(num_sms, (n + kGsMaxRowsPerCta - 1) / kGsMaxRowsPerCta);
+  grid = std::max<int64_t>(1, std::min<int64_t>(grid, (n + kGsK - 1) / kGsK));
+  int64_t rpc = (n + grid - 1) / grid;
+  rpc = (rpc + kGsK - 1) / kGsK * kGsK;
+  if (rows_per_cta) *rows_per_cta = rpc;
+  return (n + rpc - 1) / rpc;
+}
+
+bool ts_gram2_split_ok(int64_t n, int m, int num_sms, const Work& w) {
   if (m < 2 || m > 128 || (m % 2) != 0) return false;
-  const int64_t need = (int64_t)4 * kSgM * 64;  // a few CTAs' partials at least
-  return (int64_t)(w.partial_bytes / sizeof(double)) >= need;
+  const int64_t np = m <= 64 ? (m + 15) / 16 * 16 : 64;  // widest B block of a launch
+  const int64_t need = std::max<int64_t>(1, gram_split_grid(n, num_sms, nullptr)) * kSgM * np;
+  return (int64_t)(w.partial_bytes / sizeof(double)) >= need;  // every CTA's partials fit
 }
 
 // GA = W^T Y1 and GB = W^T Y2 (symmetric, upper triangle mirrored), all [n][m], m <= 128
@@ -689,11 +701,8 @@ int ts_gram2_split(pase_ctx* h, int64_t n, int m, const double* W, const double*
     h->launches++;
   }
   PASE_CUDA(cudaGetLastError());
-  int64_t grid = std::max<int64_t>(h->num_sms, (n + kGsMaxRowsPerCta - 1) / kGsMaxRowsPerCta);
-  grid = std::min<int64_t>(grid, (n + kGsK - 1) / kGsK);
-  int64_t rpc = (n + grid - 1) / grid;
-  rpc = (rpc + kGsK - 1) / kGsK * kGsK;
-  grid = (n + rpc - 1) / rpc;
+  int64_t rpc = 0;
+  const int64_t grid = gram_split_grid(n, h->num_sms, &rpc);
   const size_t smem = std::max<size_t>(sg_smem_bytes(kGsK, 64), 116 * 1024);
   PASE_TRY(ensure_max_smem((const void*)k_gram_split, 200 * 1024));
   auto launch = [&](const double* A0, int na0, const int* e0, const double* A1, int na1, const int* e1,
