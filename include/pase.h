@@ -88,8 +88,9 @@ typedef struct {
   int smoother;        /* PASE_SMOOTHER_JACOBI (default) or PASE_SMOOTHER_LEARNED: the fine-
                           level sweeps of the V-cycle use the learned network once
                           pase_set_grid and parameters are given (Jacobi until then)      */
-  int split_gemm;      /* 1 (default): the dense products of steps (b) and (d), the Gram
-                          blocks W^T(A_h W), W^T(M_h W) and W C_W (m <= 128, even), run on
+  int split_gemm;      /* 1 (default): the dense products of steps (b) and (d) (Alg. 3 steps
+                          4 and 6), the Gram blocks W^T(A_h W), W^T(M_h W) and W C_W
+                          (m <= 128, even; wider blocks use the FP64 kernels), run on
                           the BF16 tensor cores with FP64 accuracy (error-free splitting into
                           8-bit digit slices, exact FP32 sums per digit diagonal, 64-bit
                           integer recombination; error a few units of 2^-53 relative to the
