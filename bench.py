@@ -643,7 +643,9 @@ def run_ours(args):
                 "config": {"workload": wl, "N_h": pb.N, "nnz": pb.A.nnz, "N_H": pb.N_H, "nev": NEV,
                            "block": m, "linear_solve": "2 V-cycles, damped Jacobi 2+2, omega 2/3",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "inputs larger than L2 (block 0.92 GB)"},
+                           "l2": "inputs larger than L2 (block 0.92 GB)",
+                           "dense_products": "steps (b) and (d): FP64-accurate error-free digit splitting on "
+                                             "the BF16 tensor cores (option split_gemm)"},
                 "roofline": roofline, "spmm_fp64": spmm_live, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "solve": solves, "batched": batched, "learned_smoother": learned,
                 "learned_smoother_3d": learned3d}
