@@ -218,8 +218,9 @@ int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
  * Computes R = M U diag(lambda) - A U (R may be NULL) and relres[j] =
  * ||A u_j - lambda_j M u_j||_2 / (lambda_j ||M u_j||_2) for an n x n pencil in CSR that
  * shares one pattern (rowptr [n+1], colind [nnz], A_val / M_val [nnz]).
- * Every pointer must be device memory (no host staging: staging would allocate); U and R
- * are row-major [n][m] and 16-byte aligned; 8 <= m <= 64, m a multiple of 8 (larger m is
+ * Every pointer must be device memory of the current device, or managed memory (no host
+ * staging: staging would allocate; a pointer into another GPU's memory is rejected with
+ * PASE_ERR_INVALID_ARG); U and R are row-major [n][m] and 16-byte aligned; 8 <= m <= 64, m a multiple of 8 (larger m is
  * rejected with PASE_ERR_INVALID_ARG).  Work is queued on cuda_stream (NULL = legacy
  * default stream) and the call returns without synchronising.
  * Scratch: a fixed 1.19 MiB array in device memory, part of the library image, held by

@@ -29,7 +29,9 @@ from .mg import Hierarchy, cg, pcg
 
 
 def relative_residuals(A, M, U, lam):
-    """||A u_i - lam_i M u_i||_2 / (lam_i ||M u_i||_2) for every column."""
+    """||A u_i - lam_i M u_i||_2 / (|lam_i| ||M u_i||_2) for every column: the stopping test
+    of the numerical section (§6 divides by |lambda| only; the factor ||M u||_2 is added here
+    so that the test does not depend on how u is scaled)."""
     AU = A @ U
     MU = M @ U
     R = AU - MU * lam
@@ -159,10 +161,3 @@ class Solver:
                 break
         return lam, U, dict(iterations=it, history=history, converged=bool(np.all(history[-1][:nev] <= tol)))
 
-
-def normalise_signs(U):
-    """Flip each column so that its largest-|entry| (lowest index on ties) is positive."""
-    idx = np.argmax(np.abs(U), axis=0)
-    s = np.sign(U[idx, np.arange(U.shape[1])])
-    s[s == 0] = 1.0
-    return U * s

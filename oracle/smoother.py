@@ -29,12 +29,15 @@ batch loss is the mean over columns.  Adam as in Kingma & Ba (2015).
 Use in the V-cycle: on level 0 each of the nu1 pre- and nu2 post-smoothing sweeps
 x <- x + omega D^-1 (b - A x) becomes x <- x + S(b - A x); coarser levels keep Jacobi.
 Inference (the V-cycle, `apply(..., act_bf16=True)`) rounds the network input and stores
-the hidden activations in bfloat16 between layers; training differentiates the same
-network with FP32 inputs and activations.
+the hidden activations in bfloat16 between layers: tensor-core MMAs of kind f16 take both
+operands in 16-bit form, so the activations that feed them are bfloat16 numbers.  Training
+differentiates the same network with FP32 inputs and activations; `inference_error_bound`
+bounds, elementwise, how far the inference form can move from it.
 
-Parity: pinned in tests/test_oracle_pins.py (convolution against scipy.ndimage,
+Parity: pinned in tests/test_oracle_smoother.py (convolution against scipy.ndimage,
 finite-difference gradients, positive homogeneity, the Jacobi-equivalent weights,
-Adam's first step in closed form, the loss at delta = 0 and delta = e).
+Adam's first step in closed form, the loss at delta = 0 and delta = e, the inference
+form within its rounding-error bound of the FP32-activation network).
 """
 import numpy as np
 
@@ -189,6 +192,59 @@ def apply(params, r, dinv, feat, d, n1, round_bf16=True, act_bf16=False):
     s, rho = normalise(r, dinv)
     y, _ = forward(params, s, feat, d, n1, round_bf16, act_bf16)
     return (y * rho[:, None]).T
+
+
+# Relative change of one rounding of the inference form: float64 -> float32 -> bfloat16,
+# each to nearest (8 significand bits: 2^-8; the float32 step adds at most 2^-24 and its
+# product with the first term, covered by 2^-23).
+BF16_UNIT_ROUNDOFF = 2.0 ** -8 + 2.0 ** -23
+
+
+def inference_error_bound(params, r, dinv, feat, d, n1, kind="worst", c=5.0, round_bf16=True):
+    """Elementwise bound on |apply(act_bf16=True) - apply(act_bf16=False)|, [N][B].
+
+    The inference form rounds the inputs x_l of the four layers (the network input and the
+    three ReLU outputs) to bfloat16, a fresh rounding error e_l with |e_l| <= u |x_l| (u =
+    BF16_UNIT_ROUNDOFF) at each.  To first order in u the output moves by sum_l J_l e_l, J_l
+    the Jacobian of the output with respect to x_l in the FP32-activation network (with that
+    network's ReLU masks), times the column scale rho.
+
+    kind="worst": the first-order worst case  u sum_l sum_k |J_l[i,k]| |x_l[k]|.
+    kind="prob":  c sqrt(sum_l sum_k (u J_l[i,k] x_l[k])^2), the probabilistic bound of
+      rounding-error analysis (Higham and Mary, SIAM J. Sci. Comput. 41, 2019): with the
+      roundings modelled as independent, mean-zero and bounded by u |x|, Hoeffding's
+      inequality puts the first-order output error above it with probability at most
+      2 exp(-c^2 / 2) (7.5e-6 for c = 5).
+    Terms of second order in u, and ReLU outputs whose sign the roundings flip, are not in
+    either (a flip moves a value by no more than its own first-order perturbation)."""
+    if kind not in ("worst", "prob"):
+        raise ValueError(kind)
+    u = BF16_UNIT_ROUNDOFF
+    s, rho = normalise(r, dinv)
+    _, (p, cache) = forward(params, s, feat, d, n1, round_bf16)
+    layers = unpack(p, d)
+    B, N = s.shape
+    eye = np.arange(N)
+    out = np.zeros((B, N))
+    for b in range(B):
+        g = np.zeros((N, 1, N))  # g[i] = derivative of output node i
+        g[eye, 0, eye] = 1.0
+        for li in reversed(range(len(layers))):
+            W, _, relu = layers[li]
+            x, z = cache[li]  # the layer's input and pre-activation
+            if relu:
+                g = g * (z[b] > 0.0)[None]
+            gx = np.zeros((N, W.shape[1], N))
+            for t, o in enumerate(offsets(d)):
+                gx += _shift(np.einsum("oc,ion->icn", W[:, :, t], g), tuple(-v for v in o), d, n1)
+            if kind == "worst":
+                out[b] += u * np.einsum("icn,cn->i", np.abs(gx), np.abs(x[b]))
+            else:
+                out[b] += u * u * np.einsum("icn,cn->i", gx * gx, x[b] * x[b])
+            g = gx
+    if kind == "prob":
+        out = c * np.sqrt(out)
+    return (out * rho[:, None]).T
 
 
 def loss_and_grad(params, e, r, A, dinv, feat, d, n1, round_bf16=True):

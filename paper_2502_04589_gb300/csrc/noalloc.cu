@@ -14,8 +14,9 @@
 
 namespace pase {
 
-// Largest block width accepted, and the number of partial-sum rows (one per block of the
-// residual kernel, whose grid is capped at this count).
+// Largest block width accepted, and the number of partial-sum rows: one per block of the
+// residual kernel, whose grid launch_csr caps at kReduceBlocksHost (the same constant, so
+// the partial sums of any launch fit).
 constexpr int kNoAllocMaxM = 64;
 constexpr int kNoAllocBlocks = kReduceBlocksHost;
 constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocBlocks * 2 * kNoAllocMaxM + 2 * kNoAllocMaxM;
@@ -50,13 +51,16 @@ int scratch_address(double** out) {
   return PASE_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device (managed memory counts): a pointer into another
+// GPU's memory would be dereferenced without peer access by kernels launched here.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 }  // namespace
 }  // namespace pase
@@ -73,10 +77,14 @@ extern "C" int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, co
   if (n > INT32_MAX) return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: too many rows");
   if (!rowptr || !colind || !A_val || !M_val || !U || !lambda || !relres)
     return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: null argument");
+  int dev = 0;
+  PASE_CUDA(cudaGetDevice(&dev));
   const void* ptrs[] = {rowptr, colind, A_val, M_val, U, lambda, relres};
   for (const void* p : ptrs)
-    if (!on_device(p)) return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: every array must be device memory");
-  if (R && !on_device(R)) return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: R must be device memory");
+    if (!on_device(p, dev))
+      return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: every array must be device memory of the current device");
+  if (R && !on_device(R, dev))
+    return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: R must be device memory of the current device");
   if (((uintptr_t)U | (uintptr_t)(R ? R : U)) % 16 != 0)
     return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: U and R must be 16-byte aligned");
   double* scratch = nullptr;
@@ -98,10 +106,10 @@ extern "C" int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, co
   }
   int nb = 0;
   // every block writes all 2m of its partial sums and the reduction reads exactly those,
-  // so nothing in the scratch needs clearing between calls
+  // so nothing in the scratch needs clearing between calls; nb <= kNoAllocBlocks by the
+  // grid cap of launch_csr
   PASE_TRY(launch_csr<double>(&ctx, CSR_EIGRES, m, A, A_val, M_val, U, nullptr, nullptr, nullptr, lambda, 0.0,
                               R, nullptr, partial, &nb));
-  if (nb > kNoAllocBlocks) return fail(PASE_ERR_INVALID_ARG, "pase_residual_noalloc: grid exceeds the scratch");
   PASE_TRY(launch_reduce_partials(&ctx, nb, 2 * m, partial, norms));
   PASE_TRY(launch_relres(&ctx, m, norms, lambda, relres));
   return PASE_OK;

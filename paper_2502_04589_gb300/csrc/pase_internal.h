@@ -274,6 +274,8 @@ int small_gemm(pase_ctx* h, int m, int n, int k, double alpha, const double* A, 
 int small_chol_solve(pase_ctx* h, int n, int nrhs, double* S, int lds, double* B, int ldb,
                      int* status_dev, bool factor);  // [S <- chol(S) (lower)], B <- S^-1 B
 size_t small_sygv_work_doubles(int n, int k);
+// Cap on the grid of every kernel that writes per-block partial sums (the residual, the
+// CG inner products, the smoother's column sums): partial buffers hold this many blocks.
 constexpr int kReduceBlocksHost = 152 * 8;
 // column-wise residual of a block eigenproblem: R = AX - BX diag(lam), partial norms
 int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const double* BX,

@@ -162,8 +162,6 @@ static inline int grid_for(int64_t n, int rpb, int cap) {
   return (int)g;
 }
 
-// Cap on the grid of the reduction kernels: partial buffers hold this many blocks.
-constexpr int kReduceBlocks = 152 * 8;
 
 template <typename T>
 int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const T* vm,
@@ -179,7 +177,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   if (bs < tpr) bs = ((tpr + 31) / 32) * 32;
   if (bs > 512) bs = 512;
   const int rpb = bs / tpr;
-  const int grid = grid_for(A.nrows, rpb, (mode == CSR_EIGRES || mode == CSR_MVDOT) ? kReduceBlocks : 0);
+  const int grid = grid_for(A.nrows, rpb, (mode == CSR_EIGRES || mode == CSR_MVDOT) ? kReduceBlocksHost : 0);
   if (nblocks_out) *nblocks_out = grid;
   if (A.nrows == 0) return PASE_OK;
   auto s = h->stream;
@@ -406,7 +404,7 @@ int launch_coldot(pase_ctx* h, int64_t n, int m, const double* X, const double* 
   if (m <= 0 || m % 2 != 0 || m > 512) return fail(PASE_ERR_INVALID_ARG, "coldot: bad m");
   if (n == 0) return launch_fill(h, m, 0.0, out);
   const int tpr = m / 2, rpb = 256 / tpr;
-  const int grid = grid_for(n, rpb, kReduceBlocks);
+  const int grid = grid_for(n, rpb, kReduceBlocksHost);
   k_coldot<<<grid, 256, 0, h->stream>>>(n, m, tpr, rpb, X, Y, h->w.partial);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
@@ -602,7 +600,7 @@ int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const do
   if (m > 256) return fail(PASE_ERR_INVALID_ARG, "block_resid: m > 256");
   const int groups = 256 / m;
   int64_t g = (n + groups - 1) / groups;
-  if (g > kReduceBlocks) g = kReduceBlocks;
+  if (g > kReduceBlocksHost) g = kReduceBlocksHost;
   if (g < 1) g = 1;
   *nblk_out = (int)g;
   k_block_resid<<<(int)g, 256, 0, h->stream>>>(n, m, AX, BX, ldin, lam, R, ldr, h->w.partial);

@@ -79,6 +79,61 @@ def test_spmm_am_parity(which, m, request):
         c.close()
 
 
+def test_spmm_am_fresh_handles_repeat(p2d):
+    """The fused A_h/M_h product from 100 fresh handles in a row (set-up, autotuner and
+    first launch each time), every result checked: a wrong M_h X once seen on the first
+    call of a process must not come back on any first call of a handle."""
+    pb, m = p2d, 8
+    X = pin.start_vectors(3, pb.N, m)
+    Xd = dev(X)
+    AXr, MXr = pb.A @ X, pb.M @ X
+    bad = []
+    for k in range(100):
+        c = Ctx(pb)
+        try:
+            AX = torch.full((pb.N, m), np.nan, dtype=torch.float64, device="cuda")
+            MX = torch.full_like(AX, np.nan)
+            P.pase_spmm_am(c.h, m, Xd, AX, MX)
+            ea, em = _colrel(host(AX), AXr), _colrel(host(MX), MXr)
+            if not (ea < 1e-13 and em < 1e-13):
+                bad.append((k, ea, em))
+        finally:
+            c.close()
+    assert not bad, bad
+
+
+_FIRST_CALL = r"""
+import numpy as np, torch, pase_inputs as pin
+from paper_2502_04589_gb300 import pase as P
+pb = pin.build_problem(2, 64, 8, mg_min=4)
+opt = P.pase_default_options(); opt.coarse_level = pb.coarse_level
+h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+m = 8
+X = pin.start_vectors(3, pb.N, m)
+AX = torch.empty(pb.N, m, dtype=torch.float64, device="cuda"); MX = torch.empty_like(AX)
+P.pase_spmm_am(h, m, torch.from_numpy(X).cuda(), AX, MX)
+rel = lambda a, b: np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0))
+ea, em = rel(AX.cpu().numpy(), pb.A @ X), rel(MX.cpu().numpy(), pb.M @ X)
+P.pase_destroy(h)
+print("ERR", ea, em)
+assert ea < 1e-13 and em < 1e-13
+"""
+
+
+def test_spmm_am_first_call_of_fresh_processes():
+    """The same product as the first GPU work of three fresh processes."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    for _ in range(3):
+        r = subprocess.run([sys.executable, "-c", _FIRST_CALL], cwd=root, env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
 def test_residual_parity(p3d):
     pb = p3d
     m = 16

@@ -240,3 +240,67 @@ def test_split_gram_nonfinite(p3d):
         assert np.isnan(res[1][idx]).any()
         fin = np.isfinite(res[0][idx])
         np.testing.assert_allclose(res[1][idx][fin], res[0][idx][fin], rtol=1e-12, atol=1e-12 * np.abs(res[0][idx][fin]).max())
+
+
+def _gram_refs(pb, W):
+    """Extended-precision Gram blocks of the definition (upper triangle mirrored), the
+    componentwise scales sum_r |w_ri||y_rj| and the normwise scales ||w_i||_2 ||y_j||_2."""
+    Wl = W.astype(np.longdouble)
+    out = []
+    for Mat in (pb.A, pb.M):
+        Y = Mat.astype(np.longdouble) @ Wl
+        ref = Wl.T @ Y
+        ref = (np.triu(ref) + np.triu(ref, 1).T).astype(np.float64)
+        comp = (np.abs(Wl).T @ np.abs(Y)).astype(np.float64)
+        comp = np.maximum(np.triu(comp), np.triu(comp, 1).T)
+        nw = np.linalg.norm(W, axis=0)
+        ny = np.linalg.norm(Y.astype(np.float64), axis=0)
+        norm = np.outer(nw, ny)
+        norm = np.maximum(np.triu(norm), np.triu(norm, 1).T)
+        out.append((ref, comp, norm))
+    return out
+
+
+def test_split_gram_wide_row_range(p3d):
+    """Rows scaled by 2^k, k uniform in [-30, 30] and shared by the row's columns (the shape
+    of localised vectors): the split Gram's largest error relative to sum_r |w_ri||y_rj|
+    stays within twice the FP64 kernel's and below 64 u."""
+    pb, m = p3d, 24
+    rng = np.random.default_rng(80)
+    W = pin.start_vectors(80, pb.N, m) * np.exp2(rng.integers(-30, 31, size=(pb.N, 1)))
+    res = {}
+    for split in (1, 0):
+        h = _handle(pb, split)
+        try:
+            res[split] = _project(h, pb, m, W)
+        finally:
+            P.pase_destroy(h)
+    for idx, (ref, comp, _) in enumerate(_gram_refs(pb, W)):
+        r_s = (np.abs(res[1][idx] - ref) / comp).max() / U53
+        r_f = (np.abs(res[0][idx] - ref) / comp).max() / U53
+        print(f"\nwide row range, block {idx}: split {r_s:.2f} u, FP64 {r_f:.2f} u (of sum |w||y|)")
+        assert r_s <= max(2.0 * r_f, 2.0) and r_s <= 64.0, (idx, r_s, r_f)
+
+
+def test_split_gram_disjoint_localised_columns(p3d):
+    """Columns localised in disjoint row ranges (1 on their own range, 2^-40 noise elsewhere):
+    the off-diagonal Gram entries are sums of products of a large and a tiny value, where the
+    split form, which scales each column by its largest entry, is not accurate relative to
+    sum_r |w_ri||y_rj|.  It stays accurate normwise, relative to ||w_i||_2 ||y_j||_2 (the
+    measure that bounds the Rayleigh-Ritz perturbation): below 8 u there."""
+    pb, m = p3d, 16
+    N = pb.N
+    W = 2.0 ** -40 * pin.start_vectors(81, N, m)
+    span = N // m
+    for j in range(m):
+        W[j * span:(j + 1) * span, j] = 1.0 + 0.5 * pin.start_vectors(82 + j, span, 1)[:, 0]
+    h = _handle(pb, 1)
+    try:
+        G = _project(h, pb, m, W)
+    finally:
+        P.pase_destroy(h)
+    for idx, (ref, comp, norm) in enumerate(_gram_refs(pb, W)):
+        rn = (np.abs(G[idx] - ref) / norm).max() / U53
+        rc = (np.abs(G[idx] - ref) / comp).max() / U53
+        print(f"\ndisjoint localised columns, block {idx}: {rn:.2f} u normwise, {rc:.3g} u of sum |w||y|")
+        assert rn <= 8.0, (idx, rn)

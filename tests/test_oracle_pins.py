@@ -409,3 +409,49 @@ def test_planted_mistakes_are_caught(monkeypatch):
     # a transposed restriction (P instead of P^T on the wrong side) breaks the shapes
     with pytest.raises(ValueError):
         pb.P @ (pb.A @ W)
+
+
+# ------------------------------------------------------------ the acceptance residual
+
+
+def test_relative_residuals_hand_computed():
+    """relative_residuals on a 2x2 diagonal pencil, values worked out by hand.
+
+    A = diag(2, 3), M = diag(1, 4), u = (1, 1):  A u = (2, 3), M u = (1, 4), ||M u|| = sqrt(17).
+      lambda = 1:  A u - M u   = (1, -1)  ->  sqrt(2) / sqrt(17)
+      lambda = 2:  A u - 2 M u = (0, -5)  ->  5 / (2 sqrt(17))
+      lambda = -1: A u + M u   = (3, 7)   ->  sqrt(58) / sqrt(17)   (|lambda| in the scale)
+    Dividing by ||u|| = sqrt(2) instead of ||M u||, by lambda^2 instead of |lambda|, or
+    dropping M from the residual changes every one of these numbers."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.diag([2.0, 3.0]))
+    M = sp.csr_matrix(np.diag([1.0, 4.0]))
+    U = np.ones((2, 3))
+    lam = np.array([1.0, 2.0, -1.0])
+    want = np.array([np.sqrt(2.0 / 17.0), 5.0 / (2.0 * np.sqrt(17.0)), np.sqrt(58.0 / 17.0)])
+    np.testing.assert_allclose(pase.relative_residuals(A, M, U, lam), want, rtol=1e-15)
+    # an exact eigenpair of the pencil has zero residual; scaling u leaves the value unchanged
+    e = np.array([[0.0], [1.0]])
+    assert pase.relative_residuals(A, M, 7.0 * e, np.array([0.75]))[0] == 0.0
+    V = np.array([[1.0, 3.0], [2.0, -1.0]])
+    np.testing.assert_allclose(pase.relative_residuals(A, M, 5.0 * V, np.array([1.5, 2.5])),
+                               pase.relative_residuals(A, M, V, np.array([1.5, 2.5])), rtol=1e-15)
+
+
+def test_relative_residuals_planted_mistakes_fail_the_pin():
+    """The hand-computed pin rejects the plausible slips in the residual's definition."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.diag([2.0, 3.0]))
+    M = sp.csr_matrix(np.diag([1.0, 4.0]))
+    U = np.ones((2, 3))
+    lam = np.array([1.0, 2.0, -1.0])
+    want = pase.relative_residuals(A, M, U, lam)
+    R = A @ U - (M @ U) * lam
+    slips = [
+        np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(U, axis=0)),           # ||u||
+        np.linalg.norm(R, axis=0) / (lam ** 2 * np.linalg.norm(M @ U, axis=0)),          # lambda^2
+        np.linalg.norm(A @ U - U * lam, axis=0) / (np.abs(lam) * np.linalg.norm(M @ U, axis=0)),  # no M
+        np.linalg.norm(R, axis=0) / np.abs(lam),                                          # paper's raw form
+    ]
+    for s in slips:
+        assert np.max(np.abs(s - want) / want) > 0.1

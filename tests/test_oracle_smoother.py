@@ -1,7 +1,8 @@
 """Pins of the learned-smoother oracle (no GPU): convolution against scipy.ndimage,
 gradients against finite differences, positive homogeneity, the Jacobi-equivalent
 weights, Adam's first step in closed form, the loss at delta = 0 and delta = e, and the
-learned V-cycle reducing to the Jacobi V-cycle."""
+learned V-cycle reducing to the Jacobi V-cycle, and the bf16 inference form within its
+derived rounding-error bound of the FP32-activation network."""
 import numpy as np
 import pytest
 import scipy.ndimage as ndi
@@ -148,8 +149,52 @@ def test_bf16_activations_exact_when_representable():
     a = sm.apply(pj, r, dinv, feat, 2, n1, act_bf16=True)
     b = sm.apply(pj, r, dinv, feat, 2, n1, act_bf16=False)
     np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_inference_form_within_rounding_bound(d, seed):
+    """The inference form (bf16 input and hidden activations) differs from the FP32-activation
+    network by less than the probabilistic bound derived from the bf16 unit roundoff (c = 5)
+    and by less than twice the first-order worst case; the probabilistic bound is a small
+    fraction of the output scale, so it means something."""
+    A, n, feat = _tiny(d)
+    n1 = n - 1
+    dinv = 1.0 / A.diagonal()
+    p = pin.smoother_init(d, seed=3 + seed, noise=0.3)
+    r = np.random.default_rng(2 + seed).standard_normal((A.shape[0], 3))
+    a = sm.apply(p, r, dinv, feat, d, n1, act_bf16=True)
+    b = sm.apply(p, r, dinv, feat, d, n1, act_bf16=False)
+    worst = sm.inference_error_bound(p, r, dinv, feat, d, n1, kind="worst")
+    prob = sm.inference_error_bound(p, r, dinv, feat, d, n1, kind="prob")
+    slack = 1e-12 * np.max(np.abs(b), axis=0)
+    assert np.any(np.abs(a - b) > 0.0)  # the roundings do act
+    assert np.all(np.abs(a - b) <= 2.0 * worst + slack)  # 2: second-order terms, flips
+    assert np.all(np.abs(a - b) <= prob + slack)
+    assert np.all(prob <= worst * 5.0 + slack)
+    assert np.max(prob) < 0.1 * np.max(np.abs(b))
+
+
+def test_inference_bound_rejects_coarser_rounding(monkeypatch):
+    """Planted mistake: activations rounded to 4 significand bits instead of 8 leave the
+    probabilistic bf16 bound."""
+    A, n, feat = _tiny(2)
+    n1 = n - 1
+    dinv = 1.0 / A.diagonal()
     p = pin.smoother_init(2, seed=3, noise=0.3)
-    r2 = np.random.default_rng(2).standard_normal((A.shape[0], 3))
-    a = sm.apply(p, r2, dinv, feat, 2, n1, act_bf16=True)
-    b = sm.apply(p, r2, dinv, feat, 2, n1, act_bf16=False)
-    assert np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)) < 3e-2
+    r = np.random.default_rng(2).standard_normal((A.shape[0], 3))
+    b = sm.apply(p, r, dinv, feat, 2, n1, act_bf16=False)
+    bound = sm.inference_error_bound(p, r, dinv, feat, 2, n1, kind="prob")
+    pr = sm.bf16_round(p)  # the parameters as the forward pass uses them
+    exact = sm.bf16_round
+
+    def coarse(x):
+        y = exact(x)
+        e = np.floor(np.log2(np.maximum(np.abs(y), 1e-300)))
+        q = 2.0 ** (e - 3)
+        return np.where(y == 0, 0.0, np.round(y / q) * q)
+
+    monkeypatch.setattr(sm, "bf16_round", coarse)
+    a = sm.apply(pr, r, dinv, feat, 2, n1, round_bf16=False, act_bf16=True)
+    monkeypatch.undo()
+    assert np.any(np.abs(a - b) > bound)
