@@ -95,7 +95,39 @@ typedef struct {
                           8-bit digit slices, exact FP32 sums per digit diagonal, 64-bit
                           integer recombination; error a few units of 2^-53 relative to the
                           products of the row and column maxima); 0: FP64 CUDA cores      */
+  int stencil;         /* 1 (default): in PASE_PREC_MIXED, every multigrid level whose matrix
+                          couples each node only to its 3^d neighbours on an n1^d grid
+                          (x-fastest order; Q1 operators and their Galerkin coarse levels)
+                          keeps its FP32 values by grid tap, and the FP32 Jacobi sweeps,
+                          residuals and products on it run in a structured kernel without
+                          column indices; 0: the CSR kernel everywhere                    */
+  int post_solve;      /* 0 (default): one linear-solve phase per iteration (Alg. 1);
+                          1: the two-solve form of Alg. 3 - after the Rayleigh-Ritz of an
+                          iteration that has not converged, a second linear solve
+                          A_h u = lambda M_h u-hat from the prolongated u-hat (step 7) feeds
+                          the next iteration's step 3; returned vectors are always the
+                          Rayleigh-Ritz ones                                              */
+  int aug_transform;   /* congruence applied to the augmented pencil before step (c), §4:
+                          PASE_AUG_PLAIN (default) none, PASE_AUG_PRECOND_A, _PRECOND_B or
+                          _PRECOND_BA (see below)                                        */
 } pase_options;
+
+/* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the
+ * congruence [[I, Z], [0, I]] (eigenvectors mapped back by u_H = u~_H - Z gamma~):
+ *   PLAIN       Z = 0;             preconditioner: the block factorisation of A_Hh
+ *                                   (coarse V-cycle for A_H^-1, Schur complement of alpha)
+ *   PRECOND_A   Z ~ A_H^-1 a_h     (A_Hh becomes block diagonal);  same preconditioner
+ *   PRECOND_B   Z ~ B_H^-1 b_h     (B_Hh becomes block diagonal);  block-diagonal
+ *                                   preconditioner (coarse V-cycle, alpha~^-1)
+ *   PRECOND_BA  PRECOND_B, then the block-factorisation preconditioner of the transformed
+ *               A_Hh (the A-type factorisation inside the linear solves)
+ * Z comes from a coarse V-cycle (A_H) or Jacobi-preconditioned CG (B_H); the transformed
+ * blocks are formed from that Z, so the pencil stays exactly congruent whatever its
+ * accuracy. */
+#define PASE_AUG_PLAIN 0
+#define PASE_AUG_PRECOND_A 1
+#define PASE_AUG_PRECOND_B 2
+#define PASE_AUG_PRECOND_BA 3
 
 #define PASE_SMOOTHER_JACOBI 0
 #define PASE_SMOOTHER_LEARNED 1
@@ -211,6 +243,17 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
  * [N][m]).  The hot kernel of steps (b) and the residual; exposed for measurement. */
 int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
 
+/* `sweeps` damped-Jacobi sweeps x <- x + omega D^-1 (b - A_h x) on the fine level (the
+ * smoother of step (a), Alg. 3 step 3), in the precision the handle smooths in: FP32 for
+ * PASE_PREC_MIXED (B and X rounded to FP32 on entry, X returned widened to FP64), FP64
+ * otherwise.  B, X: [N][m]; X is updated in place.  For tests and measurement. */
+int pase_smooth(pase_handle h, int m, int sweeps, const double* B, double* X);
+
+/* Which form the FP32 fine-level sweeps take after pase_setup: 3 or 2 when the fine
+ * matrix was recognised as a grid-neighbour stencil in that many dimensions (structured
+ * kernel), 0 for the CSR kernel. */
+int pase_smoother_form(pase_handle h);
+
 /* Residual of a block, for callers that cannot allocate device memory.  Has no
  * counterpart in the paper: it is pase_residual without a handle and without any device
  * allocation, for code that runs under a memory arena owning every device byte, inside
@@ -247,6 +290,7 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_SYGV3 6         /* the same with n = 3m, k = m (step-(c) Rayleigh-Ritz) */
 #define PASE_KERNEL_PROLONG_SPLIT 7 /* W C over N_h rows on the tensor cores (split digits; m <= 128) */
 #define PASE_KERNEL_GRAM_SPLIT 8    /* both Gram blocks W^T R, W^T W on the tensor cores (split digits) */
+#define PASE_KERNEL_JACOBI_FP32_CSR 9 /* the FP32 sweep in the CSR kernel even on a structured grid  */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
 /* Live timing of one kernel while the handle works (pase_solve, pase_iterate, ...): with

@@ -7,14 +7,15 @@ current block and Lambda its Ritz values:
  (b) projection     aH = P^T A_h W, bH = P^T M_h W, GA = W^T A_h W, GM = W^T M_h W
                     (the blocks a_h, b_h, alpha, beta of Alg. 3 step 4)
  (c) augmented eig  [[A_H, aH],[aH^T, GA]] c = lambda [[M_H, bH],[bH^T, GM]] c,
-                    the m smallest pairs, B-normalised                        (Alg. 3 step 5)
+                    the m smallest pairs, B-normalised                        (Alg. 3 step 5);
+                    the PRECOND-A / -B / -B-A congruences of §4 transform this pencil
  (d) prolongation   U <- P C_H + W C_W                                        (Alg. 3 step 6)
 
 Readings taken where the paper is silent or garbled:
 * Alg. 3 step 6 prints the product as gamma u-hat; the shapes (N x k times k x k)
   force u-hat gamma, i.e. W C_W.
-* One linear-solve phase per Rayleigh-Ritz (Alg. 1); the post-solve of Alg. 3 step 7
-  is folded into the next iteration's step 3.
+* One linear-solve phase per Rayleigh-Ritz (Alg. 1) by default; Solver.solve(...,
+  post_solve=True) runs the two-solve form of Alg. 3 (steps 3 and 7).
 * Vectors are M-normalised (U^T M U = I) rather than a(u,u) = 1; the two differ by the
   factor sqrt(lambda) per column.
 * Convergence is ||A u - lambda M u||_2 / (lambda ||M u||_2) <= tol for the first nev
@@ -107,6 +108,32 @@ def precond_a_back(ahat, uH_t, gamma_t):
     return uH_t - ahat @ gamma_t, gamma_t
 
 
+def precond_b(A_H, M_H, aH, bH, GA, GM):
+    """PRECOND-B (§4): the same kind of congruence built from B_Hh's factorisation,
+    [[I, B_H^-1 b_h],[0, I]], which makes B_Hh block diagonal.
+
+    Returns (bhat, a_t, alpha_t, beta_t) with bhat = M_H^-1 bH, a_t = aH - A_H bhat,
+    alpha_t = GA - bhat^T aH - aH^T bhat + bhat^T A_H bhat, beta_t = GM - bH^T bhat.
+    The transformed pencil is [[A_H, a_t],[a_t^T, alpha_t]], [[M_H, 0],[0, beta_t]];
+    its eigenvectors map back as in precond_a_back (with bhat in place of ahat)."""
+    bhat = sl.cho_solve(sl.cho_factor(M_H.toarray()), bH)
+    a_t = aH - A_H @ bhat
+    alpha_t = GA - bhat.T @ aH - aH.T @ bhat + bhat.T @ (A_H @ bhat)
+    beta_t = GM - bH.T @ bhat
+    return bhat, a_t, alpha_t, beta_t
+
+
+def precond_ba(A_H, M_H, aH, bH, GA, GM):
+    """PRECOND-B-A (§4): PRECOND-B, and for the linear solves inside the augmented
+    eigensolver the block factorisation of the transformed A_Hh, as PRECOND-A factors A_Hh:
+        [[A_H, a_t],[a_t^T, alpha_t]] = L diag(A_H, S) L^T,  L = [[I, 0],[ahat2^T, I]],
+    ahat2 = A_H^-1 a_t, S = alpha_t - a_t^T ahat2.
+    Returns (bhat, a_t, alpha_t, beta_t, ahat2, S)."""
+    bhat, a_t, alpha_t, beta_t = precond_b(A_H, M_H, aH, bH, GA, GM)
+    ahat2 = sl.cho_solve(sl.cho_factor(A_H.toarray()), a_t)
+    return bhat, a_t, alpha_t, beta_t, ahat2, alpha_t - a_t.T @ ahat2
+
+
 def prolongate(P, W, C_H, C_W):
     """Step (d): U = P C_H + W C_W."""
     return P @ C_H + W @ C_W
@@ -142,9 +169,13 @@ class Solver:
         U_new = prolongate(self.P, W, C_H, C_W)
         return lam_new, U_new, dict(W=W, aH=aH, bH=bH, GA=GA, GM=GM, C_H=C_H, C_W=C_W)
 
-    def solve(self, nev, m, tol, U0=None, s=2, max_iter=100, solver="vcycle"):
+    def solve(self, nev, m, tol, U0=None, s=2, max_iter=100, solver="vcycle", post_solve=False):
         """Iterate from U0 (random start, first step (a) skipped) or from the coarse
-        start until the first nev relative residuals are <= tol."""
+        start until the first nev relative residuals are <= tol.
+
+        post_solve: the two-solve form of Alg. 3 - an iteration that has not converged is
+        followed by the step-7 solve A_h u = lambda M_h u-hat from the Rayleigh-Ritz block
+        u-hat, whose result is the next iteration's step-3 initial guess."""
         if U0 is None:
             lam, U = coarse_start(self.A_H, self.M_H, self.P, m)
             first_solve = True
@@ -154,6 +185,8 @@ class Solver:
         history = []
         it = 0
         for it in range(1, max_iter + 1):
+            if post_solve and it > 1:
+                U = linear_solve(self.A, self.M, U, lam, s, self.hier, solver)
             lam, U, _ = self.iteration(U, lam, s, solve=first_solve or it > 1, solver=solver)
             res = relative_residuals(self.A, self.M, U, lam)
             history.append(res.copy())

@@ -314,6 +314,19 @@ static int reserve(pase_ctx* h, int m) {
   PASE_TRY(dev_alloc_t(h, &w.smallvec, (size_t)16 * m));
   PASE_TRY(dev_alloc_t(h, &w.status, 8));
   PASE_TRY(dev_alloc_t(h, &w.colexp, 3 * 128));
+  if (h->opt.aug_transform != PASE_AUG_PLAIN) {
+    const size_t hm = (size_t)NH * m;
+    PASE_TRY(dev_alloc_t(h, &w.Zt, hm));
+    PASE_TRY(dev_alloc_t(h, &w.aT, hm));
+    PASE_TRY(dev_alloc_t(h, &w.bT, hm));
+    PASE_TRY(dev_alloc_t(h, &w.GAT, (size_t)m * m));
+    PASE_TRY(dev_alloc_t(h, &w.GMT, (size_t)m * m));
+    PASE_TRY(dev_alloc_t(h, &w.tr, hm));
+    PASE_TRY(dev_alloc_t(h, &w.tz, hm));
+    PASE_TRY(dev_alloc_t(h, &w.tp, hm));
+    PASE_TRY(dev_alloc_t(h, &w.tq, hm));
+    PASE_TRY(dev_alloc_t(h, &w.tsc, 4 * (size_t)m));
+  }
   PASE_TRY(dev_alloc_t(h, &h->tc_err, 1));
   PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
   PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
@@ -709,12 +722,18 @@ static int coarse_apply(pase_ctx* h, const double* r, int ld, double* y, int ldo
 // step 1): with ahat = Ainv aH and S = GA - aH^T ahat (PRECOND-A's alpha~),
 //   y1' = Ainv r1,  y2 = S^-1 (r2 - aH^T y1'),  y1 = y1' - ahat y2.
 // Ainv is the coarse V-cycle, so T is symmetric positive definite.
-static int aug_precond(pase_ctx* h, const double* R, int ld, double* Y, int ldo, const double* aH) {
+// blockdiag: the block-diagonal preconditioner [Ainv r1; GA^-1 r2] (no coupling terms).
+static int aug_precond(pase_ctx* h, const double* R, int ld, double* Y, int ldo, const double* aH,
+                       bool blockdiag = false) {
   Work& w = h->w;
   const int m = w.m;
   const int64_t NH = h->NH;
   PASE_TRY(coarse_apply(h, R, ld, Y, ldo));
   double* y2 = Y + NH * ldo;
+  if (blockdiag) {
+    PASE_TRY(launch_copy_cols(h, m, m, R + NH * ld, ld, y2, ldo));
+    return small_chol_solve(h, m, m, w.schur, m, y2, ldo, w.status + 2, false);
+  }
   PASE_TRY(ts_gram(h, NH, m, m, aH, m, Y, ldo, w.coef, m, false));
   PASE_TRY(launch_geam(h, m, m, 1.0, R + NH * ld, ld, -1.0, w.coef, m, y2, ldo));
   PASE_TRY(small_chol_solve(h, m, m, w.schur, m, y2, ldo, w.status + 2, false));
@@ -722,14 +741,77 @@ static int aug_precond(pase_ctx* h, const double* R, int ld, double* Y, int ldo,
   return PASE_OK;
 }
 
-static int aug_precond_setup(pase_ctx* h, const double* aH, const double* GA) {
+static int aug_precond_setup(pase_ctx* h, const double* aH, const double* GA, bool blockdiag = false) {
   Work& w = h->w;
   const int m = w.m;
-  PASE_TRY(coarse_apply(h, aH, m, w.ahat, m));
-  PASE_TRY(ts_gram(h, h->NH, m, m, aH, m, w.ahat, m, w.coef, m, false));
-  PASE_TRY(launch_geam(h, m, m, 1.0, GA, m, -1.0, w.coef, m, w.schur, m));
+  if (blockdiag) {  // S = GA
+    PASE_TRY(launch_copy_cols(h, m, m, GA, m, w.schur, m));
+  } else {
+    PASE_TRY(coarse_apply(h, aH, m, w.ahat, m));
+    PASE_TRY(ts_gram(h, h->NH, m, m, aH, m, w.ahat, m, w.coef, m, false));
+    PASE_TRY(launch_geam(h, m, m, 1.0, GA, m, -1.0, w.coef, m, w.schur, m));
+  }
   // factor (the Cholesky reads the lower triangle only)
   PASE_TRY(small_chol_solve(h, m, 0, w.schur, m, nullptr, 0, w.status + 1, true));
+  return PASE_OK;
+}
+
+// Z ~ M_H^-1 B for B [N_H][m]: `steps` Jacobi-preconditioned CG steps per column from
+// zero on the coarse mass matrix (well conditioned: a dozen steps gain about two digits).
+static int coarse_mass_solve(pase_ctx* h, const double* B, double* Z, int steps) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int64_t NH = h->NH;
+  DevCSR Mc = h->AH;
+  Mc.val = h->MH_val;
+  double *r = w.tr, *z = w.tz, *p = w.tp, *q = w.tq;
+  double *rz = w.tsc, *rz_new = w.tsc + m, *pq = w.tsc + 2 * m, *coef = w.tsc + 3 * m;
+  const size_t bytes = sizeof(double) * NH * m;
+  PASE_CUDA(cudaMemsetAsync(Z, 0, bytes, h->stream));
+  PASE_CUDA(cudaMemcpyAsync(r, B, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  PASE_TRY(launch_scale_dinv<double>(h, NH, m, h->MH_dinv, 1.0, r, z));
+  PASE_TRY(launch_coldot(h, NH, m, r, z, rz));
+  PASE_CUDA(cudaMemcpyAsync(p, z, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  for (int k = 0; k < steps; ++k) {
+    int nb = 0;
+    PASE_TRY(launch_csr<double>(h, CSR_MVDOT, m, Mc, Mc.val, nullptr, p, nullptr, nullptr, nullptr, nullptr, 0.0, q,
+                                nullptr, w.partial, &nb));
+    PASE_TRY(launch_reduce_partials(h, nb, m, w.partial, pq));
+    PASE_TRY(launch_ratio(h, m, rz, pq, coef));
+    PASE_TRY(launch_cg_update(h, NH, m, coef, p, q, Z, r));
+    if (k + 1 == steps) break;
+    PASE_TRY(launch_scale_dinv<double>(h, NH, m, h->MH_dinv, 1.0, r, z));
+    PASE_TRY(launch_coldot(h, NH, m, r, z, rz_new));
+    PASE_TRY(launch_ratio(h, m, rz_new, rz, coef));
+    PASE_TRY(launch_cg_dir(h, NH, m, coef, z, p));
+    std::swap(rz, rz_new);
+  }
+  return PASE_OK;
+}
+
+// The congruence T = [[I, Z], [0, I]] of §4 applied to the augmented pencil: with
+// D_A = A_H Z - aH and D_B = M_H Z - bH,
+//   aT = -D_A,  GAT = GA + Z^T D_A - aH^T Z   (= GA - Z^T aH - aH^T Z + Z^T A_H Z)
+//   bT = -D_B,  GMT = GM + Z^T D_B - bH^T Z
+// so that [[A_H, aT],[aT^T, GAT]] = T^-T A_Hh T^-1 and likewise for B_Hh, for any Z.
+static int aug_congruence(pase_ctx* h, const double* aH, const double* bH, const double* GA, const double* GM) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int64_t NH = h->NH;
+  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, m, h->AH, h->AH.val, h->MH_val, w.Zt, nullptr, nullptr, nullptr, nullptr,
+                              0.0, w.tr, w.tz, nullptr, nullptr));
+  PASE_TRY(launch_geam(h, NH, m, 1.0, w.tr, m, -1.0, aH, m, w.tr, m));  // D_A
+  PASE_TRY(launch_geam(h, NH, m, 1.0, w.tz, m, -1.0, bH, m, w.tz, m));  // D_B
+  PASE_TRY(launch_geam(h, NH, m, -1.0, w.tr, m, 0.0, w.tr, m, w.aT, m));
+  PASE_TRY(launch_geam(h, NH, m, -1.0, w.tz, m, 0.0, w.tz, m, w.bT, m));
+  PASE_TRY(ts_gram(h, NH, m, m, w.Zt, m, w.tr, m, w.coef, m, false));   // Z^T D_A
+  PASE_TRY(launch_geam(h, m, m, 1.0, GA, m, 1.0, w.coef, m, w.GAT, m));
+  PASE_TRY(ts_gram(h, NH, m, m, aH, m, w.Zt, m, w.coef, m, false));     // aH^T Z
+  PASE_TRY(launch_geam(h, m, m, 1.0, w.GAT, m, -1.0, w.coef, m, w.GAT, m));
+  PASE_TRY(ts_gram(h, NH, m, m, w.Zt, m, w.tz, m, w.coef, m, false));   // Z^T D_B
+  PASE_TRY(launch_geam(h, m, m, 1.0, GM, m, 1.0, w.coef, m, w.GMT, m));
+  PASE_TRY(ts_gram(h, NH, m, m, bH, m, w.Zt, m, w.coef, m, false));     // bH^T Z
+  PASE_TRY(launch_geam(h, m, m, 1.0, w.GMT, m, -1.0, w.coef, m, w.GMT, m));
   return PASE_OK;
 }
 
@@ -738,6 +820,7 @@ struct BlockOp {
   int64_t n;
   int kind;  // 0: augmented pencil, 1: coarse pencil (A_H, M_H)
   const double *aH, *bH, *GA, *GM;
+  bool blockdiag = false;  // augmented pencil: block-diagonal preconditioner
 };
 
 static int op_apply(pase_ctx* h, const BlockOp& op, const double* Y, int ld, double* AY, double* BY, int ldo) {
@@ -746,7 +829,7 @@ static int op_apply(pase_ctx* h, const BlockOp& op, const double* Y, int ld, dou
                             nullptr, 0.0, AY, BY, nullptr, nullptr, ld, ldo);
 }
 static int op_precond(pase_ctx* h, const BlockOp& op, const double* R, int ld, double* Y, int ldo) {
-  if (op.kind == 0) return aug_precond(h, R, ld, Y, ldo, op.aH);
+  if (op.kind == 0) return aug_precond(h, R, ld, Y, ldo, op.aH, op.blockdiag);
   return coarse_apply(h, R, ld, Y, ldo);
 }
 
@@ -847,15 +930,30 @@ static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, c
   const int m = w.m;
   const int m3 = 3 * m;
   const int64_t NH = h->NH, nc = NH + m;
-  PASE_TRY(aug_precond_setup(h, aH, GA));
-  // start block [0; I]
+  const int tr = h->opt.aug_transform;
+  if (tr != PASE_AUG_PLAIN) {  // §4: the pencil seen through T = [[I, Z], [0, I]]
+    if (tr == PASE_AUG_PRECOND_A) PASE_TRY(coarse_apply(h, aH, m, w.Zt, m));     // Z ~ A_H^-1 aH
+    else PASE_TRY(coarse_mass_solve(h, bH, w.Zt, 12));                        // Z ~ M_H^-1 bH
+    PASE_TRY(aug_congruence(h, aH, bH, GA, GM));
+    aH = w.aT;
+    bH = w.bT;
+    GA = w.GAT;
+    GM = w.GMT;
+  }
+  const bool blockdiag = tr == PASE_AUG_PRECOND_B;
+  PASE_TRY(aug_precond_setup(h, aH, GA, blockdiag));
+  // start block: the warm start u_H = 0, gamma = I, i.e. [0; I], which the congruence maps
+  // to [Z; I]
   PASE_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * nc * m3, h->stream));
   PASE_TRY(launch_set_identity_rows(h, NH, m, m3, w.S));
-  BlockOp op{nc, 0, aH, bH, GA, GM};
+  if (tr != PASE_AUG_PLAIN) PASE_TRY(launch_copy_cols(h, NH, m, w.Zt, m, w.S, m3));
+  BlockOp op{nc, 0, aH, bH, GA, GM, blockdiag};
   const double tol = h->aug_tol_now > 0 ? h->aug_tol_now : h->opt.aug_tol;
   PASE_TRY(block_eigensolver(h, op, lam, tol, h->opt.aug_max_iter, h->aug_nconv, iters));
   PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, CH, m));
   PASE_TRY(launch_copy_cols(h, m, m, w.S + NH * m3, m3, CW, m));
+  if (tr != PASE_AUG_PLAIN)  // back to the original basis: u_H = u~_H - Z gamma~ (Alg. 5 step 3)
+    PASE_TRY(ts_gemm(h, NH, m, m, -1.0, w.Zt, m, CW, m, 1.0, CH, m));
   return PASE_OK;
 }
 
@@ -923,6 +1021,9 @@ void pase_default_options(pase_options* o) {
   o->autotune = 1;
   o->smoother = PASE_SMOOTHER_JACOBI;
   o->split_gemm = 1;
+  o->stencil = 1;
+  o->post_solve = 0;
+  o->aug_transform = PASE_AUG_PLAIN;
 }
 
 const char* pase_status_string(int code) {
@@ -956,6 +1057,8 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
   if ((o.precision != PASE_PREC_FP64 && o.precision != PASE_PREC_MIXED) || o.inner_steps < 1 || o.nu1 < 0 ||
       o.linear_solver < PASE_SOLVER_VCYCLE || o.linear_solver > PASE_SOLVER_MGCG ||
       (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
+      (o.post_solve != 0 && o.post_solve != 1) || o.aug_transform < PASE_AUG_PLAIN ||
+      o.aug_transform > PASE_AUG_PRECOND_BA ||
       o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||
       !(o.aug_tol > 0.0)) {
     delete h;
@@ -1053,6 +1156,7 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
     if (mixed) {
       std::vector<float> d32(dinv.begin(), dinv.end());
       PASE_TRY(upload_vec(h, d32, &L.dinv32));
+      if (h->opt.stencil) PASE_TRY(stencil_setup(h, Al[l], dinv, L.A));
     }
     if (l < n_interp) {
       PASE_TRY(upload_csr(h, Pc[l], L.P, mixed, false, nullptr));
@@ -1072,6 +1176,14 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
     DevCSR Mtmp;
     PASE_TRY(upload_csr(h, MHc, Mtmp, false, true, &h->AH));
     h->MH_val = Mtmp.val;
+    std::vector<double> md(MHc.nrows, 0.0);
+    for (int64_t i = 0; i < MHc.nrows; ++i) {
+      for (int64_t k = MHc.rowptr[i]; k < MHc.rowptr[i + 1]; ++k)
+        if (MHc.col[k] == i) md[i] = MHc.val[k];
+      if (!(md[i] > 0.0)) return fail(PASE_ERR_NOT_SPD, "non-positive diagonal entry in M_H");
+      md[i] = 1.0 / md[i];
+    }
+    PASE_TRY(upload_vec(h, md, &h->MH_dinv));
   }
   h->ncoarsest = Ac.nrows;
   PASE_TRY(upload_vec(h, cinv, &h->cinv));
@@ -1226,6 +1338,45 @@ int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX) 
   return PASE_OK;
 }
 
+int pase_smooth(pase_handle h, int m, int sweeps, const double* B, double* X) {
+  PASE_TRY(check_m(h, m));
+  if (!B || !X || sweeps < 1) return fail(PASE_ERR_INVALID_ARG, "pase_smooth: bad argument");
+  Stage st(h);
+  const size_t nm = (size_t)h->N * m;
+  const void* dB;
+  void* dX;
+  PASE_TRY(st.in(B, nm * sizeof(double), &dB));
+  PASE_TRY(st.out(X, nm * sizeof(double), &dX, true));
+  const Level& L0 = h->lv[0];
+  Work& w = h->w;
+  if (h->opt.precision == PASE_PREC_MIXED) {
+    PASE_TRY(launch_f64_to_f32(h, (int64_t)nm, (const double*)dB, w.fb[0]));
+    PASE_TRY(launch_f64_to_f32(h, (int64_t)nm, (const double*)dX, w.fx[0]));
+    float *cur = w.fx[0], *other = w.ft1[0];
+    for (int s = 0; s < sweeps; ++s) {
+      PASE_TRY(launch_csr<float>(h, CSR_JACOBI, m, L0.A, L0.A.val32, nullptr, cur, nullptr, w.fb[0], L0.dinv32,
+                                 nullptr, h->opt.omega, other, nullptr, nullptr, nullptr));
+      std::swap(cur, other);
+    }
+    PASE_TRY(launch_f32_to_f64(h, (int64_t)nm, cur, (double*)dX));
+  } else {
+    double *cur = (double*)dX, *other = w.T1;
+    for (int s = 0; s < sweeps; ++s) {
+      PASE_TRY(launch_csr<double>(h, CSR_JACOBI, m, L0.A, L0.A.val, nullptr, cur, nullptr, (const double*)dB,
+                                  L0.dinv, nullptr, h->opt.omega, other, nullptr, nullptr, nullptr));
+      std::swap(cur, other);
+    }
+    if (cur != (double*)dX)
+      PASE_CUDA(cudaMemcpyAsync(dX, cur, nm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return st.finish();
+}
+
+int pase_smoother_form(pase_handle h) {
+  if (!h || !h->ready || h->lv.empty()) return 0;
+  return h->lv[0].A.st_val ? h->lv[0].A.st_dim : 0;
+}
+
 int64_t pase_kernel_count(pase_handle h) { return h ? h->launches : 0; }
 
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch) {
@@ -1234,9 +1385,9 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   Work& w = h->w;
   const size_t nm = (size_t)h->N * m;
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
-  if (kernel == PASE_KERNEL_JACOBI_FP32 && !mixed)
+  if ((kernel == PASE_KERNEL_JACOBI_FP32 || kernel == PASE_KERNEL_JACOBI_FP32_CSR) && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_GRAM_SPLIT)
+  if (kernel < 0 || kernel > PASE_KERNEL_JACOBI_FP32_CSR)
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
@@ -1274,6 +1425,12 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
       case PASE_KERNEL_JACOBI_FP32:
         return launch_csr<float>(h, CSR_JACOBI, m, L0.A, L0.A.val32, nullptr, w.fx[0], nullptr, w.fb[0], L0.dinv32,
                                  nullptr, h->opt.omega, w.ft1[0], nullptr, nullptr, nullptr);
+      case PASE_KERNEL_JACOBI_FP32_CSR: {  // the CSR kernel even where the structured one applies
+        DevCSR A = L0.A;
+        A.st_val = nullptr;
+        return launch_csr<float>(h, CSR_JACOBI, m, A, L0.A.val32, nullptr, w.fx[0], nullptr, w.fb[0], L0.dinv32,
+                                 nullptr, h->opt.omega, w.ft1[0], nullptr, nullptr, nullptr);
+      }
       case PASE_KERNEL_GRAM_FP64:
         return ts_gram(h, h->N, m, m, w.W, m, w.R, m, w.GA, m, true);
       case PASE_KERNEL_PROLONG_FP64:
@@ -1386,6 +1543,19 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
         break;
       }
       h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-3 * worst) : h->opt.aug_tol;
+      if (h->opt.post_solve && iter > 0) {
+        // Alg. 3 step 7: A_h u = lambda M_h u-hat from the Rayleigh-Ritz block u-hat (its
+        // residual is in w.R), then the residual of the new block for step 3
+        PASE_CUDA(cudaEventRecord(ev[0], h->stream));
+        PASE_TRY(step_linear_solve_graphed(h, w.U, w.W));
+        PASE_CUDA(cudaMemcpyAsync(w.U, w.W, nm, cudaMemcpyDeviceToDevice, h->stream));
+        PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+        PASE_CUDA(cudaEventRecord(ev[1], h->stream));
+        PASE_CUDA(cudaEventSynchronize(ev[1]));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        st.phase_ms[0] += ms;
+      }
     } else {
       h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol;
     }

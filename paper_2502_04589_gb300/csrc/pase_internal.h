@@ -65,6 +65,10 @@ struct DevCSR {
   double* val = nullptr;   // FP64 values
   float* val32 = nullptr;  // FP32 copy (mixed precision), may be null
   int block = 0;           // threads per block of the CSR kernel (0 = 256; set by the autotuner)
+  // structured-grid form of the FP32 values (stencil.cu): 3^d tap planes then 1 / a_ii,
+  // x extent padded to st_xp; null when the matrix is not a grid-neighbour stencil
+  float* st_val = nullptr;
+  int st_dim = 0, st_n1 = 0, st_xp = 0;
 };
 
 struct Level {
@@ -108,6 +112,9 @@ struct Work {
   double* cgs = nullptr;                                // CG scalars: (r,z) x2, (p,Ap), ratio [4m]
   int* status = nullptr;                                // device status words [8]
   int* colexp = nullptr;                                // split Gram column exponents [3][128]
+  // step-(c) congruences (aug_transform): Z, the transformed blocks, coarse CG buffers
+  double *Zt = nullptr, *aT = nullptr, *bT = nullptr, *GAT = nullptr, *GMT = nullptr;  // [N_H][m], [m][m]
+  double *tr = nullptr, *tz = nullptr, *tp = nullptr, *tq = nullptr, *tsc = nullptr;   // [N_H][m] x4, [4m]
   // host pinned mirror for small readbacks
   double* h_small = nullptr;
   int* h_status = nullptr;
@@ -161,6 +168,7 @@ struct pase_ctx {
   pase::DevCSR Pd, PdT;      // direct interpolation V_H -> V_h and its transpose
   pase::DevCSR AH;           // coarse pencil as given: A_H with values, M_H values below
   double* MH_val = nullptr;
+  double* MH_dinv = nullptr;  // 1 / diag(M_H) (Jacobi-preconditioned CG with the coarse mass)
   int64_t ncoarsest = 0;     // dense inverse of the coarsest multigrid operator
   double* cinv = nullptr;
   float* cinv32 = nullptr;
@@ -223,6 +231,12 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
                const T* X, const T* X2, const T* B, const T* dinv, const double* lam, double omega,
                T* Y1, T* Y2, double* partial, int* nblocks_out, int64_t ldx = 0,
                int64_t ldy = 0);
+
+// structured-grid FP32 kernels (stencil.cu)
+int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv, DevCSR& d);
+bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy);
+int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X, const float* B, double omega,
+                   float* Y);
 
 // elementwise
 template <typename T>

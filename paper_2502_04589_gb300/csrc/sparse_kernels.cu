@@ -183,9 +183,16 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
   auto s = h->stream;
   const T om = (T)omega;
   int prof_id = -1;
-  if (h->prof_kernel >= 0 && !h->lv.empty() && &A == &h->lv[0].A) {
+  if (h->prof_kernel >= 0 && !h->lv.empty() && A.rowptr == h->lv[0].A.rowptr) {
     if (mode == CSR_MV_AM && sizeof(T) == 8) prof_id = PASE_KERNEL_SPMM_AM_FP64;
     if (mode == CSR_JACOBI) prof_id = sizeof(T) == 8 ? PASE_KERNEL_JACOBI_FP64 : PASE_KERNEL_JACOBI_FP32;
+  }
+  if (sizeof(T) == 4 && h->opt.stencil && stencil_ok(A, mode, m, ldx, ldy)) {
+    // grid-neighbour operator: the structured FP32 kernel (no column indices, X reuse in registers)
+    prof_begin(h, prof_id);
+    const int rc = launch_stencil(h, mode, m, A, (const float*)X, (const float*)B, omega, (float*)Y1);
+    prof_end(h, prof_id);
+    return rc;
   }
   prof_begin(h, prof_id);
 #define PASE_CSR_CASE(MD)                                                                   \

@@ -21,6 +21,10 @@ PASE_SOLVER_CG = 1
 PASE_SOLVER_MGCG = 2
 PASE_SMOOTHER_JACOBI = 0
 PASE_SMOOTHER_LEARNED = 1
+PASE_AUG_PLAIN = 0
+PASE_AUG_PRECOND_A = 1
+PASE_AUG_PRECOND_B = 2
+PASE_AUG_PRECOND_BA = 3
 
 
 class PaseCSR(ctypes.Structure):
@@ -36,7 +40,8 @@ class PaseOptions(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("aug_max_iter", ctypes.c_int),
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int), ("stencil", ctypes.c_int),
+                ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):
@@ -69,7 +74,8 @@ _lib = None
 EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
             "pase_solve_batched", "pase_profile_kernel", "pase_profile_read",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
-            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_residual_noalloc",
+            "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_smooth", "pase_smoother_form",
+            "pase_residual_noalloc",
             "pase_time_kernel", "pase_set_grid", "pase_smoother_nparams", "pase_smoother_state",
             "pase_smoother_apply", "pase_smoother_step", "pase_default_train_options",
             "pase_train_smoother",
@@ -104,6 +110,8 @@ def load_library(path=LIB_PATH):
     L.pase_prolongate.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pase_iterate.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.pase_spmm_am.argtypes = [vp, i32, vp, vp, vp]
+    L.pase_smooth.argtypes = [vp, i32, i32, vp, vp]
+    L.pase_smoother_form.argtypes = [vp]
     L.pase_residual_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.pase_time_kernel.argtypes = [vp, i32, i32, i32, ctypes.POINTER(dbl)]
     L.pase_profile_kernel.argtypes = [vp, i32]
@@ -127,7 +135,8 @@ def load_library(path=LIB_PATH):
     for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_solve_batched",
                  "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
-                 "pase_iterate", "pase_spmm_am", "pase_residual_noalloc", "pase_time_kernel",
+                 "pase_iterate", "pase_spmm_am", "pase_smooth", "pase_smoother_form", "pase_residual_noalloc",
+                 "pase_time_kernel",
                  "pase_profile_kernel", "pase_profile_read", "pase_set_grid", "pase_smoother_nparams",
                  "pase_smoother_state", "pase_smoother_apply", "pase_smoother_step", "pase_train_smoother",
                  "pase_destroy"]:
@@ -272,6 +281,14 @@ def pase_spmm_am(h, m, X, AX, MX):
     return _check(load_library().pase_spmm_am(h, m, _ptr(X), _ptr(AX), _ptr(MX)))
 
 
+def pase_smooth(h, m, sweeps, B, X):
+    return _check(load_library().pase_smooth(h, m, sweeps, _ptr(B), _ptr(X)))
+
+
+def pase_smoother_form(h):
+    return int(load_library().pase_smoother_form(h))
+
+
 def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres, stream=None):
     """Residual without any device allocation; every array must be a CUDA tensor.
     Queued on `stream` (int handle, torch.cuda.Stream or None) without synchronising."""
@@ -283,7 +300,7 @@ def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres,
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
            "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7,
-           "gram_split": 8}
+           "gram_split": 8, "jacobi_fp32_csr": 9}
 
 
 def pase_time_kernel(h, kernel, m, reps=10):

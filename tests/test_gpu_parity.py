@@ -230,8 +230,19 @@ def test_project_parity(which, request):
 def test_augmented_eig_parity(which, m, request):
     """m = 96 gives Rayleigh-Ritz blocks of 3m = 288 whose triangles no longer fit in
     shared memory, so the global-memory variants of the small eigensolver run."""
-    pb = request.getfixturevalue(which)
-    c = Ctx(pb, aug_adaptive=0, aug_max_iter=200)
+    _augmented_eig_check(request.getfixturevalue(which), m)
+
+
+@pytest.mark.parametrize("transform", [P.PASE_AUG_PRECOND_A, P.PASE_AUG_PRECOND_B, P.PASE_AUG_PRECOND_BA])
+@pytest.mark.parametrize("which,m", [("p2d", 16), ("p3d", 24)])
+def test_augmented_eig_transform_parity(which, m, transform, request):
+    """Step (c) through the PRECOND-A / -B / -B-A congruences of §4 returns the pairs of the
+    untransformed pencil (dense oracle), mapped back to the original basis."""
+    _augmented_eig_check(request.getfixturevalue(which), m, aug_transform=transform)
+
+
+def _augmented_eig_check(pb, m, **kw):
+    c = Ctx(pb, aug_adaptive=0, aug_max_iter=200, **kw)
     try:
         if pb.N <= 5000:
             lam_d, U_d = dense.smallest_pairs(pb.A, pb.M, m)
@@ -383,6 +394,39 @@ def test_solve_laplace_3d_32_cluster():
     _check_pairs(pb, lam, U, nev, spectrum.q1_laplace_eigenvalues(3, 32, nev), 1e-8)
 
 
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_solve_post_solve_form(precision):
+    """Alg. 3's two-solve form (step-7 solve after every Rayleigh-Ritz that has not
+    converged): the closed-form pairs, no more outer iterations than the one-solve form, and
+    (FP64) the oracle's iteration count of the same form within one."""
+    pb = pin.build_problem(2, 64, 8, mg_min=4)
+    nev = 8
+    m = pin.guard_columns(nev)
+    ref = spectrum.q1_laplace_eigenvalues(2, 64, nev)
+    rc1, st1, _, _ = _solve(pb, nev, 1e-9, precision, m=m)
+    rc2, st2, lam, U = _solve(pb, nev, 1e-9, precision, m=m, post_solve=1)
+    assert rc1 == P.PASE_OK and rc2 == P.PASE_OK, (st1, st2)
+    _check_pairs(pb, lam, U, nev, ref, 1e-9)
+    assert st2["iterations"] <= st1["iterations"], (st1["iterations"], st2["iterations"])
+    if precision == P.PASE_PREC_FP64:  # step (c) to 1e-12 every time, as the oracle's dense solve
+        rc3, st3, _, _ = _solve(pb, nev, 1e-9, precision, m=m, post_solve=1, aug_adaptive=0)
+        solver = opase.Solver(pb.A, pb.M, pb.chain, pb.coarse_level)
+        _, _, info = solver.solve(nev, m, 1e-9, U0=pin.start_vectors(0, pb.N, m), post_solve=True)
+        assert rc3 == P.PASE_OK and abs(info["iterations"] - st3["iterations"]) <= 1, (info["iterations"], st3)
+
+
+@pytest.mark.parametrize("transform", [P.PASE_AUG_PLAIN, P.PASE_AUG_PRECOND_A, P.PASE_AUG_PRECOND_B,
+                                       P.PASE_AUG_PRECOND_BA])
+def test_solve_with_aug_transform(transform):
+    """Whole solves with each step-(c) variant reach the same pairs (variable kappa, 3D)."""
+    pb = pin.build_problem(3, 32, 8, kappa_seed=5, mg_min=4)
+    nev = 10
+    rc, st, lam, U = _solve(pb, nev, 1e-9, aug_transform=transform)
+    assert rc == P.PASE_OK, st
+    ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+    _check_pairs(pb, lam, U, nev, ref, 1e-9)
+
+
 def test_setup_forms_coarse_pencil_when_not_given():
     """A_H = M_H = NULL: the library's Galerkin products through the chain give the same
     solve as the caller's."""
@@ -511,3 +555,74 @@ def test_full_size_split_prolongation_sampled(p3d_128):
             ex = sum(Fraction(float(W[r, k])) * Fraction(float(CW[k, j])) for k in range(m))
             assert abs(Fraction(float(Uh[r, j])) - ex) <= Fraction(8 * u) * Fraction(float(smax[j])) + Fraction(u) * abs(ex)
     assert _colrel(Uh, W @ CW) < 1e-14
+
+
+def _jacobi_bound(A, b, x, omega, gamma):
+    """Elementwise bound on the change of one damped-Jacobi sweep x + omega D^-1 (b - A x)
+    when it runs in FP32: inputs, coefficients and 1/a_ii rounded (one unit each), the sum
+    of the row's products accumulated in FP32 (one unit per term), gamma = (terms + 8) u."""
+    d = np.abs(1.0 / A.diagonal())[:, None]
+    absA = abs(A)
+    return gamma * (np.abs(x) + omega * d * (np.abs(b) + absA @ np.abs(x))), d, absA
+
+
+@pytest.mark.parametrize("d,n,kseed", [(3, 32, 5), (3, 20, 6), (2, 64, 7), (2, 38, 8)])
+@pytest.mark.parametrize("m", [8, 56])
+@pytest.mark.parametrize("stencil", [1, 0])
+def test_fp32_smoothing_parity(d, n, kseed, m, stencil):
+    """Two FP32 damped-Jacobi sweeps on the fine level (the mixed form's smoother) against
+    the oracle's FP64 sweeps, entry by entry, within the FP32 rounding bound of the two
+    sweeps (the first sweep's error carried through the second by |I| + omega |D^-1||A|).
+    stencil=1 runs the structured-grid kernel (grids of 31^3, 19^3, 63^2, 37^2 nodes: ragged
+    against its 16 x 4 / 64-node tiles), stencil=0 the CSR kernel."""
+    pb = pin.build_problem(d, n, n // 2, kappa_seed=kseed)
+    c = Ctx(pb, precision=P.PASE_PREC_MIXED, stencil=stencil)
+    try:
+        assert P.pase_smoother_form(c.h) == (d if stencil else 0)
+        B = pin.start_vectors(30 + m, pb.N, m)
+        X0 = pin.start_vectors(31 + m, pb.N, m)
+        X = X0.copy()
+        P.pase_smooth(c.h, m, 2, B, X)
+    finally:
+        c.close()
+    hier = mg.Hierarchy(pb.A, pb.chain)
+    om = hier.omega
+    x1 = hier.smooth(0, B, X0, 1)
+    x2 = hier.smooth(0, B, x1, 1)
+    gamma = (3 ** d + 8) * 2.0 ** -24
+    e1, dd, absA = _jacobi_bound(pb.A, B, X0, om, gamma)
+    e2, _, _ = _jacobi_bound(pb.A, B, x1, om, gamma)
+    e2 = e2 + e1 + om * dd * (absA @ e1)
+    err = np.abs(X - x2)
+    assert np.all(err <= 2.0 * e2), (np.max(err / e2), np.argmax(err / e2))
+    assert np.max(err) > 0.0  # FP32 arithmetic did run
+
+
+def test_fp32_smoothing_non_stencil_matrix_uses_csr():
+    """A fine matrix with one coupling outside the grid neighbourhood is not taken for a
+    stencil: the CSR kernel runs, with the same bound."""
+    import scipy.sparse as sp
+    pb = pin.build_problem(2, 32, 16, kappa_seed=3)
+    N = pb.N
+    E = sp.csr_matrix(([-0.1, -0.1, 0.1, 0.1], ([0, N - 1, 0, N - 1], [N - 1, 0, 0, N - 1])), shape=(N, N))
+    A = pin.canonical_csr(pb.A + E)  # still symmetric and diagonally dominant
+    rows, cols = A.nonzero()
+    M = sp.csr_matrix((np.asarray(pb.M[rows, cols]).ravel(), A.indices.copy(), A.indptr.copy()), shape=A.shape)
+    opt = P.pase_default_options()
+    opt.precision = P.PASE_PREC_MIXED
+    opt.coarse_level = 1
+    h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
+    m = 16
+    try:
+        P.pase_setup(h, A, M, pb.chain)
+        assert P.pase_smoother_form(h) == 0
+        B = pin.start_vectors(40, N, m)
+        X0 = pin.start_vectors(41, N, m)
+        X = X0.copy()
+        P.pase_smooth(h, m, 1, B, X)
+    finally:
+        P.pase_destroy(h)
+    hier = mg.Hierarchy(A, pb.chain)
+    x1 = hier.smooth(0, B, X0, 1)
+    e1, _, _ = _jacobi_bound(A, B, X0, hier.omega, 20 * 2.0 ** -24)
+    assert np.all(np.abs(X - x1) <= 2.0 * e1)

@@ -368,6 +368,74 @@ def test_precond_a_congruence_preserves_spectrum():
     np.testing.assert_allclose(Ahat @ Y, Bhat @ Y * lt, atol=1e-8 * abs(lt).max())
 
 
+def _congruence_T(NH, m, Z):
+    return np.block([[np.eye(NH), Z], [np.zeros((m, NH)), np.eye(m)]])
+
+
+def test_precond_b_congruence():
+    """PRECOND-B's blocks equal T^-T A_Hh T^-1 and T^-T B_Hh T^-1 for T = [[I, B_H^-1 b_h],
+    [0, I]] formed densely (which pins every term of the formulas), B_Hh becomes block
+    diagonal, the spectrum is unchanged and eigenvectors map back."""
+    pb = _tiny(kappa_seed=4)
+    m = 5
+    W = pin.start_vectors(2, pb.N, m)
+    aH, bH, GA, GM = pase.projection(pb.A, pb.M, pb.P, W)
+    Ahat, Bhat = pase.augmented_pencil(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    NH = pb.N_H
+    bhat, a_t, alpha_t, beta_t = pase.precond_b(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    Ti = np.linalg.inv(_congruence_T(NH, m, bhat))
+    At_dense = Ti.T @ Ahat @ Ti
+    Bt_dense = Ti.T @ Bhat @ Ti
+    At = np.block([[pb.A_H.toarray(), a_t], [a_t.T, alpha_t]])
+    Bt = np.block([[pb.M_H.toarray(), np.zeros((NH, m))], [np.zeros((m, NH)), beta_t]])
+    scale = np.abs(Ahat).max()
+    np.testing.assert_allclose(At_dense, At, atol=1e-11 * scale)
+    np.testing.assert_allclose(Bt_dense, Bt, atol=1e-11 * np.abs(Bhat).max())
+    ref = sl.eigh(Ahat, Bhat, eigvals_only=True)
+    got = sl.eigh(0.5 * (At + At.T), 0.5 * (Bt + Bt.T), eigvals_only=True)
+    np.testing.assert_allclose(got, ref, rtol=1e-10)
+    lt, Yt = sl.eigh(0.5 * (At + At.T), 0.5 * (Bt + Bt.T), subset_by_index=[0, m - 1])
+    uH, g = pase.precond_a_back(bhat, Yt[:NH], Yt[NH:])
+    Y = np.vstack([uH, g])
+    np.testing.assert_allclose(Ahat @ Y, Bhat @ Y * lt, atol=1e-8 * abs(lt).max())
+
+
+def test_precond_a_blocks_equal_dense_congruence():
+    """PRECOND-A's blocks equal T^-T A_Hh T^-1, T^-T B_Hh T^-1 for T = [[I, A_H^-1 a_h],[0, I]]."""
+    pb = _tiny(kappa_seed=4)
+    m = 5
+    W = pin.start_vectors(2, pb.N, m)
+    aH, bH, GA, GM = pase.projection(pb.A, pb.M, pb.P, W)
+    Ahat, Bhat = pase.augmented_pencil(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    NH = pb.N_H
+    ahat, alpha_t, b_t, beta_t = pase.precond_a(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    Ti = np.linalg.inv(_congruence_T(NH, m, ahat))
+    At = np.block([[pb.A_H.toarray(), np.zeros((NH, m))], [np.zeros((m, NH)), alpha_t]])
+    Bt = np.block([[pb.M_H.toarray(), b_t], [b_t.T, beta_t]])
+    np.testing.assert_allclose(Ti.T @ Ahat @ Ti, At, atol=1e-11 * np.abs(Ahat).max())
+    np.testing.assert_allclose(Ti.T @ Bhat @ Ti, Bt, atol=1e-11 * np.abs(Bhat).max())
+
+
+def test_precond_ba_factorisation():
+    """PRECOND-B-A: the factors reproduce the B-transformed A_Hh, and the factorisation is
+    the one PRECOND-A applies (its Schur complement has the PRECOND-A form on the
+    transformed blocks)."""
+    pb = _tiny(kappa_seed=4)
+    m = 5
+    W = pin.start_vectors(2, pb.N, m)
+    aH, bH, GA, GM = pase.projection(pb.A, pb.M, pb.P, W)
+    NH = pb.N_H
+    bhat, a_t, alpha_t, beta_t, ahat2, S = pase.precond_ba(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    At = np.block([[pb.A_H.toarray(), a_t], [a_t.T, alpha_t]])
+    L = np.block([[np.eye(NH), np.zeros((NH, m))], [ahat2.T, np.eye(m)]])
+    D = np.block([[pb.A_H.toarray(), np.zeros((NH, m))], [np.zeros((m, NH)), S]])
+    np.testing.assert_allclose(L @ D @ L.T, At, atol=1e-11 * np.abs(At).max())
+    ahat_a, alpha_a, _, _ = pase.precond_a(pb.A_H, pb.M_H, a_t, np.zeros_like(bH), alpha_t, beta_t)
+    np.testing.assert_allclose(ahat_a, ahat2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(alpha_a, S, atol=1e-11 * np.abs(S).max())
+    assert np.all(np.linalg.eigvalsh(0.5 * (S + S.T)) > 0)  # a Schur complement of an SPD matrix
+
+
 def test_convergence_rate_independent_of_h():
     """Theorem 2.1: for a fixed coarse space the contraction per iteration does not
     deteriorate as h decreases.  Band test on the first pair, 2D, H = 1/8."""
@@ -455,3 +523,21 @@ def test_relative_residuals_planted_mistakes_fail_the_pin():
     ]
     for s in slips:
         assert np.max(np.abs(s - want) / want) > 0.1
+
+
+def test_post_solve_form_matches_brute_force():
+    """Alg. 3's two-solve form (step-7 solve after each Rayleigh-Ritz) reaches the brute-force
+    pairs and, doing two linear solves per iteration, needs no more iterations than the
+    one-solve form."""
+    pb = _tiny()
+    nev, m = 4, 8
+    lam_d, _ = dense.smallest_pairs(pb.A, pb.M, nev)
+    solver = pase.Solver(pb.A, pb.M, pb.chain, pb.coarse_level)
+    U0 = pin.start_vectors(0, pb.N, m)
+    lam1, U1, info1 = solver.solve(nev, m, 1e-10, U0=U0)
+    lam2, U2, info2 = solver.solve(nev, m, 1e-10, U0=U0, post_solve=True)
+    assert info1["converged"] and info2["converged"]
+    np.testing.assert_allclose(lam2[:nev], lam_d, rtol=1e-10)
+    assert info2["iterations"] <= info1["iterations"]
+    # the returned block is the Rayleigh-Ritz one: M-orthonormal
+    np.testing.assert_allclose(U2.T @ (pb.M @ U2), np.eye(m), atol=1e-10)
