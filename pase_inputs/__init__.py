@@ -214,6 +214,103 @@ def q1_matrices(d: int, n: int, kappa: np.ndarray | None = None):
     return A, M
 
 
+def _gauss_legendre_01(q: int):
+    """q-point Gauss-Legendre nodes and weights on [0, 1]."""
+    x, w = np.polynomial.legendre.leggauss(q)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def q1_matrices_coefficients(d: int, n: int, tensor, potential, quad: int = 3):
+    """Stiffness of a(u, v) = int (T(x) grad u) . grad v + phi(x) u v and mass int u v with Q1
+    elements on the uniform n^d mesh, interior nodes (the same ordering as q1_matrices).
+
+    tensor(X) -> [..., d, d] and potential(X) -> [...] take points X [..., d]; both are
+    integrated with the quad^d-point Gauss-Legendre rule on every element (exact for the
+    mass and for polynomial coefficients of degree <= 2 quad - 3).  The element matrix is
+    sum_q w_q h^d (sum_kl T_kl(x_q) dphi_a/dx_k dphi_b/dx_l + phi(x_q) phi_a phi_b) with
+    phi_a the tensor-product P1 hats; entries are gathered per grid tap as in q1_matrices.
+    """
+    assert d in (2, 3) and n >= 2
+    h = 1.0 / n
+    n1 = n - 1
+    N = n1 ** d
+    xg, wg = _gauss_legendre_01(quad)
+    # reference quadrature points (x fastest) and per-point basis values / gradients
+    qpts = np.array(np.meshgrid(*([xg] * d), indexing="ij")).reshape(d, -1).T[:, ::-1]  # [Q][d], col 0 = x
+    qw = np.prod(np.array(np.meshgrid(*([wg] * d), indexing="ij")).reshape(d, -1).T, axis=1)
+    corners = np.array([[(a >> k) & 1 for k in range(d)] for a in range(2 ** d)])  # [2^d][d]
+    Q, nb = len(qw), 2 ** d
+    val = np.ones((Q, nb))
+    grad = np.ones((Q, nb, d))
+    for k in range(d):
+        lk = np.where(corners[None, :, k] == 1, qpts[:, k:k + 1], 1.0 - qpts[:, k:k + 1])  # [Q][nb]
+        dk = np.where(corners[None, :, k] == 1, 1.0, -1.0) / h
+        val *= lk
+        for j in range(d):
+            grad[:, :, j] *= dk if j == k else lk
+    # reference blocks: [Q][d*d + 1][nb][nb]
+    G = np.zeros((Q, d * d + 1, nb, nb))
+    for k in range(d):
+        for l in range(d):
+            G[:, k * d + l] = np.einsum("qa,qb->qab", grad[:, :, k], grad[:, :, l])
+    G[:, d * d] = np.einsum("qa,qb->qab", val, val)
+    G *= (qw * h ** d)[:, None, None, None]
+    ne = n ** d
+    taps = 3 ** d
+    dia = np.zeros((taps, N))
+    chunk = 1 << 16
+    for e0 in range(0, ne, chunk):
+        e = np.arange(e0, min(ne, e0 + chunk), dtype=np.int64)
+        ec = np.stack([(e // n ** k) % n for k in range(d)], axis=1)  # [E][d] lower corners
+        X = (ec[:, None, :] + qpts[None, :, :]) * h                      # [E][Q][d]
+        T = tensor(X)
+        C = np.concatenate([T.reshape(T.shape[:2] + (d * d,)), potential(X)[:, :, None]], axis=2)
+        K = np.einsum("eqc,qcab->eab", C, G)
+        node = ec[:, None, :] + corners[None, :, :]                      # [E][nb][d] in 0..n
+        inner = np.all((node >= 1) & (node <= n1), axis=2)
+        gidx = np.zeros(node.shape[:2], dtype=np.int64)
+        for k in range(d):
+            gidx += (node[:, :, k] - 1) * n1 ** k
+        for a in range(nb):
+            for b in range(nb):
+                ok = inner[:, a] & inner[:, b]
+                o = corners[b] - corners[a]
+                t = int(sum((o[k] + 1) * 3 ** k for k in range(d)))
+                dia[t, gidx[ok, a]] += K[ok, a, b]
+    idx = np.arange(N, dtype=np.int64)
+    coords = [(idx // (n1 ** k)) % n1 + 1 for k in range(d)]
+    valid = np.zeros((N, taps), dtype=bool)
+    cols = np.zeros((N, taps), dtype=np.int64)
+    for t in range(taps):
+        o = [(t // 3 ** k) % 3 - 1 for k in range(d)]
+        ok = np.ones(N, dtype=bool)
+        col = np.zeros(N, dtype=np.int64)
+        for k in range(d):
+            j = coords[k] + o[k]
+            ok &= (j >= 1) & (j <= n1)
+            col += (j - 1) * n1 ** k
+        valid[:, t] = ok
+        cols[:, t] = col
+    indptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(valid.sum(axis=1), out=indptr[1:])
+    A = sp.csr_matrix((dia.T[valid], cols[valid].astype(np.int32), indptr), shape=(N, N))
+    _, M = q1_matrices(d, n)
+    return A, M
+
+
+def tensor_potential_coefficients(d: int):
+    """The coefficients of the batch-scheme test problem of the numerical section:
+    T(x) = I + (x - 1/2)(x - 1/2)^T and phi(x) = exp(prod_k (x_k - 1/2)) on (0, 1)^d."""
+    def tensor(X):
+        y = X - 0.5
+        return np.eye(d) + y[..., :, None] * y[..., None, :]
+
+    def potential(X):
+        return np.exp(np.prod(X - 0.5, axis=-1))
+
+    return tensor, potential
+
+
 def q1_interp_1d(n_fine: int, n_coarse: int) -> sp.csr_matrix:
     """1D nodal interpolation of coarse P1 hats at fine interior nodes.
 
@@ -260,9 +357,14 @@ class Problem:
     """
 
     def __init__(self, d, n, n_coarse, kappa=None, mg_min=None):
-        self.d, self.n, self.n_coarse = d, n, n_coarse
         self.kappa = kappa
-        self.A, self.M = q1_matrices(d, n, kappa)
+        self._init_from(d, n, n_coarse, q1_matrices(d, n, kappa), mg_min)
+
+    def _init_from(self, d, n, n_coarse, AM, mg_min):
+        self.d, self.n, self.n_coarse = d, n, n_coarse
+        if not hasattr(self, "kappa"):
+            self.kappa = None
+        self.A, self.M = AM
         sizes = [n]
         while sizes[-1] > n_coarse:
             sizes.append(sizes[-1] // 2)
@@ -319,6 +421,7 @@ WORKLOADS = {
     "laplace2d_128": dict(d=2, n=128, n_coarse=16, nev=10, seed=0, kappa_seed=None),
     "laplace3d_128": dict(d=3, n=128, n_coarse=16, nev=50, seed=0, kappa_seed=None),
     "kappa3d_256": dict(d=3, n=256, n_coarse=32, nev=100, seed=0, kappa_seed=1),
+    "tensor3d_128": dict(d=3, n=128, n_coarse=16, nev=50, seed=0, kappa_seed=None, operator="tensor"),
 }
 
 
@@ -340,6 +443,13 @@ def batch_workload(seed: int, count: int, sizes=(64, 128, 256, 512), nev_range=(
     return out
 
 
-def build_problem(d, n, n_coarse, kappa_seed=None, sigma=1.0, mg_min=None):
+def build_problem(d, n, n_coarse, kappa_seed=None, sigma=1.0, mg_min=None, operator="kappa"):
+    """operator "kappa": -div(kappa grad u) = lambda u with kappa per element (1 without a
+    seed); "tensor": -div(T grad u) + phi u = lambda u with the coefficients of
+    tensor_potential_coefficients."""
+    if operator == "tensor":
+        pb = Problem.__new__(Problem)
+        pb._init_from(d, n, n_coarse, q1_matrices_coefficients(d, n, *tensor_potential_coefficients(d)), mg_min)
+        return pb
     kappa = None if kappa_seed is None else lognormal_kappa(d, n, kappa_seed, sigma)
     return Problem(d, n, n_coarse, kappa, mg_min=mg_min)

@@ -427,6 +427,19 @@ def test_solve_with_aug_transform(transform):
     _check_pairs(pb, lam, U, nev, ref, 1e-9)
 
 
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_solve_tensor_potential_3d(precision):
+    """The operator of the numerical section's batch-scheme test, -div(T grad u) + phi u with
+    T = I + (x - 1/2)(x - 1/2)^T and phi = exp(prod (x_k - 1/2)), on a 32^3 Q1 mesh: the 20
+    smallest pairs against shift-invert Lanczos on the same matrices."""
+    pb = pin.build_problem(3, 32, 8, mg_min=4, operator="tensor")
+    nev = 20
+    rc, st, lam, U = _solve(pb, nev, 1e-9, precision)
+    assert rc == P.PASE_OK, st
+    ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+    _check_pairs(pb, lam, U, nev, ref, 1e-9)
+
+
 def test_setup_forms_coarse_pencil_when_not_given():
     """A_H = M_H = NULL: the library's Galerkin products through the chain give the same
     solve as the caller's."""

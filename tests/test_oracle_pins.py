@@ -541,3 +541,92 @@ def test_post_solve_form_matches_brute_force():
     assert info2["iterations"] <= info1["iterations"]
     # the returned block is the Rayleigh-Ritz one: M-orthonormal
     np.testing.assert_allclose(U2.T @ (pb.M @ U2), np.eye(m), atol=1e-10)
+
+
+# ------------------------------------------------------------ variable tensor + potential operator
+
+
+def _const_tensor(d, T):
+    return lambda X: np.broadcast_to(np.asarray(T, dtype=float), X.shape[:-1] + (d, d))
+
+
+def test_coefficient_assembly_reduces_to_laplace_and_shift():
+    """T = I, phi = 0 gives the Q1 Laplace stiffness; phi = c adds c times the mass."""
+    for d, n in ((2, 7), (3, 5)):
+        A0, M0 = pin.q1_matrices(d, n)
+        A, M = pin.q1_matrices_coefficients(d, n, _const_tensor(d, np.eye(d)), lambda X: np.zeros(X.shape[:-1]))
+        assert abs(A - A0).max() < 1e-13 * abs(A0).max() and abs(M - M0).max() == 0.0
+        A, _ = pin.q1_matrices_coefficients(d, n, _const_tensor(d, np.eye(d)), lambda X: np.full(X.shape[:-1], 2.5))
+        assert abs(A - (A0 + 2.5 * M0)).max() < 1e-13 * abs(A0).max()
+
+
+def test_coefficient_assembly_anisotropic_closed_form():
+    """T = diag(a) constant: the pencil is sum_k a_k K_k against the tensor mass, whose
+    eigenvalues are sum_k a_k mu_{i_k} with mu the 1D P1 values (6/h^2)(1-cos)/(2+cos)."""
+    d, n = 3, 6
+    a = np.array([1.0, 2.5, 0.5])
+    A, M = pin.q1_matrices_coefficients(d, n, _const_tensor(d, np.diag(a)), lambda X: np.zeros(X.shape[:-1]))
+    h = 1.0 / n
+    k = np.arange(1, n)
+    mu = (6.0 / h ** 2) * (1.0 - np.cos(k * np.pi * h)) / (2.0 + np.cos(k * np.pi * h))
+    ref = np.sort((a[0] * mu[:, None, None] + a[1] * mu[None, :, None] + a[2] * mu[None, None, :]).ravel())
+    got = sl.eigh(A.toarray(), M.toarray(), eigvals_only=True)
+    np.testing.assert_allclose(got, ref, rtol=1e-11)
+
+
+def _loop_coefficient_assembly(d, n, tensor, potential, q=3):
+    """Element-by-element assembly with explicit loops (written independently of the
+    vectorised one): Gauss-Legendre points, P1 hats and their gradients evaluated per point."""
+    h = 1.0 / n
+    n1 = n - 1
+    N = n1 ** d
+    A = np.zeros((N, N))
+    xg, wg = np.polynomial.legendre.leggauss(q)
+    xg, wg = 0.5 * (xg + 1.0), 0.5 * wg
+    import itertools
+    for ec in itertools.product(range(n), repeat=d):          # ec = (ex, ey[, ez])
+        for qi in itertools.product(range(q), repeat=d):
+            xi = np.array([xg[j] for j in qi])
+            w = np.prod([wg[j] for j in qi]) * h ** d
+            X = (np.array(ec) + xi) * h
+            T = tensor(X[None, None, :])[0, 0]
+            ph = potential(X[None, None, :])[0, 0]
+            locs, vals, grads = [], [], []
+            for a in itertools.product((0, 1), repeat=d):
+                node = [ec[k] + a[k] for k in range(d)]
+                if not all(1 <= v <= n1 for v in node):
+                    continue
+                gi = sum((node[k] - 1) * n1 ** k for k in range(d))
+                l = [xi[k] if a[k] else 1.0 - xi[k] for k in range(d)]
+                dl = [(1.0 if a[k] else -1.0) / h for k in range(d)]
+                g = np.array([dl[k] * np.prod([l[j] for j in range(d) if j != k]) for k in range(d)])
+                locs.append(gi)
+                vals.append(np.prod(l))
+                grads.append(g)
+            for i, gi in enumerate(locs):
+                for j, gj in enumerate(locs):
+                    A[gi, gj] += w * (grads[i] @ T @ grads[j] + ph * vals[i] * vals[j])
+    return A
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 4)])
+def test_coefficient_assembly_matches_loop_assembly(d, n):
+    """The section-6.3 coefficients (full tensor, potential) against the loop assembly."""
+    T, phi = pin.tensor_potential_coefficients(d)
+    A, _ = pin.q1_matrices_coefficients(d, n, T, phi)
+    ref = _loop_coefficient_assembly(d, n, T, phi)
+    np.testing.assert_allclose(A.toarray(), ref, atol=1e-13 * np.abs(ref).max())
+
+
+def test_tensor_potential_spectrum_sandwich():
+    """T(x) = I + y y^T (y = x - 1/2) has eigenvalues in [1, 1 + d/4] and phi = exp(prod y)
+    lies in [e^-1/8, e^1/8] on the cube, and the quadrature weights are positive, so by
+    Courant-Fischer every eigenvalue lies between lambda_i(Laplace) + e^-1/8 and
+    (1 + d/4) lambda_i(Laplace) + e^1/8."""
+    d, n = 3, 8
+    pb = pin.build_problem(d, n, 4, operator="tensor")
+    lam = sl.eigh(pb.A.toarray(), pb.M.toarray(), eigvals_only=True)
+    lap = spectrum.q1_laplace_eigenvalues(d, n, len(lam))
+    assert np.all(lam >= lap + np.exp(-0.125) - 1e-9)
+    assert np.all(lam <= (1 + d / 4.0) * lap + np.exp(0.125) + 1e-9)
+    assert abs(pb.A - pb.A.T).max() < 1e-14 * abs(pb.A).max()
