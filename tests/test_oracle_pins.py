@@ -630,3 +630,65 @@ def test_tensor_potential_spectrum_sandwich():
     assert np.all(lam >= lap + np.exp(-0.125) - 1e-9)
     assert np.all(lam <= (1 + d / 4.0) * lap + np.exp(0.125) + 1e-9)
     assert abs(pb.A - pb.A.T).max() < 1e-14 * abs(pb.A).max()
+
+
+# ------------------------------------------------------------ batch scheme (§5)
+
+
+def test_component_norms_equal_explicit_projection():
+    """||Pi_h v_i||_b^2 from the X beta X^T formula equals the b-norm of the b-orthogonal
+    projection of the explicitly formed fine vector v_i onto span(W)."""
+    pb = _tiny(kappa_seed=4)
+    m = 5
+    W = pin.start_vectors(2, pb.N, m)
+    aH, bH, GA, GM = pase.projection(pb.A, pb.M, pb.P, W)
+    rng = np.random.default_rng(3)
+    uH = rng.standard_normal((pb.N_H, 7))
+    gam = rng.standard_normal((m, 7))
+    V = pb.P @ uH + W @ gam
+    MW = pb.M @ W
+    Pv = W @ np.linalg.solve(W.T @ MW, MW.T @ V)          # b-orthogonal projection onto span(W)
+    ref = np.einsum("ij,ij->j", Pv, pb.M @ Pv)
+    np.testing.assert_allclose(pase.component_norms(uH, gam, bH, GM), ref, rtol=1e-10)
+    # a vector of span(W) is its own projection; one b-orthogonal to span(W) has none
+    np.testing.assert_allclose(pase.component_norms(np.zeros((pb.N_H, m)), np.eye(m), bH, GM), np.diag(GM),
+                               rtol=1e-12)
+
+
+def test_nearest_pairs_are_the_closest_to_the_shift():
+    pb = _tiny(kappa_seed=4)
+    m = 5
+    W = pin.start_vectors(2, pb.N, m)
+    aH, bH, GA, GM = pase.projection(pb.A, pb.M, pb.P, W)
+    Ahat, Bhat = pase.augmented_pencil(pb.A_H, pb.M_H, aH, bH, GA, GM)
+    full = sl.eigh(Ahat, Bhat, eigvals_only=True)
+    theta = 0.5 * (full[6] + full[7])
+    lam, CH, CW = pase.nearest_pairs(pb.A_H, pb.M_H, aH, bH, GA, GM, theta, 4)
+    # four eigenvalues of the pencil, ascending, none farther from theta than any left out
+    dist = np.abs(full - theta)
+    inside = np.array([np.min(np.abs(full - l)) for l in lam])
+    assert np.all(inside <= 1e-9 * np.abs(full).max()) and np.all(np.diff(lam) > 0)
+    kept = np.argsort(dist)[:4]
+    assert np.max(np.abs(lam - theta)) <= np.min(np.delete(dist, kept)) + 1e-9
+    Y = np.vstack([CH, CW])
+    np.testing.assert_allclose(Ahat @ Y, Bhat @ Y * lam, atol=1e-9 * np.abs(lam).max())
+
+
+def test_batch_bounds_keep_clusters_together():
+    lam = np.array([1.0, 2.0, 3.0, 3.0, 3.0, 5.0, 6.0, 7.0, 7.0000001, 9.0])
+    assert pase.batch_bounds(lam, 9, 3) == [(0, 5), (5, 9)]
+    assert pase.batch_bounds(lam, 8, 2) == [(0, 2), (2, 5), (5, 7), (7, 8)]  # nev ends the last batch
+
+
+def test_batch_scheme_matches_the_smallest_pairs():
+    """Alg. 7 with three batches on the section-6.3 operator (2D, 64^2 mesh, coarse 32^2)
+    returns the first 24 pairs of the pencil, M-orthonormal across batches."""
+    pb = pin.build_problem(2, 64, 32, mg_min=4, operator="tensor")
+    solver = pase.Solver(pb.A, pb.M, pb.chain, pb.coarse_level)
+    nev = 24
+    lam, U, info = pase.batch_scheme(solver, nev, 8, 1e-9, guard=4, max_iter=40)
+    ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+    np.testing.assert_allclose(lam, ref, rtol=1e-10)
+    assert np.all(pase.relative_residuals(pb.A, pb.M, U, lam) <= 1e-9)
+    np.testing.assert_allclose(U.T @ (pb.M @ U), np.eye(nev), atol=1e-9)
+    assert len(info["iterations"]) == 3
