@@ -678,7 +678,7 @@ static int tc_check(pase_ctx* h) {
   PASE_CUDA(cudaStreamSynchronize(h->stream));
   if (h->w.h_status[7]) {
     PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
-    return fail(PASE_ERR_TIMEOUT, "split GEMM: a tensor-core wait ran out of its limit");
+    return fail(PASE_ERR_TIMEOUT, "a tensor-core or bulk-copy wait (split GEMM, stencil kernel) ran out of its limit");
   }
   return PASE_OK;
 }

@@ -6,34 +6,53 @@
 // levels.  A Q1 operator on a uniform (n-1)^d interior grid with x-fastest ordering, and
 // every Galerkin coarse operator of nested Q1 spaces, couples node (x, y, z) only to
 // (x+dx, y+dy, z+dz) with |dx|, |dy|, |dz| <= 1, so its matrix needs no column indices.
-// Setup recognises that pattern in a CSR level and stores the values by tap (a DIA
-// layout): plane t = (dx+1) + 3(dy+1) + 9(dz+1) holds the coefficient of that neighbour
-// for every row, plane 3^d holds 1 / a_ii, and the x extent of every plane is padded to a
-// multiple of 4 (zeros) so that the coefficients of 4 consecutive x rows are one aligned
-// 16-byte load.
 //
 // Why not the CSR kernel: with node-major multivectors [N][m] the CSR kernel gathers the
-// m-wide X row of every nonzero, 27 times per row in 3D, and the L1 request rate, not
-// HBM, bounds it.  Here a thread owns 4 consecutive x rows and one 16-byte column slice
-// and marches through the grid along z (along y in 2D): each X value of plane p is loaded
-// once per (dy, dx-window) and feeds the three output planes p-1, p, p+1 through three
-// rolling register accumulators, so a thread issues 3 x 6 X loads per 4 x 3^3 row-taps
-// instead of 108, and every operand stream (X, b, coefficients, y) is read or written
-// once from HBM.
+// m-wide X row of every nonzero through L1, 27 times per row in 3D, and the L1 request
+// rate, not HBM, bounds it.
+//
+// Scheme.  A CTA owns a tile of the grid (16 x 4 nodes of an x-y plane in 3D, 64 nodes of
+// an x line in 2D) and marches along the last axis (z in 3D, y in 2D) over a chunk of
+// planes.  Plane p of X (the tile plus a one-node halo) and the coefficients that meet it
+// arrive in shared memory by bulk asynchronous copies (cp.async.bulk, completion counted
+// on an mbarrier), one plane ahead of the computation, in a ring of three stages.  A
+// thread owns 4 consecutive x rows and one 16-byte column slice; X values of plane p feed
+// the three output planes p-1, p, p+1 through three rolling register accumulators, so each
+// X value is read from shared memory once per (line, x window) and every operand stream
+// (X, b, coefficients, y) crosses HBM once.
+//
+// Coefficient layout ("step-major"), built at setup: the coefficient of row q's tap
+// t = (dx+1) + 3(dy+1) + 9(dz+1) (2D: (dx+1) + 3(dy+1), dy the marching offset) is needed
+// while plane q + dz is staged, so it is stored with step s = q + dz + 1, tile-blocked:
+//   [s = 0 .. n1+1][tile y][tile x][slot 0 .. T][TY][TX]   (zeros outside the grid)
+// slot T holding 1 / a_qq for plane q = s - 2 (the plane whose sweep completes then).  One
+// bulk copy of (T+1) TY TX floats per tile and step.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 
 #include "pase_internal.h"
+#include "tc_util.h"
 
 namespace pase {
 
 namespace {
 
-constexpr int kStRunX = 4;   // consecutive x rows per thread
-constexpr int kStRuns3 = 4;  // x runs per tile row in 3D (tile x extent 16)
+constexpr int kStStages = 3;
+constexpr int kStWaitLimit = 1 << 24;  // polls of a stage's mbarrier before giving up
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+template <int DIM>
+struct StGeo {
+  static constexpr int T = DIM == 3 ? 27 : 9;  // taps
+  static constexpr int TX = DIM == 3 ? 16 : 64;
+  static constexpr int TY = DIM == 3 ? 4 : 1;
+  static constexpr int RUNS = TX / 4;               // 4-row x runs per tile line
+  static constexpr int G = RUNS * TY;               // thread groups (16)
+  static constexpr int NL = DIM == 3 ? TY + 2 : 1;  // staged X lines (halo included)
+  static constexpr int VF = (T + 1) * TY * TX;      // coefficient floats per tile and step
+};
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void fma4(float4& a, float s, const float4& x) {
   a.x = fmaf(s, x.x, a.x);
   a.y = fmaf(s, x.y, a.y);
@@ -44,120 +63,211 @@ __device__ __forceinline__ float vcomp(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// acc[i] += sum_dx coef(t0 + dx + 1)[row i] * xl[i + dx + 1]  (i = 0..3)
-__device__ __forceinline__ void tap_line(float4 (&acc)[kStRunX], const float4 (&xl)[kStRunX + 2],
-                                         const float* __restrict__ vrow, int64_t P) {
-#pragma unroll
-  for (int dx = 0; dx < 3; ++dx) {
-    const float4 v = ldg4(vrow + dx * P);
-#pragma unroll
-    for (int i = 0; i < kStRunX; ++i) fma4(acc[i], vcomp(v, i), xl[i + dx]);
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// One staged plane: the tile's X lines (halo included) and its step's coefficients.  The
+// copies are issued by one thread; out-of-grid parts of the X lines are zero-filled by the
+// whole CTA (disjoint from the copied parts).
+template <int DIM>
+__device__ __forceinline__ void stage_issue(int tid, int nthreads, int n1, int m, int x0t, int y0t, int p, int64_t vblk,
+                                            const float* __restrict__ X, const float* __restrict__ V, float* xs,
+                                            float* vs, uint32_t mbar) {
+  using Gm = StGeo<DIM>;
+  const int64_t n1l = n1;
+  const bool have_x = p >= 0 && p < n1;
+  const int xa = max(0, x0t - 1), xb = min(n1, x0t + Gm::TX + 1);  // in-grid node range of a line
+  const bool interior = x0t >= 1 && x0t + Gm::TX + 1 <= n1 && (DIM == 2 || (y0t >= 1 && y0t + Gm::TY + 1 <= n1));
+  if (have_x && !interior) {
+    const int m4 = m / 4;
+    for (int ly = 0; ly < Gm::NL; ++ly) {
+      const int y = DIM == 3 ? y0t - 1 + ly : 0;
+      const bool yok = DIM == 2 || (unsigned)y < (unsigned)n1;
+      const int lo = yok ? xa - (x0t - 1) : Gm::TX + 2;  // nodes [0, lo) and [hi, TX+2) lie outside
+      const int hi = yok ? xb - (x0t - 1) : Gm::TX + 2;
+      const int nz = lo + (Gm::TX + 2 - hi);
+      float4* line = reinterpret_cast<float4*>(xs + (int64_t)ly * (Gm::TX + 2) * m);
+      for (int k = tid; k < nz * m4; k += nthreads) {
+        const int zn = k / m4, c = k - zn * m4;
+        line[(zn < lo ? zn : hi + (zn - lo)) * m4 + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  if (tid == 0) {
+    uint32_t bytes = (uint32_t)Gm::VF * 4u;
+    if (have_x)
+      for (int ly = 0; ly < Gm::NL; ++ly) {
+        const int y = DIM == 3 ? y0t - 1 + ly : 0;
+        if (DIM == 2 || (unsigned)y < (unsigned)n1) bytes += (uint32_t)(xb - xa) * (uint32_t)m * 4u;
+      }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    bulk_g2s(smem_u32(vs), V + vblk, (uint32_t)Gm::VF * 4u, mbar);
+    if (have_x)
+      for (int ly = 0; ly < Gm::NL; ++ly) {
+        const int y = DIM == 3 ? y0t - 1 + ly : 0;
+        if (DIM == 3 && (unsigned)y >= (unsigned)n1) continue;
+        const int64_t node0 = DIM == 3 ? ((int64_t)p * n1l + y) * n1l + xa : (int64_t)p * n1l + xa;
+        float* dst = xs + ((int64_t)ly * (Gm::TX + 2) + (xa - (x0t - 1))) * m;
+        bulk_g2s(smem_u32(dst), X + node0 * m, (uint32_t)(xb - xa) * (uint32_t)m * 4u, mbar);
+      }
   }
 }
 
 // MODE: CSR_MV (y = A x), CSR_RESID (y = b - A x), CSR_JACOBI (y = x + omega dinv (b - A x)).
-// Work item = (tile, chunk of planes along the marching axis).  3D: tiles of 16 (x) by
-// TY (y) nodes, a group of tpr threads per 4-row x run, march along z.  2D: tiles of
-// 4 G x nodes, march along y.
 template <int DIM, int MODE>
-__global__ void __launch_bounds__(256, 2)
-    k_stencil(int n1, int xp, int m, int tpr, int G, int TY, int ntx, int nty, int pch, int npc,
-              const float* __restrict__ sv, int64_t P, const float* __restrict__ X, const float* __restrict__ B,
-              float omega, float* __restrict__ Y) {
-  constexpr int T = DIM == 3 ? 27 : 9;
-  const int tid = threadIdx.x;
+__global__ void __launch_bounds__(512, 1)
+    k_stencil(int n1, int m, int tpr, int ntx, int nty, int pch, int npc, const float* __restrict__ V,
+              const float* __restrict__ X, const float* __restrict__ B, float omega, float* __restrict__ Y,
+              int* __restrict__ err) {
+  using Gm = StGeo<DIM>;
+  constexpr int T = Gm::T;
+  extern __shared__ __align__(128) float st_smem[];
+  __shared__ __align__(8) uint64_t mbar[kStStages];
+  const int tid = threadIdx.x, nthreads = blockDim.x;
   const int g = tid / tpr;
   const int col = 4 * (tid - g * tpr);
-  if (g >= G) return;
+  const bool active = g < Gm::G;
+  const int rx = g % Gm::RUNS, ly = g / Gm::RUNS;  // run and line of this group in the tile
+  const int64_t xs_floats = (int64_t)Gm::NL * (Gm::TX + 2) * m;
+  float* xs_base = st_smem;
+  float* vs_base = st_smem + kStStages * xs_floats;
+  if (tid == 0) {
+    for (int s = 0; s < kStStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
   const int64_t n1l = n1;
   const int64_t items = (int64_t)ntx * nty * npc;
-  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+  int64_t gstep = 0;  // stages used so far by this CTA (ring position and mbarrier parity)
+  bool failed = false;
+  for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
     const int tx = (int)(item % ntx);
     const int64_t r = item / ntx;
     const int ty = (int)(r % nty);
     const int pc = (int)(r / nty);
-    int x0, y;
-    if (DIM == 3) {
-      x0 = tx * (kStRuns3 * kStRunX) + (g % kStRuns3) * kStRunX;
-      y = ty * TY + g / kStRuns3;
-    } else {
-      x0 = tx * (G * kStRunX) + g * kStRunX;
-      y = 0;
-    }
-    if (x0 >= n1 || y >= n1) continue;
+    const int x0t = tx * Gm::TX, y0t = ty * Gm::TY;
     const int pb = pc * pch, pe = min(n1, pb + pch);
-    float4 aP[kStRunX], aC[kStRunX], aN[kStRunX];
+    const int x0 = x0t + 4 * rx, y = DIM == 3 ? y0t + ly : 0;
+    const bool rows = active && x0 < n1 && y < n1;
+    // coefficient block of step p (s = p + 1) for this tile
+    auto vblk = [&](int p) -> int64_t { return (((int64_t)(p + 1) * nty + ty) * ntx + tx) * Gm::VF; };
+    {  // prologue: plane pb - 1 (its stage was released by the barrier that ended the last step)
+      const int s = (int)(gstep % kStStages);
+      if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage_issue<DIM>(tid, nthreads, n1, m, x0t, y0t, pb - 1, vblk(pb - 1), X, V, xs_base + s * xs_floats,
+                       vs_base + (int64_t)s * Gm::VF, smem_u32(&mbar[s]));
+    }
+    float4 aP[4], aC[4], aN[4];
 #pragma unroll
-    for (int i = 0; i < kStRunX; ++i) aP[i] = aC[i] = aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int p = pb - 1; p <= pe; ++p) {
-      const bool hasN = p + 1 >= pb && p + 1 < pe;  // output plane p+1 (reads plane p with offset -1)
+    for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int p = pb - 1; p <= pe; ++p, ++gstep) {
+      const int s = (int)(gstep % kStStages);
+      const uint32_t phase = (uint32_t)((gstep / kStStages) & 1);
+      if (p + 1 <= pe) {  // next plane into the stage of plane p - 2 (released by the last barrier)
+        const int s1 = (int)((gstep + 1) % kStStages);
+        if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        stage_issue<DIM>(tid, nthreads, n1, m, x0t, y0t, p + 1, vblk(p + 1), X, V, xs_base + s1 * xs_floats,
+                         vs_base + (int64_t)s1 * Gm::VF, smem_u32(&mbar[s1]));
+      }
+      const bool hasN = p + 1 >= pb && p + 1 < pe;
       const bool hasC = p >= pb && p < pe;
       const bool hasP = p - 1 >= pb && p - 1 < pe;
-      if (p >= 0 && p < n1) {
+      // b of the plane that completes in this step, loaded ahead of the wait
+      float4 bq[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) bq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((MODE == CSR_RESID || MODE == CSR_JACOBI) && hasP && rows) {
+        const int64_t rbase = DIM == 3 ? ((int64_t)(p - 1) * n1l + y) * n1l + x0 : (int64_t)(p - 1) * n1l + x0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (x0 + i < n1) bq[i] = __ldg(reinterpret_cast<const float4*>(B + (rbase + i) * m + col));
+      }
+      // every thread waits for the stage itself; a wait that gives up skips the stage and
+      // the barrier at the end of the step makes the failure known to all
+      const uint32_t ok = mbar_wait_bounded(smem_u32(&mbar[s]), phase, kStWaitLimit);
+      const float* xs = xs_base + s * xs_floats;
+      const float* vs = vs_base + (int64_t)s * Gm::VF;
+      if (ok && rows && p >= 0 && p < n1) {
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
           if (DIM == 2 && dy != 0) continue;
-          const int yy = y + dy;
-          if (DIM == 3 && (unsigned)yy >= (unsigned)n1) continue;
-          float4 xl[kStRunX + 2];
-          const int64_t lbase = DIM == 3 ? ((int64_t)p * n1l + yy) * n1l : (int64_t)p * n1l;
+          const int hl = DIM == 3 ? ly + 1 + dy : 0;  // staged line
+          float4 xl[6];
+          const float* xrow = xs + ((int64_t)hl * (Gm::TX + 2) + 4 * rx) * m + col;
 #pragma unroll
-          for (int j = 0; j < kStRunX + 2; ++j) {
-            const int xx = x0 - 1 + j;
-            xl[j] = (unsigned)xx < (unsigned)n1 ? ldg4(X + (lbase + xx) * m + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = 0; j < 6; ++j) xl[j] = lds4(xrow + (int64_t)j * m);
+          const int tl = DIM == 3 ? 3 * (dy + 1) : 0;
+          const int tz = DIM == 3 ? 9 : 3;
+#pragma unroll
+          for (int role = 0; role < 3; ++role) {  // 0: plane p+1 (offset -1), 1: p, 2: p-1 (offset +1)
+            if ((role == 0 && !hasN) || (role == 1 && !hasC) || (role == 2 && !hasP)) continue;
+            float4(&acc)[4] = role == 0 ? aN : (role == 1 ? aC : aP);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              const int t = tl + role * tz + dx;
+              const float4 v = lds4(vs + ((int64_t)t * Gm::TY + ly) * Gm::TX + 4 * rx);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) fma4(acc[i], vcomp(v, i), xl[i + dx]);
+            }
           }
-          // coefficient rows of the three output planes for this line's taps
-          const int tl = DIM == 3 ? 3 * (dy + 1) : 0;      // (dy) part of the tap index
-          const int tz = DIM == 3 ? 9 : 3;                  // stride of the marching offset
-          const int64_t pstr = DIM == 3 ? n1l * xp : (int64_t)xp;
-          const int64_t ybase = DIM == 3 ? (int64_t)y * xp + x0 : (int64_t)x0;
-          if (hasN) tap_line(aN, xl, sv + (int64_t)(tl + 0 * tz) * P + (int64_t)(p + 1) * pstr + ybase, P);
-          if (hasC) tap_line(aC, xl, sv + (int64_t)(tl + 1 * tz) * P + (int64_t)p * pstr + ybase, P);
-          if (hasP) tap_line(aP, xl, sv + (int64_t)(tl + 2 * tz) * P + (int64_t)(p - 1) * pstr + ybase, P);
         }
       }
-      if (hasP) {  // plane p-1 is complete
+      if (ok && hasP && rows) {  // plane p-1 is complete
         const int q = p - 1;
         const int64_t rbase = DIM == 3 ? ((int64_t)q * n1l + y) * n1l + x0 : (int64_t)q * n1l + x0;
         float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (MODE == CSR_JACOBI) {
-          const int64_t pstr = DIM == 3 ? n1l * xp : (int64_t)xp;
-          const int64_t ybase = DIM == 3 ? (int64_t)y * xp + x0 : (int64_t)x0;
-          dv = ldg4(sv + (int64_t)T * P + (int64_t)q * pstr + ybase);
-        }
+        const float* xprev = xs_base + ((gstep + kStStages - 1) % kStStages) * xs_floats;
+        if (MODE == CSR_JACOBI) dv = lds4(vs + ((int64_t)T * Gm::TY + ly) * Gm::TX + 4 * rx);
 #pragma unroll
-        for (int i = 0; i < kStRunX; ++i) {
+        for (int i = 0; i < 4; ++i) {
           if (x0 + i >= n1) break;
-          const int64_t off = (rbase + i) * m + col;
           float4 o = aP[i];
-          if (MODE == CSR_RESID || MODE == CSR_JACOBI) {
-            const float4 b = ldg4(B + off);
-            o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
-          }
+          if (MODE == CSR_RESID || MODE == CSR_JACOBI)
+            o = make_float4(bq[i].x - o.x, bq[i].y - o.y, bq[i].z - o.z, bq[i].w - o.w);
           if (MODE == CSR_JACOBI) {
-            const float4 xo = ldg4(X + off);
+            const int hl = DIM == 3 ? ly + 1 : 0;
+            const float4 xo = lds4(xprev + ((int64_t)hl * (Gm::TX + 2) + 4 * rx + 1 + i) * m + col);
             const float d = omega * vcomp(dv, i);
             o = make_float4(fmaf(d, o.x, xo.x), fmaf(d, o.y, xo.y), fmaf(d, o.z, xo.z), fmaf(d, o.w, xo.w));
           }
-          *reinterpret_cast<float4*>(Y + off) = o;
+          *reinterpret_cast<float4*>(Y + (rbase + i) * m + col) = o;
         }
       }
 #pragma unroll
-      for (int i = 0; i < kStRunX; ++i) {
+      for (int i = 0; i < 4; ++i) {
         aP[i] = aC[i];
         aC[i] = aN[i];
         aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      // every read of this stage and of the previous one is done, zero fills are visible
+      if (!__syncthreads_and((int)ok)) {  // (uniform) a copy never completed: report, let
+        if (tid == 0) atomicExch(err, 1);  // the copies in flight land (bounded), stop
+        mbar_wait_bounded(smem_u32(&mbar[s]), phase, kStWaitLimit);
+        if (p + 1 <= pe)
+          mbar_wait_bounded(smem_u32(&mbar[(gstep + 1) % kStStages]), (uint32_t)(((gstep + 1) / kStStages) & 1),
+                            kStWaitLimit);
+        failed = true;
+        break;
+      }
     }
   }
+}
+
+template <int DIM>
+size_t st_smem_bytes(int m) {
+  using Gm = StGeo<DIM>;
+  return (size_t)kStStages * ((size_t)Gm::NL * (Gm::TX + 2) * m + Gm::VF) * sizeof(float);
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ setup
 // Recognise the 3^d neighbour pattern of a square CSR level on an n1^d grid and upload
-// the tap-plane layout (FP32 coefficients, then 1 / a_ii).  Leaves A.st_val null when the
-// level is not such a stencil (or too small to be worth it).
+// the step-major coefficient layout.  Leaves A.st_val null when the level is not such a
+// stencil (or too small to be worth it).
 int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv, DevCSR& d) {
   d.st_val = nullptr;
   d.st_dim = d.st_n1 = d.st_xp = 0;
@@ -181,66 +291,72 @@ int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv
       }
     }
     if (!ok) continue;
-    const int T = dim == 3 ? 27 : 9;
-    const int64_t xp = (n1 + 3) / 4 * 4;
-    const int64_t P = (dim == 3 ? n1 * n1 : n1) * xp;
-    std::vector<float> sv((size_t)(T + 1) * P, 0.f);
+    const int T = dim == 3 ? 27 : 9, TX = dim == 3 ? 16 : 64, TY = dim == 3 ? 4 : 1;
+    const int64_t VF = (int64_t)(T + 1) * TY * TX;
+    const int64_t ntx = (n1 + TX - 1) / TX, nty = dim == 3 ? (n1 + TY - 1) / TY : 1;
+    const int64_t steps = n1 + 2;
+    std::vector<float> sv((size_t)(steps * nty * ntx * VF), 0.f);
+    auto slot = [&](int64_t s, int64_t x, int64_t y, int t) -> size_t {
+      const int64_t tx = x / TX, ty = dim == 3 ? y / TY : 0, lx = x % TX, lyy = dim == 3 ? y % TY : 0;
+      return (size_t)(((((s * nty + ty) * ntx + tx) * (T + 1) + t) * TY + lyy) * TX + lx);
+    };
     for (int64_t i = 0; i < N; ++i) {
       const int64_t xi = i % n1, yi = (i / n1) % n1, zi = dim == 3 ? i / (n1 * n1) : 0;
-      const int64_t slot = (dim == 3 ? (zi * n1 + yi) : yi) * xp + xi;
+      const int64_t qi = dim == 3 ? zi : yi;  // plane along the marching axis
       for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
         const int64_t j = A.col[k];
         const int64_t dx = j % n1 - xi, dy = (j / n1) % n1 - yi, dz = dim == 3 ? j / (n1 * n1) - zi : 0;
+        const int64_t off = dim == 3 ? dz : dy;  // offset along the marching axis
         const int t = (int)((dx + 1) + 3 * (dy + 1) + (dim == 3 ? 9 * (dz + 1) : 0));
-        sv[(size_t)t * P + slot] = (float)A.val[k];
+        sv[slot(qi + off + 1, xi, yi, t)] = (float)A.val[k];
       }
-      sv[(size_t)T * P + slot] = (float)dinv[i];
+      sv[slot(qi + 2, xi, yi, T)] = (float)dinv[i];
     }
     PASE_TRY(dev_alloc_t(h, &d.st_val, sv.size()));
     PASE_CUDA(cudaMemcpy(d.st_val, sv.data(), sizeof(float) * sv.size(), cudaMemcpyHostToDevice));
     d.st_dim = dim;
     d.st_n1 = (int)n1;
-    d.st_xp = (int)xp;
+    d.st_xp = 0;
     return PASE_OK;
   }
   return PASE_OK;
 }
 
 bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy) {
-  return A.st_val != nullptr && (mode == CSR_MV || mode == CSR_RESID || mode == CSR_JACOBI) && m % 8 == 0 &&
-         m >= 8 && m <= 256 && (ldx <= 0 || ldx == m) && (ldy <= 0 || ldy == m);
+  if (A.st_val == nullptr || !(mode == CSR_MV || mode == CSR_RESID || mode == CSR_JACOBI)) return false;
+  if (m % 8 != 0 || m < 8 || m > 128 || (ldx > 0 && ldx != m) || (ldy > 0 && ldy != m)) return false;
+  const size_t smem = A.st_dim == 3 ? st_smem_bytes<3>(m) : st_smem_bytes<2>(m);
+  return smem <= 200 * 1024;
 }
 
 // ------------------------------------------------------------------ launch
 int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X, const float* B, double omega,
                    float* Y) {
   const int tpr = m / 4;
-  int G = 16;
-  while (G > 4 && G * tpr > 256) G /= 2;
-  const int dim = A.st_dim, n1 = A.st_n1, xp = A.st_xp;
-  const int64_t P = (int64_t)(dim == 3 ? n1 : 1) * n1 * xp;
-  int TY = 1, ntx, nty;
-  if (dim == 3) {
-    TY = G / kStRuns3;
-    ntx = (n1 + kStRuns3 * kStRunX - 1) / (kStRuns3 * kStRunX);
-    nty = (n1 + TY - 1) / TY;
-  } else {
-    ntx = (n1 + G * kStRunX - 1) / (G * kStRunX);
-    nty = 1;
-  }
-  // planes per work item: enough items for about four waves of two CTAs per SM
+  const int dim = A.st_dim, n1 = A.st_n1;
+  const int TX = dim == 3 ? 16 : 64, TY = dim == 3 ? 4 : 1;
+  const int ntx = (n1 + TX - 1) / TX, nty = dim == 3 ? (n1 + TY - 1) / TY : 1;
+  const int threads = (16 * tpr + 31) / 32 * 32;
+  const size_t smem = dim == 3 ? st_smem_bytes<3>(m) : st_smem_bytes<2>(m);
+  // resident CTAs per SM (shared memory, and the 64K registers at 128 per thread)
+  int per_sm = (int)std::min<size_t>(227 * 1024 / (smem + 1024), 65536 / ((size_t)threads * 128));
+  per_sm = std::max(1, std::min(per_sm, 4));
+  // planes per work item: about six items per resident CTA, at least 8 planes per item
   const int64_t tiles = (int64_t)ntx * nty;
-  const int64_t want = (int64_t)h->num_sms * 2 * 4;
-  int npc = (int)std::max<int64_t>(1, std::min<int64_t>(n1, (want + tiles - 1) / tiles));
+  const int64_t want = (int64_t)h->num_sms * per_sm * 6;
+  int npc = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, n1 / 8), (want + tiles - 1) / tiles));
   const int pch = (n1 + npc - 1) / npc;
   npc = (n1 + pch - 1) / pch;
   const int64_t items = tiles * npc;
-  const int threads = (G * tpr + 31) / 32 * 32;
-  const int grid = (int)std::min<int64_t>(items, 0x7fffffff);
+  const int grid = (int)std::min<int64_t>(items, (int64_t)h->num_sms * per_sm);
   auto s = h->stream;
   const float om = (float)omega;
-#define PASE_ST_LAUNCH(D, MD)                                                                                   \
-  k_stencil<D, MD><<<grid, threads, 0, s>>>(n1, xp, m, tpr, G, TY, ntx, nty, pch, npc, A.st_val, P, X, B, om, Y)
+#define PASE_ST_LAUNCH(D, MD)                                                                             \
+  do {                                                                                                    \
+    PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD>, 200 * 1024));                                \
+    k_stencil<D, MD><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, A.st_val, X, B, om, Y, \
+                                                  h->tc_err);                                             \
+  } while (0)
   if (dim == 3) {
     if (mode == CSR_JACOBI) PASE_ST_LAUNCH(3, CSR_JACOBI);
     else if (mode == CSR_RESID) PASE_ST_LAUNCH(3, CSR_RESID);
