@@ -13,13 +13,14 @@
 //
 // Scheme.  A CTA owns a tile of the grid (16 x 4 nodes of an x-y plane in 3D, 64 nodes of
 // an x line in 2D) and marches along the last axis (z in 3D, y in 2D) over a chunk of
-// planes.  Plane p of X (the tile plus a one-node halo) and the coefficients that meet it
-// arrive in shared memory by bulk asynchronous copies (cp.async.bulk, completion counted
-// on an mbarrier), one plane ahead of the computation, in a ring of three stages.  A
-// thread owns 4 consecutive x rows and one 16-byte column slice; X values of plane p feed
-// the three output planes p-1, p, p+1 through three rolling register accumulators, so each
-// X value is read from shared memory once per (line, x window) and every operand stream
-// (X, b, coefficients, y) crosses HBM once.
+// planes.  Plane p of X (the tile plus a one-node halo), the coefficients that meet it and
+// b of plane p-1 arrive in shared memory by bulk asynchronous copies (cp.async.bulk,
+// completion counted on an mbarrier), several planes ahead of the computation, in a ring
+// of stages.  A thread owns 4 consecutive x rows and one 16-byte column slice; X values of
+// plane p feed the three output planes p-1, p, p+1 through three rolling register
+// accumulators, so each X value is read from shared memory once per (line, x window), and
+// the thread keeps its own rows of plane p in registers for the update of that plane one
+// step later.  Every operand stream (X, b, coefficients, y) crosses HBM once.
 //
 // Coefficient layout ("step-major"), built at setup: the coefficient of row q's tap
 // t = (dx+1) + 3(dy+1) + 9(dz+1) (2D: (dx+1) + 3(dy+1), dy the marching offset) is needed
@@ -38,7 +39,7 @@ namespace pase {
 
 namespace {
 
-constexpr int kStStages = 3;
+constexpr int kStMaxStages = 8;
 constexpr int kStWaitLimit = 1 << 24;  // polls of a stage's mbarrier before giving up
 
 template <int DIM>
@@ -69,17 +70,21 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// One staged plane: the tile's X lines (halo included) and its step's coefficients.  The
-// copies are issued by one thread; out-of-grid parts of the X lines are zero-filled by the
-// whole CTA (disjoint from the copied parts).
-template <int DIM>
-__device__ __forceinline__ void stage_issue(int tid, int nthreads, int n1, int m, int x0t, int y0t, int p, int64_t vblk,
-                                            const float* __restrict__ X, const float* __restrict__ V, float* xs,
-                                            float* vs, uint32_t mbar) {
+// One staged plane, filled by the producer warp: the tile's X lines (halo included), the
+// step's coefficients and (RESID, JACOBI) b of plane p-1, the plane whose update completes
+// while this stage is current.  Lanes zero-fill the out-of-grid parts of the X lines, then
+// lane 0 posts the expected byte count and lanes 0..(copies-1) issue one bulk copy each.
+template <int DIM, bool WITH_B>
+__device__ __forceinline__ void stage_fill(int lane, int n1, int m, int x0t, int y0t, int p, int64_t vblk,
+                                           const float* __restrict__ X, const float* __restrict__ V,
+                                           const float* __restrict__ B, float* xs, float* vs, float* bs,
+                                           uint32_t full) {
   using Gm = StGeo<DIM>;
   const int64_t n1l = n1;
   const bool have_x = p >= 0 && p < n1;
+  const bool have_b = WITH_B && p - 1 >= 0 && p - 1 < n1;
   const int xa = max(0, x0t - 1), xb = min(n1, x0t + Gm::TX + 1);  // in-grid node range of a line
+  const int bxb = min(n1, x0t + Gm::TX);
   const bool interior = x0t >= 1 && x0t + Gm::TX + 1 <= n1 && (DIM == 2 || (y0t >= 1 && y0t + Gm::TY + 1 <= n1));
   if (have_x && !interior) {
     const int m4 = m / 4;
@@ -90,176 +95,220 @@ __device__ __forceinline__ void stage_issue(int tid, int nthreads, int n1, int m
       const int hi = yok ? xb - (x0t - 1) : Gm::TX + 2;
       const int nz = lo + (Gm::TX + 2 - hi);
       float4* line = reinterpret_cast<float4*>(xs + (int64_t)ly * (Gm::TX + 2) * m);
-      for (int k = tid; k < nz * m4; k += nthreads) {
+      for (int k = lane; k < nz * m4; k += 32) {
         const int zn = k / m4, c = k - zn * m4;
         line[(zn < lo ? zn : hi + (zn - lo)) * m4 + c] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
   }
-  if (tid == 0) {
-    uint32_t bytes = (uint32_t)Gm::VF * 4u;
-    if (have_x)
-      for (int ly = 0; ly < Gm::NL; ++ly) {
-        const int y = DIM == 3 ? y0t - 1 + ly : 0;
-        if (DIM == 2 || (unsigned)y < (unsigned)n1) bytes += (uint32_t)(xb - xa) * (uint32_t)m * 4u;
-      }
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-    bulk_g2s(smem_u32(vs), V + vblk, (uint32_t)Gm::VF * 4u, mbar);
-    if (have_x)
-      for (int ly = 0; ly < Gm::NL; ++ly) {
-        const int y = DIM == 3 ? y0t - 1 + ly : 0;
-        if (DIM == 3 && (unsigned)y >= (unsigned)n1) continue;
-        const int64_t node0 = DIM == 3 ? ((int64_t)p * n1l + y) * n1l + xa : (int64_t)p * n1l + xa;
-        float* dst = xs + ((int64_t)ly * (Gm::TX + 2) + (xa - (x0t - 1))) * m;
-        bulk_g2s(smem_u32(dst), X + node0 * m, (uint32_t)(xb - xa) * (uint32_t)m * 4u, mbar);
-      }
+  __syncwarp();
+  // copy j: 0 = coefficients, 1..NL = X lines, NL+1..NL+TY = b lines (absent ones skipped)
+  uint32_t bytes = (uint32_t)Gm::VF * 4u;
+  if (have_x)
+    for (int ly = 0; ly < Gm::NL; ++ly) {
+      const int y = DIM == 3 ? y0t - 1 + ly : 0;
+      if (DIM == 2 || (unsigned)y < (unsigned)n1) bytes += (uint32_t)(xb - xa) * (uint32_t)m * 4u;
+    }
+  if (have_b)
+    for (int ly = 0; ly < Gm::TY; ++ly)
+      if (DIM == 2 || y0t + ly < n1) bytes += (uint32_t)(bxb - x0t) * (uint32_t)m * 4u;
+  if (lane == 0) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes) : "memory");
+  __syncwarp();
+  if (lane == 0) bulk_g2s(smem_u32(vs), V + vblk, (uint32_t)Gm::VF * 4u, full);
+  if (have_x && lane >= 1 && lane <= Gm::NL) {
+    const int ly = lane - 1;
+    const int y = DIM == 3 ? y0t - 1 + ly : 0;
+    if (DIM == 2 || (unsigned)y < (unsigned)n1) {
+      const int64_t node0 = DIM == 3 ? ((int64_t)p * n1l + y) * n1l + xa : (int64_t)p * n1l + xa;
+      float* dst = xs + ((int64_t)ly * (Gm::TX + 2) + (xa - (x0t - 1))) * m;
+      bulk_g2s(smem_u32(dst), X + node0 * m, (uint32_t)(xb - xa) * (uint32_t)m * 4u, full);
+    }
+  }
+  if (have_b && lane > Gm::NL && lane <= Gm::NL + Gm::TY) {
+    const int ly = lane - Gm::NL - 1;
+    const int y = DIM == 3 ? y0t + ly : 0;
+    if (DIM == 2 || y < n1) {
+      const int64_t node0 = DIM == 3 ? ((int64_t)(p - 1) * n1l + y) * n1l + x0t : (int64_t)(p - 1) * n1l + x0t;
+      bulk_g2s(smem_u32(bs + (int64_t)ly * Gm::TX * m), B + node0 * m, (uint32_t)(bxb - x0t) * (uint32_t)m * 4u, full);
+    }
   }
 }
 
 // MODE: CSR_MV (y = A x), CSR_RESID (y = b - A x), CSR_JACOBI (y = x + omega dinv (b - A x)).
-template <int DIM, int MODE>
-__global__ void __launch_bounds__(512, 1)
-    k_stencil(int n1, int m, int tpr, int ntx, int nty, int pch, int npc, const float* __restrict__ V,
+// Warp roles: the last warp fills stages (producer); the others compute (consumers).  A
+// stage is filled once its "empty" barrier shows that every consumer warp has released its
+// previous plane, and read once its "full" barrier shows the copies landed; no CTA-wide
+// barrier in the loop, so consumer warps never wait for each other.
+// WIDE: up to 512 threads (m > 64), one CTA per SM; otherwise up to 256 threads and two
+// CTAs per SM; 128 registers per thread either way.
+template <int DIM, int MODE, bool WIDE>
+__global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
+    k_stencil(int n1, int m, int tpr, int ntx, int nty, int pch, int npc, int NS, const float* __restrict__ V,
               const float* __restrict__ X, const float* __restrict__ B, float omega, float* __restrict__ Y,
               int* __restrict__ err) {
   using Gm = StGeo<DIM>;
   constexpr int T = Gm::T;
+  constexpr bool WB = MODE == CSR_RESID || MODE == CSR_JACOBI;
   extern __shared__ __align__(128) float st_smem[];
-  __shared__ __align__(8) uint64_t mbar[kStStages];
-  const int tid = threadIdx.x, nthreads = blockDim.x;
-  const int g = tid / tpr;
-  const int col = 4 * (tid - g * tpr);
-  const bool active = g < Gm::G;
-  const int rx = g % Gm::RUNS, ly = g / Gm::RUNS;  // run and line of this group in the tile
+  __shared__ __align__(8) uint64_t full[kStMaxStages], empty[kStMaxStages];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5, ncons = nwarps - 1;  // consumer warps
+  const bool producer = warp == ncons;
   const int64_t xs_floats = (int64_t)Gm::NL * (Gm::TX + 2) * m;
+  const int64_t bs_floats = WB ? (int64_t)Gm::TY * Gm::TX * m : 0;
   float* xs_base = st_smem;
-  float* vs_base = st_smem + kStStages * xs_floats;
+  float* vs_base = st_smem + NS * xs_floats;
+  float* bs_base = vs_base + (int64_t)NS * Gm::VF;
   if (tid == 0) {
-    for (int s = 0; s < kStStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    for (int s = 0; s < NS; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(ncons));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
   }
   __syncthreads();
   const int64_t n1l = n1;
   const int64_t items = (int64_t)ntx * nty * npc;
-  int64_t gstep = 0;  // stages used so far by this CTA (ring position and mbarrier parity)
-  bool failed = false;
-  for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
-    const int tx = (int)(item % ntx);
-    const int64_t r = item / ntx;
-    const int ty = (int)(r % nty);
-    const int pc = (int)(r / nty);
-    const int x0t = tx * Gm::TX, y0t = ty * Gm::TY;
-    const int pb = pc * pch, pe = min(n1, pb + pch);
-    const int x0 = x0t + 4 * rx, y = DIM == 3 ? y0t + ly : 0;
-    const bool rows = active && x0 < n1 && y < n1;
-    // coefficient block of step p (s = p + 1) for this tile
-    auto vblk = [&](int p) -> int64_t { return (((int64_t)(p + 1) * nty + ty) * ntx + tx) * Gm::VF; };
-    {  // prologue: plane pb - 1 (its stage was released by the barrier that ended the last step)
-      const int s = (int)(gstep % kStStages);
-      if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      stage_issue<DIM>(tid, nthreads, n1, m, x0t, y0t, pb - 1, vblk(pb - 1), X, V, xs_base + s * xs_floats,
-                       vs_base + (int64_t)s * Gm::VF, smem_u32(&mbar[s]));
+  int64_t gstep = 0;  // stage uses so far (ring position and barrier parities)
+  if (producer) {
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+      const int tx = (int)(item % ntx);
+      const int64_t r = item / ntx;
+      const int ty = (int)(r % nty);
+      const int pc = (int)(r / nty);
+      const int x0t = tx * Gm::TX, y0t = ty * Gm::TY;
+      const int pb = pc * pch, pe = min(n1, pb + pch);
+      for (int p = pb - 1; p <= pe; ++p, ++gstep) {
+        const int s = (int)(gstep % NS);
+        if (gstep >= NS) {  // every consumer warp has released the plane this stage held
+          const uint32_t ok = mbar_wait_bounded(smem_u32(&empty[s]), (uint32_t)((gstep / NS - 1) & 1), kStWaitLimit);
+          if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&abort_flag) {
+            if (lane == 0) {
+              atomicExch(err, 1);
+              *(volatile int*)&abort_flag = 1;
+            }
+            item = items;
+            break;
+          }
+        }
+        const int64_t vblk = (((int64_t)(p + 1) * nty + ty) * ntx + tx) * Gm::VF;
+        stage_fill<DIM, WB>(lane, n1, m, x0t, y0t, p, vblk, X, V, B, xs_base + s * xs_floats,
+                            vs_base + (int64_t)s * Gm::VF, bs_base + s * bs_floats, smem_u32(&full[s]));
+      }
     }
-    float4 aP[4], aC[4], aN[4];
+    // let the copies in flight land before the CTA exits (bounded)
+    for (int64_t g = gstep - NS; g < gstep; ++g)
+      if (g >= 0) mbar_wait_bounded(smem_u32(&full[g % NS]), (uint32_t)((g / NS) & 1), kStWaitLimit);
+  } else {
+    const int g = tid / tpr;  // 4-row group of this thread
+    const int col = 4 * (tid - g * tpr);
+    const bool active = g < Gm::G;
+    const int rx = g % Gm::RUNS, ly = g / Gm::RUNS;
+    bool failed = false;
+    for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+      const int tx = (int)(item % ntx);
+      const int64_t r = item / ntx;
+      const int ty = (int)(r % nty);
+      const int pc = (int)(r / nty);
+      const int x0t = tx * Gm::TX, y0t = ty * Gm::TY;
+      const int pb = pc * pch, pe = min(n1, pb + pch);
+      const int x0 = x0t + 4 * rx, y = DIM == 3 ? y0t + ly : 0;
+      const bool rows = active && x0 < n1 && y < n1;
+      float4 aP[4], aC[4], aN[4], xo[4];  // xo: X of the own rows on the previous plane
 #pragma unroll
-    for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int p = pb - 1; p <= pe; ++p, ++gstep) {
-      const int s = (int)(gstep % kStStages);
-      const uint32_t phase = (uint32_t)((gstep / kStStages) & 1);
-      if (p + 1 <= pe) {  // next plane into the stage of plane p - 2 (released by the last barrier)
-        const int s1 = (int)((gstep + 1) % kStStages);
-        if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        stage_issue<DIM>(tid, nthreads, n1, m, x0t, y0t, p + 1, vblk(p + 1), X, V, xs_base + s1 * xs_floats,
-                         vs_base + (int64_t)s1 * Gm::VF, smem_u32(&mbar[s1]));
-      }
-      const bool hasN = p + 1 >= pb && p + 1 < pe;
-      const bool hasC = p >= pb && p < pe;
-      const bool hasP = p - 1 >= pb && p - 1 < pe;
-      // b of the plane that completes in this step, loaded ahead of the wait
-      float4 bq[4];
+      for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = xo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int p = pb - 1; p <= pe; ++p, ++gstep) {
+        const int s = (int)(gstep % NS);
+        const bool hasN = p + 1 >= pb && p + 1 < pe;
+        const bool hasC = p >= pb && p < pe;
+        const bool hasP = p - 1 >= pb && p - 1 < pe;
+        const uint32_t ok = mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((gstep / NS) & 1), kStWaitLimit);
+        if (!ok || *(volatile int*)&abort_flag) {
+          if (!ok) {
+            atomicExch(err, 1);
+            *(volatile int*)&abort_flag = 1;
+          }
+          failed = true;
+          break;
+        }
+        const float* xs = xs_base + s * xs_floats;
+        const float* vs = vs_base + (int64_t)s * Gm::VF;
+        const float* bs = bs_base + s * bs_floats;
+        // the update of plane p-1, complete once plane p's lines have been applied
+        auto epilogue = [&]() {
+          const int q = p - 1;
+          const int64_t rbase = DIM == 3 ? ((int64_t)q * n1l + y) * n1l + x0 : (int64_t)q * n1l + x0;
+          float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (MODE == CSR_JACOBI) dv = lds4(vs + ((int64_t)T * Gm::TY + ly) * Gm::TX + 4 * rx);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) bq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if ((MODE == CSR_RESID || MODE == CSR_JACOBI) && hasP && rows) {
-        const int64_t rbase = DIM == 3 ? ((int64_t)(p - 1) * n1l + y) * n1l + x0 : (int64_t)(p - 1) * n1l + x0;
+          for (int i = 0; i < 4; ++i) {
+            if (x0 + i >= n1) break;
+            float4 o = aP[i];
+            if (WB) {
+              const float4 b = lds4(bs + ((int64_t)ly * Gm::TX + 4 * rx + i) * m + col);
+              o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
+            }
+            if (MODE == CSR_JACOBI) {
+              const float d = omega * vcomp(dv, i);
+              o = make_float4(fmaf(d, o.x, xo[i].x), fmaf(d, o.y, xo[i].y), fmaf(d, o.z, xo[i].z),
+                              fmaf(d, o.w, xo[i].w));
+            }
+            *reinterpret_cast<float4*>(Y + (rbase + i) * m + col) = o;
+          }
+        };
+        if (rows && p >= 0 && p < n1) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (x0 + i < n1) bq[i] = __ldg(reinterpret_cast<const float4*>(B + (rbase + i) * m + col));
-      }
-      // every thread waits for the stage itself; a wait that gives up skips the stage and
-      // the barrier at the end of the step makes the failure known to all
-      const uint32_t ok = mbar_wait_bounded(smem_u32(&mbar[s]), phase, kStWaitLimit);
-      const float* xs = xs_base + s * xs_floats;
-      const float* vs = vs_base + (int64_t)s * Gm::VF;
-      if (ok && rows && p >= 0 && p < n1) {
+          for (int dl = 0; dl < 3; ++dl) {  // lines y-1, y+1, then the centre line
+            const int dy = dl == 0 ? -1 : (dl == 1 ? 1 : 0);
+            if (DIM == 2 && dy != 0) continue;
+            const int hl = DIM == 3 ? ly + 1 + dy : 0;  // staged line
+            float4 xl[6];
+            const float* xrow = xs + ((int64_t)hl * (Gm::TX + 2) + 4 * rx) * m + col;
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          if (DIM == 2 && dy != 0) continue;
-          const int hl = DIM == 3 ? ly + 1 + dy : 0;  // staged line
-          float4 xl[6];
-          const float* xrow = xs + ((int64_t)hl * (Gm::TX + 2) + 4 * rx) * m + col;
+            for (int j = 0; j < 6; ++j) xl[j] = lds4(xrow + (int64_t)j * m);
+            const int tl = DIM == 3 ? 3 * (dy + 1) : 0;
+            const int tz = DIM == 3 ? 9 : 3;
 #pragma unroll
-          for (int j = 0; j < 6; ++j) xl[j] = lds4(xrow + (int64_t)j * m);
-          const int tl = DIM == 3 ? 3 * (dy + 1) : 0;
-          const int tz = DIM == 3 ? 9 : 3;
+            for (int role = 0; role < 3; ++role) {  // 0: plane p+1 (offset -1), 1: p, 2: p-1 (offset +1)
+              if ((role == 0 && !hasN) || (role == 1 && !hasC) || (role == 2 && !hasP)) continue;
+              float4(&acc)[4] = role == 0 ? aN : (role == 1 ? aC : aP);
 #pragma unroll
-          for (int role = 0; role < 3; ++role) {  // 0: plane p+1 (offset -1), 1: p, 2: p-1 (offset +1)
-            if ((role == 0 && !hasN) || (role == 1 && !hasC) || (role == 2 && !hasP)) continue;
-            float4(&acc)[4] = role == 0 ? aN : (role == 1 ? aC : aP);
+              for (int dx = 0; dx < 3; ++dx) {
+                const int t = tl + role * tz + dx;
+                const float4 v = lds4(vs + ((int64_t)t * Gm::TY + ly) * Gm::TX + 4 * rx);
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const int t = tl + role * tz + dx;
-              const float4 v = lds4(vs + ((int64_t)t * Gm::TY + ly) * Gm::TX + 4 * rx);
+                for (int i = 0; i < 4; ++i) fma4(acc[i], vcomp(v, i), xl[i + dx]);
+              }
+            }
+            if (dy == 0) {  // last line: plane p-1 is complete; the own rows of plane p are kept
+              if (hasP) epilogue();
 #pragma unroll
-              for (int i = 0; i < 4; ++i) fma4(acc[i], vcomp(v, i), xl[i + dx]);
+              for (int i = 0; i < 4; ++i) xo[i] = xl[i + 1];
             }
           }
+        } else if (rows && hasP) {
+          epilogue();
         }
-      }
-      if (ok && hasP && rows) {  // plane p-1 is complete
-        const int q = p - 1;
-        const int64_t rbase = DIM == 3 ? ((int64_t)q * n1l + y) * n1l + x0 : (int64_t)q * n1l + x0;
-        float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float* xprev = xs_base + ((gstep + kStStages - 1) % kStStages) * xs_floats;
-        if (MODE == CSR_JACOBI) dv = lds4(vs + ((int64_t)T * Gm::TY + ly) * Gm::TX + 4 * rx);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          if (x0 + i >= n1) break;
-          float4 o = aP[i];
-          if (MODE == CSR_RESID || MODE == CSR_JACOBI)
-            o = make_float4(bq[i].x - o.x, bq[i].y - o.y, bq[i].z - o.z, bq[i].w - o.w);
-          if (MODE == CSR_JACOBI) {
-            const int hl = DIM == 3 ? ly + 1 : 0;
-            const float4 xo = lds4(xprev + ((int64_t)hl * (Gm::TX + 2) + 4 * rx + 1 + i) * m + col);
-            const float d = omega * vcomp(dv, i);
-            o = make_float4(fmaf(d, o.x, xo.x), fmaf(d, o.y, xo.y), fmaf(d, o.z, xo.z), fmaf(d, o.w, xo.w));
-          }
-          *reinterpret_cast<float4*>(Y + (rbase + i) * m + col) = o;
+          aP[i] = aC[i];
+          aC[i] = aN[i];
+          aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        aP[i] = aC[i];
-        aC[i] = aN[i];
-        aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      // every read of this stage and of the previous one is done, zero fills are visible
-      if (!__syncthreads_and((int)ok)) {  // (uniform) a copy never completed: report, let
-        if (tid == 0) atomicExch(err, 1);  // the copies in flight land (bounded), stop
-        mbar_wait_bounded(smem_u32(&mbar[s]), phase, kStWaitLimit);
-        if (p + 1 <= pe)
-          mbar_wait_bounded(smem_u32(&mbar[(gstep + 1) % kStStages]), (uint32_t)(((gstep + 1) / kStStages) & 1),
-                            kStWaitLimit);
-        failed = true;
-        break;
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
       }
     }
   }
+  __syncthreads();
 }
 
 template <int DIM>
-size_t st_smem_bytes(int m) {
+size_t st_stage_bytes(int m, bool with_b) {
   using Gm = StGeo<DIM>;
-  return (size_t)kStStages * ((size_t)Gm::NL * (Gm::TX + 2) * m + Gm::VF) * sizeof(float);
+  return ((size_t)Gm::NL * (Gm::TX + 2) * m + Gm::VF + (with_b ? (size_t)Gm::TY * Gm::TX * m : 0)) * sizeof(float);
 }
 
 }  // namespace
@@ -325,8 +374,8 @@ int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv
 bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy) {
   if (A.st_val == nullptr || !(mode == CSR_MV || mode == CSR_RESID || mode == CSR_JACOBI)) return false;
   if (m % 8 != 0 || m < 8 || m > 128 || (ldx > 0 && ldx != m) || (ldy > 0 && ldy != m)) return false;
-  const size_t smem = A.st_dim == 3 ? st_smem_bytes<3>(m) : st_smem_bytes<2>(m);
-  return smem <= 200 * 1024;
+  const size_t stage = A.st_dim == 3 ? st_stage_bytes<3>(m, true) : st_stage_bytes<2>(m, true);
+  return 2 * stage <= 200 * 1024;
 }
 
 // ------------------------------------------------------------------ launch
@@ -336,11 +385,20 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
   const int dim = A.st_dim, n1 = A.st_n1;
   const int TX = dim == 3 ? 16 : 64, TY = dim == 3 ? 4 : 1;
   const int ntx = (n1 + TX - 1) / TX, nty = dim == 3 ? (n1 + TY - 1) / TY : 1;
-  const int threads = (16 * tpr + 31) / 32 * 32;
-  const size_t smem = dim == 3 ? st_smem_bytes<3>(m) : st_smem_bytes<2>(m);
-  // resident CTAs per SM (shared memory, and the 64K registers at 128 per thread)
-  int per_sm = (int)std::min<size_t>(227 * 1024 / (smem + 1024), 65536 / ((size_t)threads * 128));
-  per_sm = std::max(1, std::min(per_sm, 4));
+  const int threads = (16 * tpr + 31) / 32 * 32 + 32;  // consumer warps + the producer warp
+  const bool wb = mode == CSR_RESID || mode == CSR_JACOBI;
+  const size_t stage = dim == 3 ? st_stage_bytes<3>(m, wb) : st_stage_bytes<2>(m, wb);
+  // Resident consumer warps, not pipeline depth, set the rate (measured at 128^3, m = 56:
+  // one CTA per SM 0.55 ms with 2 to 4 stages, two CTAs per SM 0.37 ms with 2), so two
+  // CTAs per SM when their registers (128 per thread) and stages fit, each with as many
+  // stages as shared memory leaves.
+  int per_sm = threads <= 256 ? 2 : 1;
+  int NS = (int)std::min<size_t>(kStMaxStages, (200 * 1024) / per_sm / stage);
+  if (NS < 2) {
+    per_sm = 1;
+    NS = (int)std::min<size_t>(kStMaxStages, (200 * 1024) / stage);
+  }
+  const size_t smem = (size_t)NS * stage;
   // planes per work item: about six items per resident CTA, at least 8 planes per item
   const int64_t tiles = (int64_t)ntx * nty;
   const int64_t want = (int64_t)h->num_sms * per_sm * 6;
@@ -351,11 +409,17 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
   const int grid = (int)std::min<int64_t>(items, (int64_t)h->num_sms * per_sm);
   auto s = h->stream;
   const float om = (float)omega;
-#define PASE_ST_LAUNCH(D, MD)                                                                             \
-  do {                                                                                                    \
-    PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD>, 200 * 1024));                                \
-    k_stencil<D, MD><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, A.st_val, X, B, om, Y, \
-                                                  h->tc_err);                                             \
+#define PASE_ST_LAUNCH(D, MD)                                                                                 \
+  do {                                                                                                        \
+    if (threads > 256) {                                                                                      \
+      PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, true>, 200 * 1024));                              \
+      k_stencil<D, MD, true><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B, om, \
+                                                          Y, h->tc_err);                                      \
+    } else {                                                                                                  \
+      PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, false>, 200 * 1024));                             \
+      k_stencil<D, MD, false><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B,    \
+                                                           om, Y, h->tc_err);                                 \
+    }                                                                                                         \
   } while (0)
   if (dim == 3) {
     if (mode == CSR_JACOBI) PASE_ST_LAUNCH(3, CSR_JACOBI);
