@@ -243,6 +243,28 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
  * [N][m]).  The hot kernel of steps (b) and the residual; exposed for measurement. */
 int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX);
 
+/* The batch scheme of §5 (Alg. 7) for many eigenpairs: the first nev pairs computed in
+ * batches of about k, one batch after the other, each with a block of m columns (its own
+ * pairs plus guard columns).
+ *   1. the first nev + m pairs of the coarse pencil (A_H, M_H), by a dense solve;
+ *   2. batch bounds every k pairs, moved up past coarse eigenvalues within a relative gap
+ *      of 1e-3 of their predecessor (no coarse cluster split between batches);
+ *   3. per batch, from U = I_H^h u_H and the coarse eigenvalues: (c) the linear solve of the
+ *      handle's options, (d) the 2m pairs of the augmented pencil nearest the shift theta
+ *      (the midpoint of the batch's coarse eigenvalues), by a dense generalized eigensolve
+ *      of the (N_H + m)-sized pencil, (e) the m of them with the largest b-norm component
+ *      in span(W) (X GM = C_H^T bH + C_W^T GM, component X(i,:) GM X(i,:)^T), prolongated,
+ *      stop when the batch's own pairs meet tol, else (f) the linear solve again from the
+ *      new block.
+ * The dense step (d) needs N_H + m <= 6400 and nev + 3m <= 1024 unless N_H + m <= 1024.
+ * The scheme relies on V_H resolving the pairs of earlier batches (their components grow
+ * in the later batches' linear solves): with too coarse a V_H later batches stall.
+ * lambda [nev] (ascending within a batch), U [N][nev] (row-major, M-orthonormal within a
+ * batch).  Returns PASE_ERR_NOT_CONVERGED (outputs written) when a batch stops at max_iter.
+ * st->iterations sums the iterations of all batches. */
+int pase_solve_batches(pase_handle h, int nev, int k, int m, double tol, double* lambda, double* U,
+                       pase_stats* st);
+
 /* `sweeps` damped-Jacobi sweeps x <- x + omega D^-1 (b - A_h x) on the fine level (the
  * smoother of step (a), Alg. 3 step 3), in the precision the handle smooths in: FP32 for
  * PASE_PREC_MIXED (B and X rounded to FP32 on entry, X returned widened to FP64), FP64

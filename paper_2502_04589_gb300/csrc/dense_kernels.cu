@@ -9,6 +9,8 @@
 #include <cooperative_groups.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include "pase_internal.h"
 
 namespace pase {
@@ -1443,6 +1445,74 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
   k_sygv_back<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+}  // namespace pase
+
+namespace pase {
+
+// ------------------------------------------------------------------ dense helpers (batch scheme)
+// Row r of a CSR matrix into row r of a dense row-major block (zeros elsewhere); one CTA
+// per row.
+__global__ void k_csr_to_dense(int64_t n, int64_t ncols, const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, const double* __restrict__ val, double* __restrict__ D,
+                               int64_t ld) {
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    double* row = D + r * ld;
+    for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) row[c] = 0.0;
+    __syncthreads();
+    for (int64_t k = rowptr[r] + threadIdx.x; k < rowptr[r + 1]; k += blockDim.x) row[col[k]] = val[k];
+    __syncthreads();
+  }
+}
+int launch_csr_to_dense(pase_ctx* h, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
+                        const double* val, double* D, int64_t ld) {
+  if (n == 0) return PASE_OK;
+  k_csr_to_dense<<<(unsigned)std::min<int64_t>(n, 152 * 8), 256, 0, h->stream>>>(n, ncols, rowptr, col, val, D, ld);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// B[j][i] = A[i][j] for an rows x cols block
+__global__ void k_transpose(int64_t rows, int64_t cols, const double* __restrict__ A, int64_t lda,
+                            double* __restrict__ B, int64_t ldb) {
+  const int64_t total = rows * cols;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / cols, j = idx % cols;
+    B[j * ldb + i] = A[i * lda + j];
+  }
+}
+int launch_transpose(pase_ctx* h, int64_t rows, int64_t cols, const double* A, int64_t lda, double* B, int64_t ldb) {
+  const int64_t total = rows * cols;
+  if (total == 0) return PASE_OK;
+  k_transpose<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, h->stream>>>(rows, cols, A, lda,
+                                                                                                 B, ldb);
+  h->launches++;
+  PASE_CUDA(cudaGetLastError());
+  return PASE_OK;
+}
+
+// dst[r][c] = src[r][idx[c]] for r < n, c < k
+__global__ void k_gather_cols(int64_t n, int k, const double* __restrict__ src, int64_t lds,
+                              const int* __restrict__ idx, double* __restrict__ dst, int64_t ldd) {
+  const int64_t total = n * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / k;
+    const int c = (int)(t % k);
+    dst[r * ldd + c] = src[r * lds + idx[c]];
+  }
+}
+int launch_gather_cols(pase_ctx* h, int64_t n, int k, const double* src, int64_t lds, const int* idx, double* dst,
+                       int64_t ldd) {
+  const int64_t total = n * k;
+  if (total == 0) return PASE_OK;
+  k_gather_cols<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, h->stream>>>(n, k, src, lds, idx,
+                                                                                                   dst, ldd);
+  h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
 }

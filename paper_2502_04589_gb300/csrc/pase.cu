@@ -995,6 +995,90 @@ static int iterate_body(pase_ctx* h, double* U, double* lam, bool do_solve, pase
   return PASE_OK;
 }
 
+// ------------------------------------------------------------------ batch scheme (§5)
+// Batch boundaries (Alg. 7 step 2): batches of k pairs, a boundary moved up past any coarse
+// eigenvalue within a relative gap of its predecessor, so that no cluster of the coarse
+// spectrum is split between two batches.
+static std::vector<std::pair<int, int>> batch_bounds(const std::vector<double>& lamH, int nev, int k) {
+  std::vector<std::pair<int, int>> out;
+  int m0 = 0;
+  while (m0 < nev) {
+    int e = std::min(nev, m0 + k);
+    while (e < nev && lamH[e] - lamH[e - 1] <= 1e-3 * lamH[e]) ++e;
+    out.push_back({m0, e});
+    m0 = e;
+  }
+  return out;
+}
+
+static int batch_alloc(pase_ctx* h, int nev, int m) {
+  auto& b = h->bb;
+  if (b.AHd && b.nev >= nev && b.m == m) return PASE_OK;
+  const int64_t NH = h->NH;
+  b.nev = nev;
+  b.m = m;
+  b.top = nev + m;
+  b.n = (int)NH + m;
+  b.kk = std::min(b.n, nev + 3 * m);
+  b.nw = std::min(2 * m, b.kk);
+  PASE_TRY(dev_alloc_t(h, &b.AHd, (size_t)NH * NH));
+  PASE_TRY(dev_alloc_t(h, &b.MHd, (size_t)NH * NH));
+  PASE_TRY(dev_alloc_t(h, &b.CHc, (size_t)NH * b.top));
+  PASE_TRY(dev_alloc_t(h, &b.lamH, (size_t)b.top));
+  PASE_TRY(dev_alloc_t(h, &b.Ad, (size_t)b.n * b.n));
+  PASE_TRY(dev_alloc_t(h, &b.Bd, (size_t)b.n * b.n));
+  PASE_TRY(dev_alloc_t(h, &b.Cw, (size_t)b.n * b.kk));
+  PASE_TRY(dev_alloc_t(h, &b.lamw, (size_t)b.kk));
+  PASE_TRY(dev_alloc_t(h, &b.Cc, (size_t)b.n * b.nw));
+  PASE_TRY(dev_alloc_t(h, &b.Rm, (size_t)b.nw * m));
+  PASE_TRY(dev_alloc_t(h, &b.Rt, (size_t)m * b.nw));
+  PASE_TRY(dev_alloc_t(h, &b.Rt2, (size_t)m * b.nw));
+  PASE_TRY(dev_alloc_t(h, &b.S, (size_t)m * m));
+  PASE_TRY(dev_alloc_t(h, &b.comp, (size_t)b.nw));
+  PASE_TRY(dev_alloc_t(h, &b.idx, (size_t)std::max(b.nw, m)));
+  b.eig_doubles = std::max(small_sygv_work_doubles((int)NH, b.top), small_sygv_work_doubles(b.n, b.kk)) + 64;
+  PASE_TRY(dev_alloc_t(h, &b.eig, b.eig_doubles));
+  return PASE_OK;
+}
+
+// small_sygv on the batch workspace (the handle's own is sized for 3m)
+static int batch_sygv(pase_ctx* h, int n, int k, const double* A, const double* B, double* lam, double* C) {
+  Work& w = h->w;
+  double* keep = w.eigwork;
+  const size_t keep_n = w.eigwork_doubles;
+  w.eigwork = h->bb.eig;
+  w.eigwork_doubles = h->bb.eig_doubles;
+  const int rc = small_sygv(h, n, k, A, n, B, n, lam, C, k, w.status);
+  w.eigwork = keep;
+  w.eigwork_doubles = keep_n;
+  PASE_TRY(rc);
+  PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
+  if (w.h_status[0] != 0) return fail(PASE_ERR_NOT_SPD, "batch scheme: dense generalized eigensolve failed");
+  return PASE_OK;
+}
+
+static int upload_ints(pase_ctx* h, const std::vector<int>& v, int* d) {
+  PASE_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, h->stream));
+  return PASE_OK;
+}
+
+// the augmented pencil of Alg. 7 step (d), dense: [[A_H, aH], [aH^T, GA]], [[M_H, bH], [bH^T, GM]]
+static int batch_assemble(pase_ctx* h) {
+  auto& b = h->bb;
+  Work& w = h->w;
+  const int64_t NH = h->NH, n = b.n;
+  const int m = w.m;
+  const double* src[2][3] = {{b.AHd, w.aH, w.GA}, {b.MHd, w.bH, w.GM}};
+  double* dst[2] = {b.Ad, b.Bd};
+  for (int q = 0; q < 2; ++q) {
+    PASE_TRY(launch_geam(h, NH, (int)NH, 1.0, src[q][0], NH, 0.0, src[q][0], NH, dst[q], n));
+    PASE_TRY(launch_copy_cols(h, NH, m, src[q][1], m, dst[q] + NH, (int)n));
+    PASE_TRY(launch_transpose(h, NH, m, src[q][1], m, dst[q] + NH * n, n));
+    PASE_TRY(launch_copy_cols(h, m, m, src[q][2], m, dst[q] + NH * n + NH, (int)n));
+  }
+  return PASE_OK;
+}
+
 }  // namespace pase
 
 using namespace pase;
@@ -1579,6 +1663,145 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   h->aug_nconv = 0;
   if (stp) *stp = st;
   if (sm_active(h)) PASE_TRY(sm_check_timeout(h));
+  PASE_TRY(tc_check(h));
+  return rc;
+}
+
+int pase_solve_batches(pase_handle h, int nev, int k, int m, double tol, double* lambda, double* U,
+                                  pase_stats* stp) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (!h->ready) return fail(PASE_ERR_STATE, "pase_setup has not completed");
+  if (nev < 1 || k < 1 || m < k + 1 || !(tol > 0.0) || !lambda || !U)
+    return fail(PASE_ERR_INVALID_ARG, "pase_solve_batches: bad arguments (need nev >= 1, 1 <= k < m)");
+  PASE_TRY(reserve(h, m));
+  const int64_t NH = h->NH, N = h->N;
+  if (NH < (int64_t)nev + m) return fail(PASE_ERR_INVALID_ARG, "pase_solve_batches: the coarse space needs nev + m pairs");
+  if (nev + 3 * m > 1024 && NH + m > 1024)
+    return fail(PASE_ERR_INVALID_ARG, "pase_solve_batches: nev + 3m above 1024 pairs of the dense solve");
+  PASE_TRY(batch_alloc(h, nev, m));
+  auto& b = h->bb;
+  Work& w = h->w;
+  pase_stats st;
+  memset(&st, 0, sizeof(st));
+  const int64_t launches0 = h->launches;
+  auto t0 = std::chrono::steady_clock::now();
+  Stage sg(h);
+  void *dl, *dU;
+  PASE_TRY(sg.out(lambda, sizeof(double) * nev, &dl));
+  PASE_TRY(sg.out(U, sizeof(double) * N * nev, &dU));
+  // step 1: the first nev + m coarse pairs (dense)
+  DevCSR MHc = h->AH;
+  MHc.val = h->MH_val;
+  PASE_TRY(launch_csr_to_dense(h, NH, NH, h->AH.rowptr, h->AH.col, h->AH.val, b.AHd, NH));
+  PASE_TRY(launch_csr_to_dense(h, NH, NH, MHc.rowptr, MHc.col, MHc.val, b.MHd, NH));
+  PASE_TRY(batch_sygv(h, (int)NH, b.top, b.AHd, b.MHd, b.lamH, b.CHc));
+  std::vector<double> lamH(b.top), lamw(b.kk), comp(b.nw), lam_out(nev), lam_b(m), rr(m);
+  PASE_CUDA(cudaMemcpyAsync(lamH.data(), b.lamH, sizeof(double) * b.top, cudaMemcpyDeviceToHost, h->stream));
+  PASE_CUDA(cudaStreamSynchronize(h->stream));
+  int rc = PASE_OK;
+  double worst_all = 0.0;
+  int conv_all = 0;
+  // step 2: batches; step 3 for each
+  for (const auto& be : batch_bounds(lamH, nev, k)) {
+    const int m0 = be.first, kb = be.second - be.first;
+    if (kb >= m) {
+      rc = fail(PASE_ERR_INVALID_ARG, "pase_solve_batches: a coarse cluster is wider than the block (raise m)");
+      break;
+    }
+    // (a) U = I_H^h u_H[:, m0 .. m0+m), Lambda = lambda_H[m0 .. m0+m)
+    PASE_TRY(launch_copy_cols(h, NH, m, b.CHc + m0, b.top, w.CH, m));
+    PASE_TRY(launch_csr<double>(h, CSR_MV, m, h->Pd, h->Pd.val, nullptr, w.CH, nullptr, nullptr, nullptr, nullptr, 0.0,
+                                w.U, nullptr, nullptr, nullptr));
+    for (int j = 0; j < m; ++j) lam_b[j] = lamH[m0 + j];
+    PASE_CUDA(cudaMemcpyAsync(w.lam, lam_b.data(), sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+    // (b) the shift: midpoint of the batch's coarse eigenvalues
+    const double theta = 0.5 * (lamH[m0] + lamH[m0 + kb - 1]);
+    bool conv = false;
+    double worst = INFINITY;
+    for (int it = 1; it <= h->opt.max_iter && !conv; ++it) {
+      st.iterations++;
+      // (c) linear solve A_h w = lambda M_h u from u
+      PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+      PASE_TRY(step_linear_solve(h, w.U, w.W));
+      // (d) the pairs of the augmented pencil nearest theta
+      PASE_TRY(step_project(h, w.W, w.aH, w.bH, w.GA, w.GM));
+      PASE_TRY(batch_assemble(h));
+      PASE_TRY(batch_sygv(h, b.n, b.kk, b.Ad, b.Bd, b.lamw, b.Cw));
+      PASE_CUDA(cudaMemcpyAsync(lamw.data(), b.lamw, sizeof(double) * b.kk, cudaMemcpyDeviceToHost, h->stream));
+      PASE_CUDA(cudaStreamSynchronize(h->stream));
+      std::vector<int> order(b.kk);
+      for (int i = 0; i < b.kk; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int c) { return std::fabs(lamw[a] - theta) < std::fabs(lamw[c] - theta); });
+      std::vector<int> win(order.begin(), order.begin() + b.nw);
+      std::sort(win.begin(), win.end());
+      if (win.back() == b.kk - 1 && b.kk < b.n) {
+        rc = fail(PASE_ERR_INVALID_ARG, "pase_solve_batches: the window reaches past the computed pairs");
+        break;
+      }
+      // (e) components in span(W): X GM = C_H^T bH + C_W^T GM, ||Pi v_i||_b^2 = X(i,:) GM X(i,:)^T
+      PASE_TRY(upload_ints(h, win, b.idx));
+      PASE_TRY(launch_gather_cols(h, b.n, b.nw, b.Cw, b.kk, b.idx, b.Cc, b.nw));
+      PASE_TRY(ts_gram(h, NH, b.nw, m, b.Cc, b.nw, w.bH, m, b.Rm, m, false));
+      PASE_TRY(small_gemm(h, b.nw, m, m, 1.0, b.Cc + NH * b.nw, b.nw, true, w.GM, m, 1.0, b.Rm, m));
+      PASE_TRY(launch_transpose(h, b.nw, m, b.Rm, m, b.Rt, b.nw));
+      PASE_CUDA(cudaMemcpyAsync(b.Rt2, b.Rt, sizeof(double) * m * b.nw, cudaMemcpyDeviceToDevice, h->stream));
+      PASE_TRY(launch_copy_cols(h, m, m, w.GM, m, b.S, m));
+      PASE_TRY(small_chol_solve(h, m, b.nw, b.S, m, b.Rt, b.nw, w.status, true));  // X^T = GM^-1 R^T
+      PASE_TRY(launch_coldot(h, m, b.nw, b.Rt2, b.Rt, b.comp));
+      PASE_CUDA(cudaMemcpyAsync(comp.data(), b.comp, sizeof(double) * b.nw, cudaMemcpyDeviceToHost, h->stream));
+      PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
+      if (w.h_status[0] != 0) {
+        rc = fail(PASE_ERR_NOT_SPD, "pase_solve_batches: the Gram block of M_h is not positive definite");
+        break;
+      }
+      std::vector<int> pick(b.nw);
+      for (int i = 0; i < b.nw; ++i) pick[i] = i;
+      std::stable_sort(pick.begin(), pick.end(), [&](int a, int c) { return comp[a] > comp[c]; });
+      pick.resize(m);
+      std::sort(pick.begin(), pick.end());
+      std::vector<int> sel(m);
+      for (int j = 0; j < m; ++j) {
+        sel[j] = win[pick[j]];
+        lam_b[j] = lamw[sel[j]];
+      }
+      PASE_TRY(upload_ints(h, sel, b.idx));
+      PASE_TRY(launch_gather_cols(h, NH, m, b.Cw, b.kk, b.idx, w.CH, m));
+      PASE_TRY(launch_gather_cols(h, m, m, b.Cw + NH * b.kk, b.kk, b.idx, w.CW, m));
+      PASE_CUDA(cudaMemcpyAsync(w.lam, lam_b.data(), sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+      PASE_TRY(step_prolongate(h, w.W, w.CH, w.CW, w.U));
+      // convergence of the owned pairs
+      PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+      PASE_TRY(sync_small(h, w.relres, m, nullptr, 0));
+      worst = 0.0;
+      for (int j = 0; j < kb; ++j) worst = std::max(worst, w.h_small[j]);
+      if (!(worst == worst)) {
+        rc = fail(PASE_ERR_NAN, "pase_solve_batches: NaN in the eigen-residual");
+        break;
+      }
+      if (h->opt.verbose)
+        fprintf(stderr, "[pase] batch at %d (%d pairs) iter %d  max relres %.3e\n", m0, kb, it, worst);
+      conv = worst <= tol;
+      if (!conv) {  // (f) linear solve A_h u = lambda M_h u-hat from u-hat
+        PASE_TRY(step_linear_solve(h, w.U, w.W));
+        PASE_CUDA(cudaMemcpyAsync(w.U, w.W, sizeof(double) * N * m, cudaMemcpyDeviceToDevice, h->stream));
+      }
+    }
+    if (rc != PASE_OK) break;
+    PASE_TRY(launch_copy_cols(h, N, kb, w.U, m, (double*)dU + m0, nev));
+    for (int j = 0; j < kb; ++j) lam_out[m0 + j] = lam_b[j];
+    worst_all = std::max(worst_all, worst);
+    if (conv) conv_all += kb;
+    else if (rc == PASE_OK) rc = PASE_ERR_NOT_CONVERGED;
+  }
+  PASE_CUDA(cudaMemcpyAsync(dl, lam_out.data(), sizeof(double) * nev, cudaMemcpyHostToDevice, h->stream));
+  PASE_TRY(sg.finish());
+  st.converged = conv_all;
+  st.max_residual = worst_all;
+  st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  st.kernel_launches = (int)(h->launches - launches0);
+  if (stp) *stp = st;
+  if (rc == PASE_ERR_NOT_CONVERGED) set_error("a batch reached the maximum number of iterations");
   PASE_TRY(tc_check(h));
   return rc;
 }

@@ -199,6 +199,17 @@ struct pase_ctx {
   pase::Smoother* sm = nullptr;  // learned smoother (pase_set_grid)
   bool sm_suspend = false;       // Jacobi while the trainer generates samples
   double aug_tol_now = 0;    // current inner tolerance
+  // batch scheme (pase_solve_batches): dense coarse pencil and augmented-pencil buffers,
+  // allocated on first use (sizes fixed by the first call's nev and m)
+  struct BatchBufs {
+    int nev = 0, m = 0, top = 0, n = 0, kk = 0, nw = 0;
+    double *AHd = nullptr, *MHd = nullptr, *CHc = nullptr, *lamH = nullptr;  // coarse pencil, pairs
+    double *Ad = nullptr, *Bd = nullptr, *Cw = nullptr, *lamw = nullptr;    // augmented pencil, pairs
+    double *Cc = nullptr, *Rm = nullptr, *Rt = nullptr, *Rt2 = nullptr, *S = nullptr, *comp = nullptr;
+    double* eig = nullptr;  // small eigensolver workspace
+    size_t eig_doubles = 0;
+    int* idx = nullptr;
+  } bb;
   std::vector<void*> allocations;
 };
 
@@ -279,6 +290,13 @@ int ts_gemm(pase_ctx* h, int64_t n, int k1, int k2, double alpha, const double* 
             const double* C, int ldc, double beta, double* Y, int ldy);  // Y = a X C + b Y
 template <typename T>
 int dense_mm(pase_ctx* h, int64_t n, int m, const T* Ainv, const T* B, T* X);  // X = Ainv B
+
+// dense helpers of the batch scheme: CSR rows into a dense block, transpose, column gather
+int launch_csr_to_dense(pase_ctx* h, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
+                        const double* val, double* D, int64_t ld);
+int launch_transpose(pase_ctx* h, int64_t rows, int64_t cols, const double* A, int64_t lda, double* B, int64_t ldb);
+int launch_gather_cols(pase_ctx* h, int64_t n, int k, const double* src, int64_t lds, const int* idx, double* dst,
+                       int64_t ldd);
 
 // small dense matrices on one CTA
 int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,

@@ -71,7 +71,7 @@ class PaseError(RuntimeError):
 
 _lib = None
 
-EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve",
+EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_solve_batches",
             "pase_solve_batched", "pase_profile_kernel", "pase_profile_read",
             "pase_residual", "pase_linear_solve", "pase_project", "pase_augmented_eig",
             "pase_prolongate", "pase_iterate", "pase_spmm_am", "pase_smooth", "pase_smoother_form",
@@ -100,6 +100,7 @@ def load_library(path=LIB_PATH):
                              ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR), ctypes.POINTER(PaseCSR)]
     L.pase_reserve.argtypes = [vp, i32]
     L.pase_solve.argtypes = [vp, i32, dbl, i32, vp, vp, vp, ctypes.POINTER(PaseStats)]
+    L.pase_solve_batches.argtypes = [vp, i32, i32, i32, dbl, vp, vp, ctypes.POINTER(PaseStats)]
     L.pase_solve_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
                                      ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), ctypes.POINTER(PaseStats)]
@@ -132,7 +133,7 @@ def load_library(path=LIB_PATH):
     L.pase_status_string.restype = ctypes.c_char_p
     L.pase_last_error.argtypes = []
     L.pase_last_error.restype = ctypes.c_char_p
-    for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_solve_batched",
+    for name in ["pase_create", "pase_setup", "pase_reserve", "pase_solve", "pase_solve_batched", "pase_solve_batches",
                  "pase_residual",
                  "pase_linear_solve", "pase_project", "pase_augmented_eig", "pase_prolongate",
                  "pase_iterate", "pase_spmm_am", "pase_smooth", "pase_smoother_form", "pase_residual_noalloc",
@@ -229,6 +230,15 @@ def pase_solve(h, nev, tol, m, U0, lam, U):
     st = PaseStats()
     rc = _check(load_library().pase_solve(h, nev, tol, m, _ptr(U0), _ptr(lam), _ptr(U),
                                           ctypes.byref(st)), allow=(PASE_ERR_NOT_CONVERGED,))
+    return rc, st.as_dict()
+
+
+def pase_solve_batches(h, nev, k, m, tol, lam, U):
+    """The batch scheme of §5 (Alg. 7): first nev pairs in batches of about k, block m.
+    Returns (status, stats dict); status may be PASE_ERR_NOT_CONVERGED."""
+    st = PaseStats()
+    rc = _check(load_library().pase_solve_batches(h, nev, k, m, tol, _ptr(lam), _ptr(U), ctypes.byref(st)),
+                allow=(PASE_ERR_NOT_CONVERGED,))
     return rc, st.as_dict()
 
 
