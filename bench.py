@@ -10,10 +10,15 @@ A step is one augmented subspace iteration (residual, step (a) linear solve, ste
 projection, step (c) augmented eigensolve, step (d) prolongation) on that workload.
 value = DOF*nev per second (N_h * nev / step time), summed over ranks.
 
-Extra keys: the whole solve to relative residual 1e-8 in FP64 and in the mixed form
-(FP32 V-cycle inside FP64 refinement) with the speedup per converged eigenpair, the
-roofline of the hot sparse kernel, the oracle timed on the host cores (cpu_baseline),
-and an end-to-end number through the C ABI with host buffers.
+Extra keys: `converged` - DOF*nev/s to relative residual 1e-8 (whole solves, FP64 and the
+mixed form, FP32 V-cycle inside FP64 refinement) with the speedup per converged eigenpair;
+the roofline of the hot sparse kernel; per-kernel rooflines (`kernels`, with the measured
+FP64 FMA rate); `cfg1_latency` (2D 128^2, nev 10: per-iteration latency and launches);
+`variants` (step-(c) congruences PRECOND-A/-B/-B-A, Alg. 3's two-solve form, CG(40) and
+MG-preconditioned CG step (a)); `tensor_operator` (the section-6.3 operator on the bench
+mesh); `batch_scheme` (Alg. 7); the batch of 64 independent problems; the learned smoother;
+the oracle timed on the host cores (cpu_baseline); an end-to-end number through the C ABI
+with host buffers.
 
 --impl reference times the FP64 CPU oracle (one oracle iteration per step) instead.
 """
@@ -366,6 +371,112 @@ def run_learned3d(args, P, pin, torch, np):
             "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
 
 
+def _solve_once(P, torch, stream, pb, nev, m, U0, tol=1e-8, **opts):
+    """One pase_solve on a fresh handle with the given options; device-event timed."""
+    opt = P.pase_default_options()
+    opt.coarse_level = pb.coarse_level
+    for k, v in opts.items():
+        setattr(opt, k, v)
+    h = P.pase_create(opt, stream.cuda_stream)
+    try:
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        U = torch.empty_like(U0)
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st = P.pase_solve(h, nev, tol, m, U0, lam, U)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        out = {"status": rc, "iterations": st["iterations"], "seconds": sec, "max_relres": st["max_residual"],
+               "dof_nev_per_s": pb.N * nev / sec, "ms_per_iteration": 1e3 * sec / max(1, st["iterations"]),
+               "phase_ms": st["phase_ms"], "aug_iterations": st["aug_iterations"],
+               "launches_per_iteration": st["kernel_launches"] / max(1, st["iterations"])}
+        return out, lam[:nev].cpu().numpy()
+    finally:
+        P.pase_destroy(h)
+
+
+def run_cfg1(P, pin, torch, np, stream):
+    """Configuration 1 (2D Q1 128^2, coarse 16^2, nev 10): L2-resident, so the numbers are
+    latency and launch counts per iteration, FP64 and mixed (one untimed solve first)."""
+    pb = pin.build_problem(2, 128, 16, mg_min=4)
+    nev = 10
+    m = pin.guard_columns(nev)
+    U0 = torch.from_numpy(pin.start_vectors(0, pb.N, m)).cuda()
+    out = {"workload": "laplace2d_q1_128_coarse16_nev10", "N_h": pb.N, "block": m}
+    for name, prec in (("fp64", P.PASE_PREC_FP64), ("mixed", P.PASE_PREC_MIXED)):
+        _solve_once(P, torch, stream, pb, nev, m, U0, precision=prec)
+        out[name], _ = _solve_once(P, torch, stream, pb, nev, m, U0, precision=prec)
+    return out
+
+
+def run_variants(P, torch, stream, pb, m, U0):
+    """The solver variants of the bench workload (FP64 solves to 1e-8): the step-(c)
+    congruences of §4 (plain, PRECOND-A, -B, -B-A; the paper's Fig. 1 question), Alg. 3's
+    two-solve form, and step (a) as plain CG with 40 steps (the numerical section's linear
+    solver) or as 3 V-cycle-preconditioned CG steps, against 2 V-cycles."""
+    rows = {}
+    for name, kw in (("plain", dict(aug_transform=P.PASE_AUG_PLAIN)),
+                     ("precond_a", dict(aug_transform=P.PASE_AUG_PRECOND_A)),
+                     ("precond_b", dict(aug_transform=P.PASE_AUG_PRECOND_B)),
+                     ("precond_ba", dict(aug_transform=P.PASE_AUG_PRECOND_BA)),
+                     ("post_solve", dict(post_solve=1)),
+                     ("cg40", dict(linear_solver=P.PASE_SOLVER_CG, inner_steps=40)),
+                     ("mgcg3", dict(linear_solver=P.PASE_SOLVER_MGCG, inner_steps=3))):
+        try:
+            rows[name], _ = _solve_once(P, torch, stream, pb, NEV, m, U0, **kw)
+        except Exception as exc:  # pragma: no cover
+            rows[name] = {"error": str(exc)}
+    return rows
+
+
+def run_tensor(P, pin, torch, np, stream):
+    """The operator of the numerical section's batch-scheme test, -div(T grad u) + phi u
+    (T = I + (x-1/2)(x-1/2)^T, phi = exp(prod (x_k - 1/2))), on the bench mesh (3D Q1 128^3,
+    coarse 16^3, nev 50): whole solves to 1e-8, FP64 and mixed."""
+    t0 = time.perf_counter()
+    pb = pin.build_problem(D, NFINE, NCOARSE, mg_min=4, operator="tensor")
+    build_s = time.perf_counter() - t0
+    m = pin.guard_columns(NEV)
+    U0 = torch.from_numpy(pin.start_vectors(SEED, pb.N, m)).cuda()
+    out = {"workload": "tensor_potential3d_q1_128_coarse16_nev50", "assembly_seconds_host": build_s}
+    lams = {}
+    for name, prec in (("fp64", P.PASE_PREC_FP64), ("mixed", P.PASE_PREC_MIXED)):
+        out[name], lams[name] = _solve_once(P, torch, stream, pb, NEV, m, U0, precision=prec)
+    out["mixed_speedup_per_converged_pair"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["mixed_vs_fp64_max_rel_eig_diff"] = float(np.max(np.abs(lams["mixed"] - lams["fp64"]) / lams["fp64"]))
+    return out
+
+
+def run_batch_scheme(P, pin, torch, np, stream):
+    """The batch scheme of §5 (Alg. 7), FP64, on the section-6.3 operator in 2D (64^2 mesh,
+    coarse 32^2): the first 24 pairs in batches of 8 (block 16), against one pase_solve of
+    all 24 (block 32)."""
+    pb = pin.build_problem(2, 64, 32, mg_min=4, operator="tensor")
+    nev, k, m = 24, 8, 16
+    opt = P.pase_default_options()
+    opt.coarse_level = pb.coarse_level
+    h = P.pase_create(opt, stream.cuda_stream)
+    out = {"workload": "tensor_potential2d_q1_64_coarse32_nev24", "k": k, "block": m}
+    try:
+        P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
+        lam = np.empty(nev)
+        U = np.empty((pb.N, nev))
+        t0 = time.perf_counter()
+        rc, st = P.pase_solve_batches(h, nev, k, m, 1e-8, lam, U)
+        sec = time.perf_counter() - t0
+        out["batches"] = {"status": rc, "seconds": sec, "iterations": st["iterations"],
+                          "max_relres": st["max_residual"], "converged": st["converged"]}
+    finally:
+        P.pase_destroy(h)
+    U0 = torch.from_numpy(pin.start_vectors(0, pb.N, 32)).cuda()
+    out["one_block"], lam1 = _solve_once(P, torch, stream, pb, nev, 32, U0)
+    out["max_rel_eig_diff"] = float(np.max(np.abs(lam - lam1) / lam1))
+    return out
+
+
 def run_profile_smoother(args):
     """The learned smoother's inference pass (tensor-core convolutions) on a 2D lognormal
     field at --size (8 columns, Jacobi-equivalent weights plus noise), three applications,
@@ -577,10 +688,20 @@ def run_ours(args):
         return d
 
     hk = make(P.PASE_PREC_MIXED)
+    # FP64 FMA rate of this GPU (the measured ceiling of the FP64-pipe-bound kernels)
+    try:
+        fma_ms = P.pase_time_kernel(hk, "fma_fp64", m, 5)
+        kernels["fma_fp64"] = {"ms": fma_ms, "tflops": P.FMA_FP64_FLOPS / (fma_ms * 1e-3) / 1e12,
+                               "what": "8 independent FP64 FMA chains per thread, 1216 x 256 threads"}
+    except Exception as exc:  # pragma: no cover
+        kernels["fma_fp64"] = {"error": str(exc)}
+    n1 = NFINE - 1
+    st_vbytes = (n1 + 2) * ((n1 + 3) // 4) * ((n1 + 15) // 16) * 28 * 64 * 4  # step-major coefficients
     for name, flops, nbytes, bound in (
             ("spmm_am_fp64", 4.0 * nnz * m, nnz * 20 + 8 * (N + 1) + 3 * N * m * 8, "alu"),
             ("jacobi_fp64", 2.0 * nnz * m + 3.0 * N * m, nnz * 12 + 16 * N + 3 * N * m * 8, "alu"),
-            ("jacobi_fp32", 2.0 * nnz * m + 3.0 * N * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
+            ("jacobi_fp32", 2.0 * nnz * m + 3.0 * N * m, st_vbytes + 3 * N * m * 4, "hbm"),
+            ("jacobi_fp32_csr", 2.0 * nnz * m + 3.0 * N * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
             ("gram_fp64", 1.0 * N * m * (m + 4), 2 * N * m * 8, "alu"),
             ("prolong_fp64", 2.0 * N * m * m, 2 * N * m * 8, "alu"),
             ("prolong_split", 2.0 * N * m * m, 2 * N * m * 8, "hbm"),
@@ -588,8 +709,14 @@ def run_ours(args):
         try:
             ms_k = P.pase_time_kernel(hk, name, m, 10)
             kernels[name] = kinfo(name, ms_k, flops, nbytes, bound)
+            if bound == "alu" and "tflops" in kernels.get("fma_fp64", {}):
+                kernels[name]["frac_of_measured_fma"] = kernels[name]["tflops"] / kernels["fma_fp64"]["tflops"]
         except Exception as exc:  # pragma: no cover
             kernels[name] = {"error": str(exc)}
+    kernels["jacobi_fp32"]["kernel"] = "k_stencil<3, JACOBI> (structured grid, bulk-copy staged planes)"
+    kernels["jacobi_fp32"]["bytes_model"] = ("step-major coefficients (28 per row, tile-padded) + X, b, y "
+                                             "of [N][m] FP32 (no column indices)")
+    kernels["jacobi_fp32_csr"]["kernel"] = "k_csr<float, JACOBI> (the CSR kernel, same sweep)"
     for name, nn in (("sygv", m), ("sygv3", 3 * m)):
         try:
             kernels[name] = {"ms": P.pase_time_kernel(hk, name, m, 5), "n": nn, "k": m, "bound": "latency"}
@@ -624,6 +751,27 @@ def run_ours(args):
             solves["mixed_speedup_per_converged_pair"] = solves["fp64"]["seconds"] / solves["mixed"]["seconds"]
             solves["mixed_vs_fp64_max_rel_eig_diff"] = float(np.max(np.abs(lam_mixed - lam_fp64) / lam_fp64))
 
+    if "tflops" in kernels.get("fma_fp64", {}):
+        roofline["peak_measured_fma_tflops"] = kernels["fma_fp64"]["tflops"]
+        roofline["frac_of_measured_fma"] = roofline["achieved"] / kernels["fma_fp64"]["tflops"]
+    converged = None
+    if "fp64" in solves and "mixed" in solves:
+        converged = {"metric": "DOF*nev/s to relative residual 1e-8 (whole pase_solve, 3D Q1 128^3, nev 50)",
+                     "fp64": solves["fp64"]["dof_nev_per_s"], "mixed": solves["mixed"]["dof_nev_per_s"],
+                     "fp64_seconds": solves["fp64"]["seconds"], "mixed_seconds": solves["mixed"]["seconds"],
+                     "fp64_ms_per_iteration": solves["fp64"]["ms_per_iteration"],
+                     "mixed_ms_per_iteration": solves["mixed"]["ms_per_iteration"],
+                     "mixed_speedup_per_converged_pair": solves["mixed_speedup_per_converged_pair"]}
+    extra = {}
+    if rank == 0 and not args.no_solve:
+        for key, fn in (("cfg1_latency", lambda: run_cfg1(P, pin, torch, np, stream)),
+                        ("variants", lambda: run_variants(P, torch, stream, pb, m, U0)),
+                        ("tensor_operator", lambda: run_tensor(P, pin, torch, np, stream)),
+                        ("batch_scheme", lambda: run_batch_scheme(P, pin, torch, np, stream))):
+            try:
+                extra[key] = fn()
+            except Exception as exc:  # pragma: no cover
+                extra[key] = {"error": str(exc)}
     batched = run_batched(args, P, pin, torch, np, barrier) if args.batch > 0 else None
     learned = run_learned(args, P, pin, torch, np) if (args.learned and rank == 0) else None
     learned3d = run_learned3d(args, P, pin, torch, np) if (args.learned and rank == 0) else None
@@ -647,8 +795,9 @@ def run_ours(args):
                            "dense_products": "steps (b) and (d): FP64-accurate error-free digit splitting on "
                                              "the BF16 tensor cores (option split_gemm)"},
                 "roofline": roofline, "spmm_fp64": spmm_live, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "solve": solves, "batched": batched, "learned_smoother": learned,
-                "learned_smoother_3d": learned3d}
+                "clocks": clocks, "converged": converged, "solve": solves, "batched": batched,
+                "learned_smoother": learned, "learned_smoother_3d": learned3d}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -313,6 +313,8 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_PROLONG_SPLIT 7 /* W C over N_h rows on the tensor cores (split digits; m <= 128) */
 #define PASE_KERNEL_GRAM_SPLIT 8    /* both Gram blocks W^T R, W^T W on the tensor cores (split digits) */
 #define PASE_KERNEL_JACOBI_FP32_CSR 9 /* the FP32 sweep in the CSR kernel even on a structured grid  */
+#define PASE_KERNEL_FMA_FP64 10     /* FP64 FMA rate: 1216 x 256 threads, 8 independent chains of
+                                       4096 FMAs each, 2.04e10 flops per launch, no memory traffic */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
 /* Live timing of one kernel while the handle works (pase_solve, pase_iterate, ...): with

@@ -1471,7 +1471,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
   if ((kernel == PASE_KERNEL_JACOBI_FP32 || kernel == PASE_KERNEL_JACOBI_FP32_CSR) && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_JACOBI_FP32_CSR)
+  if (kernel < 0 || kernel > PASE_KERNEL_FMA_FP64)
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
@@ -1517,6 +1517,8 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
       }
       case PASE_KERNEL_GRAM_FP64:
         return ts_gram(h, h->N, m, m, w.W, m, w.R, m, w.GA, m, true);
+      case PASE_KERNEL_FMA_FP64:
+        return launch_fma_fp64(h, w.smallvec);
       case PASE_KERNEL_PROLONG_FP64:
         return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
       case PASE_KERNEL_PROLONG_SPLIT:

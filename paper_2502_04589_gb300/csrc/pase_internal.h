@@ -309,6 +309,9 @@ size_t small_sygv_work_doubles(int n, int k);
 // Cap on the grid of every kernel that writes per-block partial sums (the residual, the
 // CG inner products, the smoother's column sums): partial buffers hold this many blocks.
 constexpr int kReduceBlocksHost = 152 * 8;
+// FP64 FMA-rate launch (pase_time_kernel PASE_KERNEL_FMA_FP64): 2 * 8 * iters * threads * blocks flops
+constexpr int kFmaBlocks = 152 * 8, kFmaThreads = 256, kFmaIters = 4096;
+int launch_fma_fp64(pase_ctx* h, double* out);
 // column-wise residual of a block eigenproblem: R = AX - BX diag(lam), partial norms
 int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const double* BX,
                        int64_t ldin, const double* lam, double* R, int64_t ldr, int* nblk_out);

@@ -310,7 +310,8 @@ def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres,
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
            "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7,
-           "gram_split": 8, "jacobi_fp32_csr": 9}
+           "gram_split": 8, "jacobi_fp32_csr": 9, "fma_fp64": 10}
+FMA_FP64_FLOPS = 2.0 * 8 * 4096 * 256 * 152 * 8  # flops of one fma_fp64 launch
 
 
 def pase_time_kernel(h, kernel, m, reps=10):

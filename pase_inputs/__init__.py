@@ -265,7 +265,7 @@ def q1_matrices_coefficients(d: int, n: int, tensor, potential, quad: int = 3):
         X = (ec[:, None, :] + qpts[None, :, :]) * h                      # [E][Q][d]
         T = tensor(X)
         C = np.concatenate([T.reshape(T.shape[:2] + (d * d,)), potential(X)[:, :, None]], axis=2)
-        K = np.einsum("eqc,qcab->eab", C, G)
+        K = (C.reshape(len(e), -1) @ G.reshape(-1, nb * nb)).reshape(len(e), nb, nb)
         node = ec[:, None, :] + corners[None, :, :]                      # [E][nb][d] in 0..n
         inner = np.all((node >= 1) & (node <= n1), axis=2)
         gidx = np.zeros(node.shape[:2], dtype=np.int64)
