@@ -214,15 +214,18 @@ def run_learned(args, P, pin, torch, np):
     """Configuration 4, 2D: one smoother network trained on the solver's own samples from
     64 seeded lognormal fields (sigma 1, seeds 1000-1063, 256^2 meshes, 20 steps of 8
     pairs each: 10,240 pairs), evaluated on 16 held-out fields (seeds 2000-2015) by the
-    two-V-cycle energy error factor against damped Jacobi, and by a full FP64 solve of
-    the 1024^2 held-out field 2000 (coarse 128^2, nev 32, tol 1e-8) with each smoother."""
+    two-V-cycle energy error factor against damped Jacobi, and by full solves of the
+    1024^2 held-out field 2000 (coarse 128^2, nev 32, tol 1e-8): Jacobi and learned
+    smoothing, FP64 and mixed, 2+2 sweeps and (learned) 1+1."""
     stream = torch.cuda.current_stream().cuda_stream
 
-    def make(n, seed, params=None, smoother=0, m=None):
+    def make(n, seed, params=None, smoother=0, m=None, precision=0, nu=2):
         pb = pin.build_problem(2, n, n // 8, kappa_seed=seed, sigma=1.0, mg_min=4)
         opt = P.pase_default_options()
         opt.coarse_level = pb.coarse_level
         opt.smoother = smoother
+        opt.precision = precision
+        opt.nu1 = opt.nu2 = nu
         h = P.pase_create(opt, stream)
         P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
         P.pase_set_grid(h, 2, n, np.log(pb.kappa))
@@ -263,8 +266,14 @@ def run_learned(args, P, pin, torch, np):
     nev = 32
     m = pin.guard_columns(nev)
     lam_ref = None
-    for name, sm_ in (("jacobi", P.PASE_SMOOTHER_JACOBI), ("learned", P.PASE_SMOOTHER_LEARNED)):
-        pb, h = make(1024, 2000, params if sm_ else None, smoother=sm_, m=m)
+    variants = (("jacobi", P.PASE_SMOOTHER_JACOBI, P.PASE_PREC_FP64, 2),
+                ("learned", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_FP64, 2),
+                ("learned_1+1", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_FP64, 1),
+                ("jacobi_mixed", P.PASE_SMOOTHER_JACOBI, P.PASE_PREC_MIXED, 2),
+                ("learned_mixed", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_MIXED, 2),
+                ("learned_mixed_1+1", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_MIXED, 1))
+    for name, sm_, prec, nu in variants:
+        pb, h = make(1024, 2000, params if sm_ else None, smoother=sm_, m=m, precision=prec, nu=nu)
         U0 = torch.from_numpy(pin.start_vectors(SEED, pb.N, m)).cuda()
         U = torch.empty_like(U0)
         lam = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -288,21 +297,28 @@ def run_learned(args, P, pin, torch, np):
             "vcycle2_energy_factor_learned": float(np.mean(fl)), "vcycle2_energy_factor_jacobi": float(np.mean(fj)),
             "heldout_fields_better": int(sum(a < b for a, b in zip(fl, fj))),
             "solve_1024": solves,
-            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
+            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"],
+            "speedup_per_converged_pair_mixed": solves["jacobi_mixed"]["seconds"] / solves["learned_mixed"]["seconds"],
+            "best_learned_vs_best_jacobi": min(solves["jacobi"]["seconds"], solves["jacobi_mixed"]["seconds"])
+            / min(v["seconds"] for k, v in solves.items() if k.startswith("learned"))}
 
 
 def run_learned3d(args, P, pin, torch, np):
-    """Configuration 4, 3D: one smoother network (27 taps) trained on 16 seeded lognormal
-    fields (sigma 1, seeds 1000-1015) at 32^3, evaluated by the two-V-cycle energy error
-    factor on 4 held-out 64^3 fields (seeds 2000-2003) and by a full FP64 solve of the
-    128^3 held-out field 2000 (coarse 16^3, nev 32, tol 1e-8) with each smoother."""
+    """Configuration 4, 3D: one smoother network (27 taps) trained on the solver's own
+    samples from 64 seeded lognormal fields (sigma 1, seeds 1000-1063) at 32^3 (20 steps
+    of 8 pairs each: 10,240 pairs), evaluated by the two-V-cycle energy error factor on 16
+    held-out 64^3 fields (seeds 2000-2015) and by full solves of the 128^3 held-out field
+    2000 (coarse 16^3, nev 32, tol 1e-8): Jacobi and learned smoothing, FP64 and mixed,
+    2+2 sweeps and (learned) 1+1."""
     stream = torch.cuda.current_stream().cuda_stream
 
-    def make(n, seed, params=None, smoother=0, m=None):
+    def make(n, seed, params=None, smoother=0, m=None, precision=0, nu=2):
         pb = pin.build_problem(3, n, n // 8, kappa_seed=seed, sigma=1.0, mg_min=4)
         opt = P.pase_default_options()
         opt.coarse_level = pb.coarse_level
         opt.smoother = smoother
+        opt.precision = precision
+        opt.nu1 = opt.nu2 = nu
         h = P.pase_create(opt, stream)
         P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
         P.pase_set_grid(h, 3, n, np.log(pb.kappa))
@@ -315,9 +331,9 @@ def run_learned3d(args, P, pin, torch, np):
     t0 = time.perf_counter()
     state = (pin.smoother_init(3, seed=1, noise=0.02),)
     accepted = 0
-    for f in range(16):
+    for f in range(64):
         pb, h = make(32, 1000 + f, state)
-        out = P.pase_train_smoother(h, steps=40, lr=1e-3, seed=f)
+        out = P.pase_train_smoother(h, steps=20, lr=1e-3, seed=f)
         accepted += int(out["accepted"])
         state = P.pase_smoother_state(h, 3)
         P.pase_destroy(h)
@@ -332,7 +348,7 @@ def run_learned3d(args, P, pin, torch, np):
         return float(np.mean(np.sqrt(np.einsum("ij,ij->j", E, pb.A @ E) / np.einsum("ij,ij->j", e0, pb.A @ e0))))
 
     fl, fj = [], []
-    for f in range(4):
+    for f in range(16):
         pb, hl = make(64, 2000 + f, params, smoother=P.PASE_SMOOTHER_LEARNED, m=8)
         fl.append(factor(pb, hl))
         P.pase_destroy(hl)
@@ -343,8 +359,14 @@ def run_learned3d(args, P, pin, torch, np):
     nev = 32
     m = pin.guard_columns(nev)
     lam_ref = None
-    for name, sm_ in (("jacobi", P.PASE_SMOOTHER_JACOBI), ("learned", P.PASE_SMOOTHER_LEARNED)):
-        pb, h = make(128, 2000, params if sm_ else None, smoother=sm_, m=m)
+    variants = (("jacobi", P.PASE_SMOOTHER_JACOBI, P.PASE_PREC_FP64, 2),
+                ("learned", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_FP64, 2),
+                ("learned_1+1", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_FP64, 1),
+                ("jacobi_mixed", P.PASE_SMOOTHER_JACOBI, P.PASE_PREC_MIXED, 2),
+                ("learned_mixed", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_MIXED, 2),
+                ("learned_mixed_1+1", P.PASE_SMOOTHER_LEARNED, P.PASE_PREC_MIXED, 1))
+    for name, sm_, prec, nu in variants:
+        pb, h = make(128, 2000, params if sm_ else None, smoother=sm_, m=m, precision=prec, nu=nu)
         U0 = torch.from_numpy(pin.start_vectors(SEED, pb.N, m)).cuda()
         U = torch.empty_like(U0)
         lam = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -362,13 +384,16 @@ def run_learned3d(args, P, pin, torch, np):
         else:
             solves[name]["max_rel_eig_diff_vs_jacobi"] = float(np.max(np.abs(lamh - lam_ref) / lam_ref))
         P.pase_destroy(h)
-    return {"workload": "3D Q1 lognormal kappa (sigma 1): train 16 fields at 32^3, evaluate 4 held-out fields "
-                        "at 64^3 and a full solve at 128^3 (coarse 16^3), nev 32",
+    return {"workload": "3D Q1 lognormal kappa (sigma 1): train 64 fields at 32^3 (10,240 pairs), evaluate 16 "
+                        "held-out fields at 64^3 and full solves at 128^3 (coarse 16^3), nev 32",
             "train_seconds": train_s, "fields_accepted_by_validation": accepted,
             "vcycle2_energy_factor_learned": float(np.mean(fl)), "vcycle2_energy_factor_jacobi": float(np.mean(fj)),
             "heldout_fields_better": int(sum(a < b for a, b in zip(fl, fj))),
             "solve_128": solves,
-            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"]}
+            "speedup_per_converged_pair": solves["jacobi"]["seconds"] / solves["learned"]["seconds"],
+            "speedup_per_converged_pair_mixed": solves["jacobi_mixed"]["seconds"] / solves["learned_mixed"]["seconds"],
+            "best_learned_vs_best_jacobi": min(solves["jacobi"]["seconds"], solves["jacobi_mixed"]["seconds"])
+            / min(v["seconds"] for k, v in solves.items() if k.startswith("learned"))}
 
 
 def _solve_once(P, torch, stream, pb, nev, m, U0, tol=1e-8, **opts):

@@ -110,6 +110,12 @@ typedef struct {
   int aug_transform;   /* congruence applied to the augmented pencil before step (c), §4:
                           PASE_AUG_PLAIN (default) none, PASE_AUG_PRECOND_A, _PRECOND_B or
                           _PRECOND_BA (see below)                                        */
+  int spmm_df64;       /* 1 (default): the fused fine-level products A_h X, M_h X of step (b)
+                          and of the eigen-residual run in double-float arithmetic (each
+                          FP64 value as a sum of two FP32 numbers, error-free products and
+                          sums on the FP32 pipe; errors a few 2^-48 relative to the row's
+                          sum of |a||x|); a block entry above 2^100 or not finite is then
+                          reported as PASE_ERR_NAN; 0: FP64 CUDA cores                     */
 } pase_options;
 
 /* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the
@@ -315,6 +321,7 @@ int pase_residual_noalloc(int64_t n, int m, const int64_t* rowptr, const int32_t
 #define PASE_KERNEL_JACOBI_FP32_CSR 9 /* the FP32 sweep in the CSR kernel even on a structured grid  */
 #define PASE_KERNEL_FMA_FP64 10     /* FP64 FMA rate: 1216 x 256 threads, 8 independent chains of
                                        4096 FMAs each, 2.04e10 flops per launch, no memory traffic */
+#define PASE_KERNEL_SPMM_AM_DF64 11 /* the fused A_h X, M_h X in double-float (split + product)     */
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch);
 
 /* Live timing of one kernel while the handle works (pase_solve, pase_iterate, ...): with

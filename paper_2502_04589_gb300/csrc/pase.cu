@@ -314,6 +314,12 @@ static int reserve(pase_ctx* h, int m) {
   PASE_TRY(dev_alloc_t(h, &w.smallvec, (size_t)16 * m));
   PASE_TRY(dev_alloc_t(h, &w.status, 8));
   PASE_TRY(dev_alloc_t(h, &w.colexp, 3 * 128));
+  if (h->opt.spmm_df64) {
+    PASE_TRY(dev_alloc_t(h, &w.dfh, nm));
+    PASE_TRY(dev_alloc_t(h, &w.dfl, nm));
+    PASE_TRY(dev_alloc_t(h, &w.df_flag, 1));
+    PASE_CUDA(cudaMemsetAsync(w.df_flag, 0, sizeof(int), h->stream));
+  }
   if (h->opt.aug_transform != PASE_AUG_PLAIN) {
     const size_t hm = (size_t)NH * m;
     PASE_TRY(dev_alloc_t(h, &w.Zt, hm));
@@ -633,12 +639,41 @@ static int step_linear_solve_graphed(pase_ctx* h, const double* U, double* W) {
 }
 
 // Residual R = M U Lambda - A U and relative residuals into w.relres (device).
+// The fused fine-level products A_h X, M_h X (and the eigen-residual) in double-float
+// arithmetic when the handle has the split values (spmm_df64), else in FP64.
+static bool use_df64(const pase_ctx* h) { return h->opt.spmm_df64 && h->A0h && h->w.dfh; }
+static int fine_products(pase_ctx* h, int mode, const double* X, const double* lam, double* Y1, double* Y2,
+                         int* nb) {
+  Work& w = h->w;
+  const int m = w.m;
+  if (use_df64(h)) {
+    PASE_TRY(launch_split_df64(h, h->N * m, X, w.dfh, w.dfl, w.df_flag));
+    return launch_csr_df64(h, mode, m, h->lv[0].A, h->A0h, h->A0l, h->M0h, h->M0l, w.dfh, w.dfl, lam, Y1, Y2,
+                           w.partial, nb);
+  }
+  return launch_csr<double>(h, mode, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, X, nullptr, nullptr, nullptr, lam,
+                            0.0, Y1, Y2, w.partial, nb);
+}
+
+// PASE_ERR_NAN if a double-float split met a value outside 2^+-100 (clears the flag)
+static int df_check(pase_ctx* h) {
+  if (!h->w.df_flag) return PASE_OK;
+  int f = 0;
+  PASE_CUDA(cudaMemcpyAsync(&f, h->w.df_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  PASE_CUDA(cudaStreamSynchronize(h->stream));
+  if (f) {
+    PASE_CUDA(cudaMemsetAsync(h->w.df_flag, 0, sizeof(int), h->stream));
+    return fail(PASE_ERR_NAN, "a block entry above 2^100 (or not finite) met the double-float products; "
+                              "set spmm_df64 = 0 for such data");
+  }
+  return PASE_OK;
+}
+
 static int step_residual(pase_ctx* h, const double* U, const double* lam, double* R) {
   Work& w = h->w;
   const int m = w.m;
   int nb = 0;
-  PASE_TRY(launch_csr<double>(h, CSR_EIGRES, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, U, nullptr, nullptr,
-                              nullptr, lam, 0.0, R, nullptr, w.partial, &nb));
+  PASE_TRY(fine_products(h, CSR_EIGRES, U, lam, R, nullptr, &nb));
   PASE_TRY(launch_reduce_partials(h, nb, 2 * m, w.partial, w.norms));
   PASE_TRY(launch_relres(h, m, w.norms, lam, w.relres));
   return PASE_OK;
@@ -648,8 +683,7 @@ static int step_residual(pase_ctx* h, const double* U, const double* lam, double
 static int step_project(pase_ctx* h, const double* W, double* aH, double* bH, double* GA, double* GM) {
   Work& w = h->w;
   const int m = w.m;
-  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, W, nullptr, nullptr,
-                              nullptr, nullptr, 0.0, w.T1, w.T2, nullptr, nullptr));
+  PASE_TRY(fine_products(h, CSR_MV_AM, W, nullptr, w.T1, w.T2, nullptr));
   PASE_TRY(launch_csr<double>(h, CSR_MV2, m, h->PdT, h->PdT.val, nullptr, w.T1, w.T2, nullptr, nullptr,
                               nullptr, 0.0, aH, bH, nullptr, nullptr));
   if (h->opt.split_gemm && ts_gram2_split_ok(h->N, m, h->num_sms, w))
@@ -1108,6 +1142,7 @@ void pase_default_options(pase_options* o) {
   o->stencil = 1;
   o->post_solve = 0;
   o->aug_transform = PASE_AUG_PLAIN;
+  o->spmm_df64 = 1;
 }
 
 const char* pase_status_string(int code) {
@@ -1253,6 +1288,20 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
     h->M0_val = Mtmp.val;
     h->M0_val32 = Mtmp.val32;
   }
+  if (h->opt.spmm_df64) {  // hi = fl32(v), lo = fl32(v - hi) of the fine pencil's values
+    const int64_t nz = A0.nnz();
+    std::vector<float> hi(std::max<int64_t>(1, nz)), lo(std::max<int64_t>(1, nz));
+    float** dst[4] = {&h->A0h, &h->A0l, &h->M0h, &h->M0l};
+    for (int q = 0; q < 2; ++q) {
+      const std::vector<double>& v = q == 0 ? A0.val : M0.val;
+      for (int64_t k = 0; k < nz; ++k) {
+        hi[k] = (float)v[k];
+        lo[k] = (float)(v[k] - (double)hi[k]);
+      }
+      PASE_TRY(upload_vec(h, hi, dst[2 * q]));
+      PASE_TRY(upload_vec(h, lo, dst[2 * q + 1]));
+    }
+  }
   PASE_TRY(upload_csr(h, Pd, h->Pd, false, false, nullptr));
   PASE_TRY(upload_csr(h, csr_transpose(Pd), h->PdT, false, false, nullptr));
   PASE_TRY(upload_csr(h, AHc, h->AH, false, false, nullptr));
@@ -1303,7 +1352,8 @@ int pase_residual(pase_handle h, int m, const double* U, const double* lambda, d
   PASE_TRY(st.out(relres, m * sizeof(double), &drr));
   PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, dR ? (double*)dR : h->w.R));
   if (drr) PASE_CUDA(cudaMemcpyAsync(drr, h->w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  return st.finish();
+  PASE_TRY(st.finish());
+  return df_check(h);
 }
 
 int pase_linear_solve(pase_handle h, int m, const double* U, const double* lambda, const double* R, double* W) {
@@ -1337,7 +1387,8 @@ int pase_project(pase_handle h, int m, const double* W, double* aH, double* bH, 
   PASE_TRY(st.out(GA, mm, &dga));
   PASE_TRY(st.out(GM, mm, &dgm));
   PASE_TRY(step_project(h, (const double*)dW, (double*)da, (double*)db, (double*)dga, (double*)dgm));
-  return st.finish();
+  PASE_TRY(st.finish());
+  return df_check(h);
 }
 
 int pase_augmented_eig(pase_handle h, int m, const double* aH, const double* bH, const double* GA,
@@ -1409,6 +1460,7 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
   h->aug_nconv = 0;
   PASE_TRY(rc);
   PASE_TRY(st.finish());
+  PASE_TRY(df_check(h));
   return tc_check(h);
 }
 
@@ -1416,10 +1468,9 @@ int pase_spmm_am(pase_handle h, int m, const double* X, double* AX, double* MX) 
   PASE_TRY(check_m(h, m));
   if (!is_device_ptr(X) || !is_device_ptr(AX) || !is_device_ptr(MX))
     return fail(PASE_ERR_INVALID_ARG, "pase_spmm_am: device pointers required");
-  PASE_TRY(launch_csr<double>(h, CSR_MV_AM, m, h->lv[0].A, h->lv[0].A.val, h->M0_val, X, nullptr, nullptr,
-                              nullptr, nullptr, 0.0, AX, MX, nullptr, nullptr));
+  PASE_TRY(fine_products(h, CSR_MV_AM, X, nullptr, AX, MX, nullptr));
   PASE_CUDA(cudaStreamSynchronize(h->stream));
-  return PASE_OK;
+  return df_check(h);
 }
 
 int pase_smooth(pase_handle h, int m, int sweeps, const double* B, double* X) {
@@ -1471,7 +1522,7 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
   const bool mixed = h->opt.precision == PASE_PREC_MIXED;
   if ((kernel == PASE_KERNEL_JACOBI_FP32 || kernel == PASE_KERNEL_JACOBI_FP32_CSR) && !mixed)
     return fail(PASE_ERR_STATE, "pase_time_kernel: the FP32 smoother needs a PASE_PREC_MIXED handle");
-  if (kernel < 0 || kernel > PASE_KERNEL_FMA_FP64)
+  if (kernel < 0 || kernel > PASE_KERNEL_SPMM_AM_DF64)
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: unknown kernel");
   if (kernel == PASE_KERNEL_PROLONG_SPLIT && !ts_gemm_split_ok(m, m, h->w.W, m, h->w.T1, m))
     return fail(PASE_ERR_INVALID_ARG, "pase_time_kernel: the split GEMM takes m <= 128");
@@ -1519,6 +1570,9 @@ int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_
         return ts_gram(h, h->N, m, m, w.W, m, w.R, m, w.GA, m, true);
       case PASE_KERNEL_FMA_FP64:
         return launch_fma_fp64(h, w.smallvec);
+      case PASE_KERNEL_SPMM_AM_DF64:
+        if (!use_df64(h)) return fail(PASE_ERR_STATE, "pase_time_kernel: the handle has spmm_df64 = 0");
+        return fine_products(h, CSR_MV_AM, w.W, nullptr, w.T1, w.T2, nullptr);
       case PASE_KERNEL_PROLONG_FP64:
         return ts_gemm(h, h->N, m, m, 1.0, w.W, m, w.CW, m, 0.0, w.T1, m);
       case PASE_KERNEL_PROLONG_SPLIT:
@@ -1597,7 +1651,8 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
       PASE_CUDA(cudaEventRecord(r0, h->stream));
       PASE_TRY(step_residual(h, w.U, w.lam, w.R));
       PASE_CUDA(cudaEventRecord(r1, h->stream));
-      PASE_TRY(sync_small(h, w.relres, m, nullptr, 0));
+      PASE_TRY(sync_small(h, w.relres, m, w.df_flag, w.df_flag ? 1 : 0));
+      if (w.df_flag && w.h_status[0]) PASE_TRY(df_check(h));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, r0, r1);
       st.phase_ms[4] += ms;
@@ -1774,7 +1829,8 @@ int pase_solve_batches(pase_handle h, int nev, int k, int m, double tol, double*
       PASE_TRY(step_prolongate(h, w.W, w.CH, w.CW, w.U));
       // convergence of the owned pairs
       PASE_TRY(step_residual(h, w.U, w.lam, w.R));
-      PASE_TRY(sync_small(h, w.relres, m, nullptr, 0));
+      PASE_TRY(sync_small(h, w.relres, m, w.df_flag, w.df_flag ? 1 : 0));
+      if (w.df_flag && w.h_status[0]) PASE_TRY(df_check(h));
       worst = 0.0;
       for (int j = 0; j < kb; ++j) worst = std::max(worst, w.h_small[j]);
       if (!(worst == worst)) {

@@ -112,6 +112,8 @@ struct Work {
   double* cgs = nullptr;                                // CG scalars: (r,z) x2, (p,Ap), ratio [4m]
   int* status = nullptr;                                // device status words [8]
   int* colexp = nullptr;                                // split Gram column exponents [3][128]
+  float *dfh = nullptr, *dfl = nullptr;                 // double-float split of a block [N][m]
+  int* df_flag = nullptr;                               // a split value was outside 2^+-100
   // step-(c) congruences (aug_transform): Z, the transformed blocks, coarse CG buffers
   double *Zt = nullptr, *aT = nullptr, *bT = nullptr, *GAT = nullptr, *GMT = nullptr;  // [N_H][m], [m][m]
   double *tr = nullptr, *tz = nullptr, *tp = nullptr, *tq = nullptr, *tsc = nullptr;   // [N_H][m] x4, [4m]
@@ -165,6 +167,7 @@ struct pase_ctx {
   std::vector<pase::Level> lv;
   double* M0_val = nullptr;  // M_h values (pattern of A_h)
   float* M0_val32 = nullptr;
+  float *A0h = nullptr, *A0l = nullptr, *M0h = nullptr, *M0l = nullptr;  // double-float split of A_h, M_h
   pase::DevCSR Pd, PdT;      // direct interpolation V_H -> V_h and its transpose
   pase::DevCSR AH;           // coarse pencil as given: A_H with values, M_H values below
   double* MH_val = nullptr;
@@ -242,6 +245,12 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
                const T* X, const T* X2, const T* B, const T* dinv, const double* lam, double omega,
                T* Y1, T* Y2, double* partial, int* nblocks_out, int64_t ldx = 0,
                int64_t ldy = 0);
+
+// double-float products of the fine level (df64.cu)
+int launch_split_df64(pase_ctx* h, int64_t count, const double* x, float* hi, float* lo, int* flag);
+int launch_csr_df64(pase_ctx* h, int mode, int m, const DevCSR& A, const float* ah, const float* al,
+                    const float* mh, const float* ml, const float* xh, const float* xl, const double* lam,
+                    double* Y1, double* Y2, double* partial, int* nblocks_out);
 
 // structured-grid FP32 kernels (stencil.cu)
 int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv, DevCSR& d);

@@ -617,20 +617,23 @@ int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const do
 }
 
 // ------------------------------------------------------------------ FP64 FMA rate
-// Eight independent FMA chains per thread (no memory traffic): the FP64 arithmetic rate of
-// the part, the peak that the FP64-pipe-bound kernels of the path are measured against.
+// Independent FMA chains (no memory traffic, the loop unrolled so that loop control does
+// not share the issue slots): the FP64 arithmetic rate of the part, the peak that the
+// FP64-pipe-bound kernels of the path are measured against.
 __global__ void __launch_bounds__(256) k_fma_fp64(int iters, double seed, double* out) {
-  double a[8];
+  constexpr int kChains = 8;
+  double a[kChains];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) a[j] = seed * (threadIdx.x + 1 + j);
+  for (int j = 0; j < kChains; ++j) a[j] = seed * (threadIdx.x + 1 + j);
   const double b = 0.999999999, c = 1e-12;
+#pragma unroll 16
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+    for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
   }
   double s = 0.0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) s += a[j];
+  for (int j = 0; j < kChains; ++j) s += a[j];
   if (s == -1.0) out[0] = s;  // never true; keeps the chains alive
 }
 int launch_fma_fp64(pase_ctx* h, double* out) {

@@ -41,7 +41,7 @@ class PaseOptions(ctypes.Structure):
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int)]
+                ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int), ("spmm_df64", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):
@@ -310,7 +310,7 @@ def pase_residual_noalloc(n, m, rowptr, colind, A_val, M_val, U, lam, R, relres,
 
 KERNELS = {"spmm_am_fp64": 0, "jacobi_fp64": 1, "jacobi_fp32": 2, "gram_fp64": 3,
            "prolong_fp64": 4, "sygv": 5, "sygv3": 6, "prolong_split": 7,
-           "gram_split": 8, "jacobi_fp32_csr": 9, "fma_fp64": 10}
+           "gram_split": 8, "jacobi_fp32_csr": 9, "fma_fp64": 10, "spmm_am_df64": 11}
 FMA_FP64_FLOPS = 2.0 * 8 * 4096 * 256 * 152 * 8  # flops of one fma_fp64 launch
 
 

@@ -134,6 +134,52 @@ def test_spmm_am_first_call_of_fresh_processes():
         assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
+@pytest.mark.parametrize("which,m", [("p2d", 8), ("p3d", 40)])
+def test_spmm_df64_matches_fp64_and_definition(which, m, request):
+    """The double-float fused product (default) against the FP64 kernel (spmm_df64 = 0) and
+    the definition, entry by entry: within 2048 u of sum_k |a_ik||x_kj| (the split loses 5
+    of 53 bits per operand, the sums gather a few 2^-48 per term); inputs spread over 2^+-60."""
+    pb = request.getfixturevalue(which)
+    rng = np.random.default_rng(5)
+    X = pin.start_vectors(21, pb.N, m) * np.exp2(rng.integers(-60, 61, size=(pb.N, 1)))
+    out = {}
+    for df in (1, 0):
+        c = Ctx(pb, spmm_df64=df)
+        try:
+            AX = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+            MX = torch.empty_like(AX)
+            P.pase_spmm_am(c.h, m, dev(X), AX, MX)
+            out[df] = (host(AX), host(MX))
+        finally:
+            c.close()
+    u = 2.0 ** -53
+    for q, Mat in ((0, pb.A), (1, pb.M)):
+        scale = abs(Mat) @ np.abs(X)
+        ref = Mat @ X
+        assert np.all(np.abs(out[1][q] - ref) <= 2048 * u * scale)
+        assert np.all(np.abs(out[1][q] - out[0][q]) <= 2048 * u * scale)
+
+
+def test_spmm_df64_reports_out_of_range_entries(p2d):
+    """An entry above 2^100 cannot be split into FP32 pairs: the call reports PASE_ERR_NAN,
+    and the next call on ordinary data works (the flag is cleared)."""
+    pb, m = p2d, 8
+    c = Ctx(pb)
+    try:
+        X = pin.start_vectors(22, pb.N, m)
+        X[17, 3] = 1e40
+        AX = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        MX = torch.empty_like(AX)
+        with pytest.raises(P.PaseError) as e:
+            P.pase_spmm_am(c.h, m, dev(X), AX, MX)
+        assert e.value.code == -5
+        X[17, 3] = 0.5
+        P.pase_spmm_am(c.h, m, dev(X), AX, MX)
+        assert _colrel(host(AX), pb.A @ X) < 1e-13
+    finally:
+        c.close()
+
+
 def test_residual_parity(p3d):
     pb = p3d
     m = 16
