@@ -727,6 +727,9 @@ def run_ours(args):
             ("jacobi_fp64", 2.0 * nnz * m + 3.0 * N * m, nnz * 12 + 16 * N + 3 * N * m * 8, "alu"),
             ("jacobi_fp32", 2.0 * nnz * m + 3.0 * N * m, st_vbytes + 3 * N * m * 4, "hbm"),
             ("jacobi_fp32_csr", 2.0 * nnz * m + 3.0 * N * m, nnz * 8 + 12 * N + 3 * N * m * 4, "hbm"),
+            # split of X (read 8, write 8 per entry), then index + 4 FP32 value streams, the split
+            # X (8 per entry) and two FP64 outputs
+            ("spmm_am_df64", 4.0 * nnz * m, nnz * 20 + 8 * (N + 1) + 2 * N * m * 8 + 3 * N * m * 8, "hbm"),
             ("gram_fp64", 1.0 * N * m * (m + 4), 2 * N * m * 8, "alu"),
             ("prolong_fp64", 2.0 * N * m * m, 2 * N * m * 8, "alu"),
             ("prolong_split", 2.0 * N * m * m, 2 * N * m * 8, "hbm"),
@@ -734,14 +737,15 @@ def run_ours(args):
         try:
             ms_k = P.pase_time_kernel(hk, name, m, 10)
             kernels[name] = kinfo(name, ms_k, flops, nbytes, bound)
-            if bound == "alu" and "tflops" in kernels.get("fma_fp64", {}):
-                kernels[name]["frac_of_measured_fma"] = kernels[name]["tflops"] / kernels["fma_fp64"]["tflops"]
         except Exception as exc:  # pragma: no cover
             kernels[name] = {"error": str(exc)}
     kernels["jacobi_fp32"]["kernel"] = "k_stencil<3, JACOBI> (structured grid, bulk-copy staged planes)"
     kernels["jacobi_fp32"]["bytes_model"] = ("step-major coefficients (28 per row, tile-padded) + X, b, y "
                                              "of [N][m] FP32 (no column indices)")
     kernels["jacobi_fp32_csr"]["kernel"] = "k_csr<float, JACOBI> (the CSR kernel, same sweep)"
+    kernels["spmm_am_df64"]["kernel"] = ("k_split_df64 + k_csr_df64<MV_AM> (fused A_h X, M_h X in double-float "
+                                         "on the FP32 pipe; issue-bound)")
+    kernels["spmm_am_df64"]["speedup_vs_fp64"] = kernels["spmm_am_fp64"]["ms"] / kernels["spmm_am_df64"]["ms"]
     for name, nn in (("sygv", m), ("sygv3", 3 * m)):
         try:
             kernels[name] = {"ms": P.pase_time_kernel(hk, name, m, 5), "n": nn, "k": m, "bound": "latency"}
@@ -777,8 +781,9 @@ def run_ours(args):
             solves["mixed_vs_fp64_max_rel_eig_diff"] = float(np.max(np.abs(lam_mixed - lam_fp64) / lam_fp64))
 
     if "tflops" in kernels.get("fma_fp64", {}):
-        roofline["peak_measured_fma_tflops"] = kernels["fma_fp64"]["tflops"]
-        roofline["frac_of_measured_fma"] = roofline["achieved"] / kernels["fma_fp64"]["tflops"]
+        # the microbenchmark stays below what the FP64-pipe-bound kernels reach, so the
+        # nominal rate remains the peak; the measured rate is reported beside it
+        roofline["fma_microbenchmark_tflops"] = kernels["fma_fp64"]["tflops"]
     converged = None
     if "fp64" in solves and "mixed" in solves:
         converged = {"metric": "DOF*nev/s to relative residual 1e-8 (whole pase_solve, 3D Q1 128^3, nev 50)",
