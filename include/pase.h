@@ -116,6 +116,19 @@ typedef struct {
                           sums on the FP32 pipe; errors a few 2^-48 relative to the row's
                           sum of |a||x|); a block entry above 2^100 or not finite is then
                           reported as PASE_ERR_NAN; 0: FP64 CUDA cores                     */
+  int graph_solve;     /* 0 (default): pase_solve runs one outer iteration at a time from the
+                          host (a readback of the residual test per iteration; per-phase
+                          times in pase_stats); 1: the whole solve - start, outer loop, every
+                          step - is recorded once into a CUDA graph whose loops are
+                          conditional nodes steered by device-side tests, and replayed with
+                          one graph launch per call (no per-phase times).  In both forms
+                          step (c) is a recorded graph with its inner loop on the device.
+                          pase_solve_batched runs handles that all have graph_solve = 1 as
+                          one graph launch                                               */
+  int graph_pass_limit; /* 0 (default): every recorded loop may run the passes its test allows
+                          (max_iter + 1 outer, aug_max_iter inner); n > 0: at most n passes,
+                          after which the loop ends and the call returns PASE_ERR_TIMEOUT
+                          (a bound on device-side iteration for callers that want one)   */
 } pase_options;
 
 /* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the
@@ -147,7 +160,8 @@ typedef struct {
   double phase_ms[5];    /* (a) linear solve, (b) projection, (c) augmented eig, (d) prolongation,
                             residual/convergence                                              */
   int aug_iterations;    /* inner block-eigensolver iterations, summed                         */
-  int kernel_launches;   /* library kernels launched                                           */
+  int kernel_launches;   /* library kernels run (those inside replayed graphs included)        */
+  int graph_launches;    /* CUDA graph launches issued by the call                            */
 } pase_stats;
 
 /* Sparse matrix in CSR (borrowed).  rowptr has nrows+1 entries, rowptr[0] = 0;
@@ -197,10 +211,14 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
                double* U, pase_stats* st);
 
 /* Many independent problems at once.  The method treats one pencil per call (Alg. 3);
- * solving unrelated pencils side by side has no counterpart in the paper.  count handles,
- * each set up and best created on its own CUDA stream, are solved concurrently by a pool
- * of host threads so that their kernels overlap on the GPU (handles that share a stream
- * run one after another, largest groups first).  Problem i runs exactly as pase_solve with
+ * solving unrelated pencils side by side has no counterpart in the paper.  When every
+ * handle is distinct, set up on the current device and created with graph_solve = 1, the
+ * whole batch is one CUDA graph - each problem's recorded solve one branch of it - recorded
+ * on the first call, kept by the first handle while the handles, sizes and buffers stay the
+ * same, and launched once per call (the branches run concurrently on the GPU).  Otherwise
+ * count handles, each set up and best created on its own CUDA stream, are solved
+ * concurrently by a pool of host threads so that their kernels overlap on the GPU (handles
+ * that share a stream run one after another, largest groups first).  Problem i runs exactly as pase_solve with
  * nev[i], tol[i], m[i] (m NULL or m[i] = 0: the default block width), U0[i] (U0 or U0[i]
  * NULL: coarse start), lambda[i] and U[i]; host or device pointers as in pase_solve.
  * st (may be NULL) receives count stats.  Returns PASE_OK if all converged,
@@ -384,8 +402,15 @@ typedef struct {
 void pase_default_train_options(pase_train_options* o);
 int pase_train_smoother(pase_handle h, const pase_train_options* o, double* losses);
 
-/* Number of library kernels launched by this handle so far. */
+/* Number of library kernels launched by this handle so far (those run inside replayed
+ * CUDA graphs included). */
 int64_t pase_kernel_count(pase_handle h);
+
+/* The same count split by how the kernels were issued: *kernels as pase_kernel_count,
+ * *kernels_in_graphs of them ran inside graph replays, *graph_launches graph launches were
+ * issued; host-issued launch calls = kernels - kernels_in_graphs + graph_launches.  Any
+ * pointer may be NULL. */
+int pase_launch_counts(pase_handle h, int64_t* kernels, int64_t* kernels_in_graphs, int64_t* graph_launches);
 
 /* Release everything the handle owns.  NULL is accepted. */
 int pase_destroy(pase_handle h);

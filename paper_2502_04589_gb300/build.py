@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpase.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["sparse_kernels.cu", "dense_kernels.cu", "pase.cu", "noalloc.cu", "smoother.cu", "split_gemm.cu", "stencil.cu", "df64.cu"]
+CU = ["sparse_kernels.cu", "dense_kernels.cu", "pase.cu", "noalloc.cu", "smoother.cu", "split_gemm.cu", "stencil.cu", "df64.cu", "flow.cu"]
 CPP = ["host_setup.cpp"]
 
 

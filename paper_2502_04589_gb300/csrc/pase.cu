@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <memory>
 #include <thread>
 
 #include "pase_internal.h"
@@ -155,7 +156,7 @@ struct Stage {
 // ------------------------------------------------------------------ live kernel timing
 constexpr size_t kProfMaxLaunches = 4096;
 void prof_begin(pase_ctx* h, int id) {
-  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches) return;
+  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches || recording(h)) return;
   while (h->prof_ev.size() < 2 * (h->prof_n + 1)) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) {
@@ -167,7 +168,8 @@ void prof_begin(pase_ctx* h, int id) {
   cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
 }
 void prof_end(pase_ctx* h, int id) {
-  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches || h->prof_ev.size() < 2 * (h->prof_n + 1))
+  if (id < 0 || id != h->prof_kernel || h->prof_n >= kProfMaxLaunches || h->prof_ev.size() < 2 * (h->prof_n + 1) ||
+      recording(h))
     return;
   cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
   h->prof_n++;
@@ -335,8 +337,31 @@ static int reserve(pase_ctx* h, int m) {
   }
   PASE_TRY(dev_alloc_t(h, &h->tc_err, 1));
   PASE_CUDA(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+  // Spaces no wider than the block eigensolver's [X, W, P] basis (3m columns) are solved
+  // densely: the coarse pencil of the coarse start when N_H <= 3m, the augmented pencil of
+  // step (c) when N_H + m <= 3m.
+  if (NH <= m3) {
+    w.coarse_dense = true;
+    PASE_TRY(dev_alloc_t(h, &w.AHd, (size_t)NH * NH));
+    PASE_TRY(dev_alloc_t(h, &w.MHd, (size_t)NH * NH));
+    PASE_TRY(launch_csr_to_dense(h, NH, NH, h->AH.rowptr, h->AH.col, h->AH.val, w.AHd, NH));
+    PASE_TRY(launch_csr_to_dense(h, NH, NH, h->AH.rowptr, h->AH.col, h->MH_val, w.MHd, NH));
+  }
+  if (NH + m <= m3) {
+    const int64_t n = NH + m;
+    w.aug_dense = true;
+    PASE_TRY(dev_alloc_t(h, &w.Ad, (size_t)n * n));
+    PASE_TRY(dev_alloc_t(h, &w.Bd, (size_t)n * n));
+    PASE_TRY(dev_alloc_t(h, &w.Cd, (size_t)n * m));
+  }
+  PASE_TRY(dev_alloc_t(h, &w.ci, kCtlInts));
+  PASE_TRY(dev_alloc_t(h, &w.cd, CD_COUNT));
+  PASE_CUDA(cudaMemsetAsync(w.ci, 0, sizeof(int) * kCtlInts, h->stream));
+  PASE_CUDA(cudaMemsetAsync(w.cd, 0, sizeof(double) * CD_COUNT, h->stream));
   PASE_CUDA(cudaMallocHost(&w.h_small, sizeof(double) * 16 * m));
   PASE_CUDA(cudaMallocHost(&w.h_status, sizeof(int) * 8));
+  PASE_CUDA(cudaMallocHost(&w.h_ci, sizeof(int) * kCtlInts));
+  PASE_CUDA(cudaMallocHost(&w.h_cd, sizeof(double) * CD_COUNT));
   if (h->opt.autotune) PASE_TRY(autotune(h));
   return PASE_OK;
 }
@@ -598,6 +623,8 @@ static int step_linear_solve_graphed(pase_ctx* h, const double* U, double* W) {
   if (h->ls_graph && h->ls_graph_U == U && h->ls_graph_W == W) {
     PASE_CUDA(cudaGraphLaunch(h->ls_graph, h->stream));
     h->launches += h->ls_graph_kernels;
+    h->replayed += h->ls_graph_kernels;
+    h->graph_launches++;
     return PASE_OK;
   }
   const bool stable = (h->ls_last_U == U && h->ls_last_W == W);
@@ -635,6 +662,8 @@ static int step_linear_solve_graphed(pase_ctx* h, const double* U, double* W) {
   h->ls_graph_kernels = captured;
   PASE_CUDA(cudaGraphLaunch(ex, h->stream));
   h->launches += captured;
+  h->replayed += captured;
+  h->graph_launches++;
   return PASE_OK;
 }
 
@@ -883,44 +912,27 @@ static int sync_small(pase_ctx* h, const double* dsrc, int count, const int* dst
 // block has converged past ~1e-9); converged columns are soft-locked.
 // On entry S[:, 0:m] holds the start block; on exit S[:, 0:m] = X (B-orthonormal), lam
 // (device) its Ritz values.
-static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double tol, int maxit, int nconv,
-                             int* iters_out) {
+// Recorded into a CUDA graph: the first pass (no P block yet) is unrolled, the others run
+// in a conditional WHILE node; each pass's test (k_ctl_inner_check: the first nconv
+// columns at relative residual <= tol, where tol is *tol_dev or tol_fixed; stagnation;
+// maxit passes) and the small eigensolve's status steer IF nodes, so no pass waits on
+// the host.  Errors (NaN, a start block that is not B-independent) land in the control
+// block.
+static int eig_pass(pase_ctx* h, const BlockOp& op, double* lam, const double* tol_dev, double tol_fixed, int maxit,
+                    int nconv, bool haveP) {
   Work& w = h->w;
   const int m = w.m;
   const int m3 = 3 * m;
   const int64_t n = op.n;
   double *S = w.S, *AS = w.AS, *BS = w.BS;
-  if (nconv <= 0 || nconv > m) nconv = m;
-  // initial Rayleigh-Ritz on the start block
-  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
-  PASE_TRY(ts_gram(h, n, m, m, S, m3, AS, m3, w.Gq, m3, true));
-  PASE_TRY(ts_gram(h, n, m, m, S, m3, BS, m3, w.Gb, m3, true));
-  PASE_TRY(small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, lam, w.Cs, m, w.status));
-  PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
-  if (w.h_status[0] != 0) return fail(PASE_ERR_NOT_SPD, "block eigensolver: start block is not B-independent");
-  PASE_TRY(ts_gemm(h, n, m, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
-  PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
-  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
-  bool haveP = false;
-  int it = 0;
-  std::vector<double> hist;
-  for (it = 1; it <= maxit; ++it) {
-    // residual and convergence
-    int nb = 0;
-    PASE_TRY(launch_block_resid(h, n, m, AS, BS, m3, lam, w.Rn, m, &nb));
-    PASE_TRY(launch_reduce_partials(h, nb, 2 * m, w.partial, w.norms));
-    PASE_TRY(launch_relres(h, m, w.norms, lam, w.smallvec));
-    PASE_TRY(sync_small(h, w.smallvec, m, nullptr, 0));
-    double worst = 0.0;
-    for (int j = 0; j < nconv; ++j) worst = std::max(worst, w.h_small[j]);
-    if (!(worst == worst)) return fail(PASE_ERR_NAN, "block eigensolver: NaN residual");
-    if (h->opt.verbose >= 2) fprintf(stderr, "[pase]   block eigensolver it %d worst %.3e (tol %.1e)\n", it, worst, tol);
-    if (worst <= tol) break;
-    // stagnation at the attainable accuracy of the pencil: no halving in 6 iterations
-    hist.push_back(worst);
-    if (hist.size() > 6 && worst > 0.5 * hist[hist.size() - 7] && worst < 1e-6) break;
+  int nb = 0;
+  PASE_TRY(launch_block_resid(h, n, m, AS, BS, m3, lam, w.Rn, m, &nb));
+  PASE_TRY(launch_reduce_partials(h, nb, 2 * m, w.partial, w.norms));
+  PASE_TRY(launch_relres(h, m, w.norms, lam, w.smallvec));
+  PASE_TRY(launch_ctl_inner_check(h, nconv, w.smallvec, tol_dev, tol_fixed, maxit));
+  return cond_node(h, false, w.ci + CI_IN_GO, [&]() -> int {
     // soft locking: converged columns contribute no new search direction
-    PASE_TRY(launch_zero_cols_if(h, n, m, m, w.smallvec, tol, w.Rn));
+    PASE_TRY(launch_zero_cols_if(h, n, m, m, w.smallvec, tol_fixed, w.Rn, tol_dev));
     // W = T R, B-orthogonal to X (two Gram-Schmidt passes), products computed afresh
     double* Wb = S + m;
     PASE_TRY(op_precond(h, op, w.Rn, m, Wb, m3));
@@ -943,24 +955,73 @@ static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, double
     PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, AS, m3, w.Gq, m3, true));
     PASE_TRY(ts_gram(h, n, nbw, nbw, S, m3, BS, m3, w.Gb, m3, true));
     PASE_TRY(small_sygv(h, nbw, m, w.Gq, m3, w.Gb, m3, w.smallvec + m, w.Cs, m, w.status));
-    PASE_TRY(sync_small(h, nullptr, 0, w.status, 1));
-    if (w.h_status[0] != 0) break;  // fewer than m independent directions left
-    // X = S C, P = S[:, m:] C[m:, :]; products of X recomputed
-    PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
-    PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, S + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.Pn, m));
-    haveP = true;
-    PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
-    PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
-    PASE_CUDA(cudaMemcpyAsync(lam, w.smallvec + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
-  }
-  if (iters_out) *iters_out = std::min(it, maxit);
-  return PASE_OK;
+    PASE_TRY(launch_ctl_status(h, w.status, false));  // fewer than m independent directions: stop
+    return cond_node(h, false, w.ci + CI_IN_OK, [&]() -> int {
+      // X = S C, P = S[:, m:] C[m:, :]; products of X recomputed
+      PASE_TRY(ts_gemm(h, n, nbw, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
+      PASE_TRY(ts_gemm(h, n, nbw - m, m, 1.0, S + m, m3, w.Cs + (size_t)m * m, m, 0.0, w.Pn, m));
+      PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
+      PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
+      PASE_CUDA(cudaMemcpyAsync(lam, w.smallvec + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+      return PASE_OK;
+    });
+  });
 }
 
-// Step (c): the m smallest pairs of the augmented pencil, warm start u_H = 0, gamma = I.
-static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, const double* GA,
-                              const double* GM, double* lam, double* CH, double* CW, int* iters) {
+static int block_eigensolver(pase_ctx* h, const BlockOp& op, double* lam, const double* tol_dev, double tol_fixed,
+                             int maxit, int nconv) {
   Work& w = h->w;
+  const int m = w.m;
+  const int m3 = 3 * m;
+  const int64_t n = op.n;
+  double *S = w.S, *AS = w.AS, *BS = w.BS;
+  if (nconv <= 0 || nconv > m) nconv = m;
+  // initial Rayleigh-Ritz on the start block
+  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
+  PASE_TRY(ts_gram(h, n, m, m, S, m3, AS, m3, w.Gq, m3, true));
+  PASE_TRY(ts_gram(h, n, m, m, S, m3, BS, m3, w.Gb, m3, true));
+  PASE_TRY(small_sygv(h, m, m, w.Gq, m3, w.Gb, m3, lam, w.Cs, m, w.status));
+  PASE_TRY(launch_ctl_status(h, w.status, true));  // start block not B-independent: error
+  PASE_TRY(ts_gemm(h, n, m, m, 1.0, S, m3, w.Cs, m, 0.0, w.Xn, m));
+  PASE_TRY(launch_copy_cols(h, n, m, w.Xn, m, S, m3));
+  PASE_TRY(op_apply(h, op, S, m3, AS, BS, m3));
+  PASE_TRY(launch_ctl_inner_init(h));
+  PASE_TRY(eig_pass(h, op, lam, tol_dev, tol_fixed, maxit, nconv, false));
+  return cond_node(
+      h, true, w.ci + CI_IN_CONT, [&]() -> int { return eig_pass(h, op, lam, tol_dev, tol_fixed, maxit, nconv, true); },
+      maxit + 1);
+}
+
+// Step (c) when the augmented space is no wider than the block eigensolver's basis
+// (N_H + m <= 3m, small coarse spaces): the pencil is assembled densely and its m
+// smallest pairs come from one generalized eigensolve (M-orthonormal, exact to rounding;
+// the congruences of §4 leave the pairs unchanged, so they are not applied).
+static int dense_step_c(pase_ctx* h, const double* aH, const double* bH, const double* GA, const double* GM,
+                        double* lam, double* CH, double* CW) {
+  Work& w = h->w;
+  const int m = w.m;
+  const int64_t NH = h->NH, n = NH + m;
+  const double* src[2][3] = {{w.AHd, aH, GA}, {w.MHd, bH, GM}};
+  double* dst[2] = {w.Ad, w.Bd};
+  for (int q = 0; q < 2; ++q) {
+    if (NH) PASE_TRY(launch_geam(h, NH, (int)NH, 1.0, src[q][0], NH, 0.0, src[q][0], NH, dst[q], n));
+    PASE_TRY(launch_copy_cols(h, NH, m, src[q][1], m, dst[q] + NH, (int)n));
+    PASE_TRY(launch_transpose(h, NH, m, src[q][1], m, dst[q] + NH * n, n));
+    PASE_TRY(launch_copy_cols(h, m, m, src[q][2], m, dst[q] + NH * n + NH, (int)n));
+  }
+  PASE_TRY(small_sygv(h, (int)n, m, w.Ad, (int)n, w.Bd, (int)n, lam, w.Cd, m, w.status));
+  PASE_TRY(launch_ctl_status(h, w.status, true));
+  PASE_TRY(launch_ctl_put(h, w.ci + CI_AUG_IT, 1, true, nullptr, 0.0));
+  PASE_TRY(launch_copy_cols(h, NH, m, w.Cd, m, CH, m));
+  return launch_copy_cols(h, m, m, w.Cd + NH * m, m, CW, m);
+}
+
+// Step (c), recorded: the m smallest pairs of the augmented pencil, warm start u_H = 0,
+// gamma = I, to the inner tolerance held in the control block.
+static int record_step_c(pase_ctx* h, const double* aH, const double* bH, const double* GA, const double* GM,
+                         double* lam, double* CH, double* CW) {
+  Work& w = h->w;
+  if (w.aug_dense) return dense_step_c(h, aH, bH, GA, GM, lam, CH, CW);
   const int m = w.m;
   const int m3 = 3 * m;
   const int64_t NH = h->NH, nc = NH + m;
@@ -982,8 +1043,7 @@ static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, c
   PASE_TRY(launch_set_identity_rows(h, NH, m, m3, w.S));
   if (tr != PASE_AUG_PLAIN) PASE_TRY(launch_copy_cols(h, NH, m, w.Zt, m, w.S, m3));
   BlockOp op{nc, 0, aH, bH, GA, GM, blockdiag};
-  const double tol = h->aug_tol_now > 0 ? h->aug_tol_now : h->opt.aug_tol;
-  PASE_TRY(block_eigensolver(h, op, lam, tol, h->opt.aug_max_iter, h->aug_nconv, iters));
+  PASE_TRY(block_eigensolver(h, op, lam, w.cd + CD_AUG_TOL, 0.0, h->opt.aug_max_iter, h->aug_nconv));
   PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, CH, m));
   PASE_TRY(launch_copy_cols(h, m, m, w.S + NH * m3, m3, CW, m));
   if (tr != PASE_AUG_PLAIN)  // back to the original basis: u_H = u~_H - Z gamma~ (Alg. 5 step 3)
@@ -991,42 +1051,95 @@ static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, c
   return PASE_OK;
 }
 
+static uint64_t key_of(const void* p) { return (uint64_t)(uintptr_t)p; }
+static uint64_t key_of(double v) {
+  uint64_t u;
+  memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+// Step (c): recorded once per set of buffers and replayed (one graph launch); inside a
+// recording it is recorded in place.
+static int step_augmented_eig(pase_ctx* h, const double* aH, const double* bH, const double* GA,
+                              const double* GM, double* lam, double* CH, double* CW) {
+  auto rec = [=]() -> int { return record_step_c(h, aH, bH, GA, GM, lam, CH, CW); };
+  if (recording(h)) return rec();
+  const std::vector<uint64_t> key = {key_of(aH), key_of(bH), key_of(GA), key_of(GM), key_of(lam), key_of(CH),
+                                     key_of(CW), (uint64_t)h->aug_nconv};
+  if (!h->g_stepc.exec || h->g_stepc.key != key) {
+    PASE_TRY(graph_record(h, h->g_stepc, rec));
+    h->g_stepc.key = key;
+  }
+  return graph_launch(h, h->g_stepc);
+}
+
 // Alg. 3 steps 1-2: coarse eigenpairs of (A_H, M_H), interpolated: U = I_H^h u_H.
-static int coarse_start(pase_ctx* h, double* U, double* lam, int* iters) {
+static int record_coarse_start(pase_ctx* h, double* U, double* lam) {
   Work& w = h->w;
   const int m = w.m;
   const int m3 = 3 * m;
   const int64_t NH = h->NH;
-  if (NH < m) return fail(PASE_ERR_INVALID_ARG, "coarse start needs N_H >= m");
-  PASE_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * (NH + m) * m3, h->stream));
-  PASE_TRY(launch_hash_fill(h, NH, m, m3, 12345u, w.S));
-  BlockOp op{NH, 1, nullptr, nullptr, nullptr, nullptr};
-  PASE_TRY(block_eigensolver(h, op, lam, 1e-12, 10 * h->opt.aug_max_iter, m, iters));
-  PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, w.CH, m));
+  if (w.coarse_dense) {  // a coarse space no wider than the [X, W, P] basis: dense (A_H, M_H)
+    PASE_TRY(small_sygv(h, (int)NH, m, w.AHd, (int)NH, w.MHd, (int)NH, lam, w.CH, m, w.status));
+    PASE_TRY(launch_ctl_status(h, w.status, true));
+    PASE_TRY(launch_ctl_put(h, w.ci + CI_AUG_IT, 1, true, nullptr, 0.0));
+  } else {
+    PASE_CUDA(cudaMemsetAsync(w.S, 0, sizeof(double) * (NH + m) * m3, h->stream));
+    PASE_TRY(launch_hash_fill(h, NH, m, m3, 12345u, w.S));
+    BlockOp op{NH, 1, nullptr, nullptr, nullptr, nullptr};
+    PASE_TRY(block_eigensolver(h, op, lam, nullptr, 1e-12, 10 * h->opt.aug_max_iter, m));
+    PASE_TRY(launch_copy_cols(h, NH, m, w.S, m3, w.CH, m));
+  }
   PASE_TRY(launch_csr<double>(h, CSR_MV, m, h->Pd, h->Pd.val, nullptr, w.CH, nullptr, nullptr, nullptr, nullptr,
                               0.0, U, nullptr, nullptr, nullptr));
   return PASE_OK;
 }
+static int coarse_start(pase_ctx* h, double* U, double* lam) {
+  if (h->NH < h->w.m) return fail(PASE_ERR_INVALID_ARG, "coarse start needs N_H >= m");
+  auto rec = [=]() -> int { return record_coarse_start(h, U, lam); };
+  if (recording(h)) return rec();
+  const std::vector<uint64_t> key = {key_of(U), key_of(lam)};
+  if (!h->g_start.exec || h->g_start.key != key) {
+    PASE_TRY(graph_record(h, h->g_start, rec));
+    h->g_start.key = key;
+  }
+  return graph_launch(h, h->g_start);
+}
 
 // One outer iteration after the residual has been formed in w.R (or with W = U when
-// do_solve is false): (a) (b) (c) (d); U and lam are overwritten.
-static int iterate_body(pase_ctx* h, double* U, double* lam, bool do_solve, pase_stats* st,
-                        cudaEvent_t* ev, bool graphed = false) {
+// do_solve is false): (a) (b) (c) (d); U and lam are overwritten.  Inside a recording
+// step (a) is recorded in place (its own graph is for eager solves).
+static int iterate_body(pase_ctx* h, double* U, double* lam, bool do_solve, cudaEvent_t* ev, bool graphed = false) {
   Work& w = h->w;
   const size_t nm = (size_t)h->N * w.m;
+  if (recording(h)) ev = nullptr;
   if (ev) PASE_CUDA(cudaEventRecord(ev[0], h->stream));
-  if (do_solve) PASE_TRY(graphed ? step_linear_solve_graphed(h, U, w.W) : step_linear_solve(h, U, w.W));
+  if (do_solve)
+    PASE_TRY(graphed && !recording(h) ? step_linear_solve_graphed(h, U, w.W) : step_linear_solve(h, U, w.W));
   else PASE_CUDA(cudaMemcpyAsync(w.W, U, sizeof(double) * nm, cudaMemcpyDeviceToDevice, h->stream));
   if (ev) PASE_CUDA(cudaEventRecord(ev[1], h->stream));
   PASE_TRY(step_project(h, w.W, w.aH, w.bH, w.GA, w.GM));
   if (ev) PASE_CUDA(cudaEventRecord(ev[2], h->stream));
-  int it = 0;
-  PASE_TRY(step_augmented_eig(h, w.aH, w.bH, w.GA, w.GM, lam, w.CH, w.CW, &it));
-  if (st) st->aug_iterations += it;
+  PASE_TRY(step_augmented_eig(h, w.aH, w.bH, w.GA, w.GM, lam, w.CH, w.CW));
   if (ev) PASE_CUDA(cudaEventRecord(ev[3], h->stream));
   PASE_TRY(step_prolongate(h, w.W, w.CH, w.CW, U));
   if (ev) PASE_CUDA(cudaEventRecord(ev[4], h->stream));
   return PASE_OK;
+}
+
+// An error the device control block holds (cleared here): NaN, a start block that is not
+// B-independent, or a double-float range flag.
+static int ctl_error(pase_ctx* h, int err) {
+  PASE_CUDA(cudaMemsetAsync(h->w.ci + CI_ERR, 0, sizeof(int), h->stream));
+  if (err == kCtlErrDfRange) {
+    PASE_CUDA(cudaMemsetAsync(h->w.df_flag, 0, sizeof(int), h->stream));
+    return fail(PASE_ERR_NAN, "a block entry above 2^100 (or not finite) met the double-float products; "
+                              "set spmm_df64 = 0 for such data");
+  }
+  if (err == PASE_ERR_NOT_SPD) return fail(err, "block eigensolver: start block is not B-independent");
+  if (err == PASE_ERR_NAN) return fail(err, "NaN in an eigen-residual");
+  if (err == PASE_ERR_TIMEOUT) return fail(err, "a recorded loop reached its pass limit");
+  return fail(err, "device-side error");
 }
 
 // ------------------------------------------------------------------ batch scheme (§5)
@@ -1113,6 +1226,235 @@ static int batch_assemble(pase_ctx* h) {
   return PASE_OK;
 }
 
+// ------------------------------------------------------------------ the solve loop
+// Default block width: nev plus max(4, nev/10) guard columns, rounded up to 8.
+static int default_block(int nev, int m) {
+  if (m != 0) return m;
+  const int g = nev + std::max(4, (nev + 9) / 10);
+  return (g + 7) / 8 * 8;
+}
+
+// Alg. 3 step 7 (post_solve): A_h u = lambda M_h u-hat from the Rayleigh-Ritz block u-hat
+// (its residual is in w.R), then the residual of the new block for the next step 3.
+static int post_solve_step(pase_ctx* h) {
+  Work& w = h->w;
+  PASE_TRY(recording(h) ? step_linear_solve(h, w.U, w.W) : step_linear_solve_graphed(h, w.U, w.W));
+  PASE_CUDA(cudaMemcpyAsync(w.U, w.W, sizeof(double) * h->N * w.m, cudaMemcpyDeviceToDevice, h->stream));
+  return step_residual(h, w.U, w.lam, w.R);
+}
+
+// The start of a solve: the given block, or the coarse start of Alg. 3 steps 1-2.  With
+// a given block the first iteration skips step (a) (W = U) and its inner tolerance is
+// max(aug_tol, 1e-6) under the adaptive rule.
+static int solve_start(pase_ctx* h, const double* dU0) {
+  Work& w = h->w;
+  PASE_TRY(launch_ctl_init(h));
+  if (!dU0) return coarse_start(h, w.U, w.lam);
+  PASE_CUDA(cudaMemcpyAsync(w.U, dU0, sizeof(double) * h->N * w.m, cudaMemcpyDeviceToDevice, h->stream));
+  return launch_ctl_put(h, nullptr, 0, false, w.cd + CD_AUG_TOL,
+                        h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol);
+}
+
+// The whole solve, recorded (graph_solve): the start, the outer loop as a WHILE node
+// whose test is k_ctl_outer_check (§6 stopping rule, max_iter, pending errors), the
+// iteration under an IF node, and the copies of the result.
+static int record_solve(pase_ctx* h, int nev, double tol, const double* dU0, double* dl, double* dU) {
+  Work& w = h->w;
+  PASE_TRY(solve_start(h, dU0));
+  if (dU0) {
+    PASE_TRY(iterate_body(h, w.U, w.lam, false, nullptr));
+    PASE_TRY(launch_ctl_put(h, w.ci + CI_ITER, 1, true, nullptr, 0.0));
+  }
+  PASE_TRY(launch_ctl_put(h, w.ci + CI_OUT_CONT, 1, false, nullptr, 0.0));
+  PASE_TRY(cond_node(h, true, w.ci + CI_OUT_CONT, [&]() -> int {
+    PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+    PASE_TRY(launch_ctl_outer_check(h, nev, tol));
+    return cond_node(h, false, w.ci + CI_OUT_GO, [&]() -> int {
+      if (h->opt.post_solve)
+        PASE_TRY(cond_node(h, false, w.ci + CI_POST, [&]() -> int { return post_solve_step(h); }));
+      PASE_TRY(iterate_body(h, w.U, w.lam, true, nullptr));
+      return launch_ctl_put(h, w.ci + CI_ITER, 1, true, nullptr, 0.0);
+    });
+  }, h->opt.max_iter + 2));
+  PASE_CUDA(cudaMemcpyAsync(dl, w.lam, w.m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  PASE_CUDA(cudaMemcpyAsync(dU, w.U, sizeof(double) * h->N * w.m, cudaMemcpyDeviceToDevice, h->stream));
+  return PASE_OK;
+}
+
+// What a recorded solve depends on besides the handle's fixed buffers.
+static std::vector<uint64_t> solve_key(pase_ctx* h, int nev, double tol, const void* dU0, const void* dl,
+                                       const void* dU) {
+  return {(uint64_t)nev, key_of(tol), key_of(dU0), key_of(dl), key_of(dU), (uint64_t)h->aug_nconv,
+          (uint64_t)sm_active(h), (uint64_t)h->opt.smoother};
+}
+
+// Statistics and status of a solve from the control block (read by sync_ctl).
+static int solve_outcome(pase_ctx* h, pase_stats* st) {
+  const Work& w = h->w;
+  st->iterations = w.h_ci[CI_ITER];
+  st->converged = w.h_ci[CI_CONV];
+  st->max_residual = w.h_cd[CD_WORST];
+  st->aug_iterations = w.h_ci[CI_AUG_IT];
+  if (w.h_ci[CI_ERR]) return ctl_error(h, w.h_ci[CI_ERR]);
+  if (w.h_ci[CI_MAXED]) return fail(PASE_ERR_NOT_CONVERGED, "maximum number of iterations reached");
+  return PASE_OK;
+}
+
+// The solve driven from the host, one outer iteration at a time (per-phase timing): the
+// same tests as the recorded solve, read back once per iteration; step (c) is a graph
+// launch.
+static int solve_stepwise(pase_ctx* h, int nev, double tol, const double* dU0, pase_stats* st) {
+  Work& w = h->w;
+  cudaEvent_t ev[6];
+  for (auto& e : ev) PASE_CUDA(cudaEventCreate(&e));
+  struct EvFree {
+    cudaEvent_t* e;
+    ~EvFree() {
+      for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]);
+    }
+  } evfree{ev};
+  PASE_TRY(solve_start(h, dU0));
+  bool skip_test = dU0 != nullptr;  // the given block's first iteration has no test
+  for (;;) {
+    if (!skip_test) {
+      PASE_CUDA(cudaEventRecord(ev[0], h->stream));
+      PASE_TRY(step_residual(h, w.U, w.lam, w.R));
+      PASE_CUDA(cudaEventRecord(ev[5], h->stream));
+      PASE_TRY(launch_ctl_outer_check(h, nev, tol));
+      PASE_TRY(sync_ctl(h));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[5]);
+      st->phase_ms[4] += ms;
+      const int rc = solve_outcome(h, st);
+      if (h->opt.verbose)
+        fprintf(stderr, "[pase] iter %d  max relres(first %d) %.3e  aug_iters %d\n", st->iterations, nev,
+                st->max_residual, st->aug_iterations);
+      if (rc != PASE_OK) return rc;
+      if (!w.h_ci[CI_OUT_GO]) return PASE_OK;
+      if (w.h_ci[CI_POST]) {
+        PASE_CUDA(cudaEventRecord(ev[0], h->stream));
+        PASE_TRY(post_solve_step(h));
+        PASE_CUDA(cudaEventRecord(ev[1], h->stream));
+        PASE_CUDA(cudaEventSynchronize(ev[1]));
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        st->phase_ms[0] += ms;
+      }
+    }
+    PASE_TRY(iterate_body(h, w.U, w.lam, !skip_test, ev, true));
+    skip_test = false;
+    PASE_TRY(launch_ctl_put(h, w.ci + CI_ITER, 1, true, nullptr, 0.0));
+    PASE_CUDA(cudaEventSynchronize(ev[4]));
+    for (int p = 0; p < 4; ++p) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
+      st->phase_ms[p] += ms;
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------ batched solve, one graph
+// All handles distinct, set up, with graph_solve, on the current device.
+static bool batch_graph_ok(pase_ctx* const* hs, int count) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !hs[i]->ready || !hs[i]->opt.graph_solve || hs[i]->device != dev) return false;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return false;
+  }
+  return true;
+}
+
+// Every problem's whole solve (as record_solve) is one branch of a single graph, launched
+// once; the graph is kept by the first handle and reused while the handles, sizes and
+// buffers stay the same.
+static int solve_batched_graph(pase_ctx* const* hs, int count, const int* nev, const double* tol, const int* m,
+                               const double* const* U0, double* const* lambda, double* const* U, pase_stats* st) {
+  pase_ctx* h0 = hs[0];
+  std::vector<std::unique_ptr<Stage>> sg(count);
+  std::vector<const void*> dU0(count);
+  std::vector<void*> dl(count), dU(count);
+  std::vector<uint64_t> key;
+  std::vector<int64_t> l0(count);
+  auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < count; ++i) {
+    pase_ctx* h = hs[i];
+    const int mi = default_block(nev[i], m ? m[i] : 0);
+    if (nev[i] < 1 || !(tol[i] > 0.0) || !lambda[i] || !U[i] || mi <= nev[i])
+      return fail(PASE_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": bad arguments");
+    PASE_TRY(reserve(h, mi));
+    const double* u0 = U0 ? U0[i] : nullptr;
+    if (!u0 && h->NH < mi) return fail(PASE_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": coarse start needs N_H >= m");
+    sg[i].reset(new Stage(h));
+    const size_t nm = (size_t)h->N * mi * sizeof(double);
+    PASE_TRY(sg[i]->in(u0, nm, &dU0[i]));
+    PASE_TRY(sg[i]->out(lambda[i], mi * sizeof(double), &dl[i]));
+    PASE_TRY(sg[i]->out(U[i], nm, &dU[i]));
+    h->aug_nconv = std::min(mi, nev[i] + std::max(1, (mi - nev[i]) / 2));
+    key.push_back(h->serial);
+    for (uint64_t k : solve_key(h, nev[i], tol[i], dU0[i], dl[i], dU[i])) key.push_back(k);
+    l0[i] = h->launches;
+  }
+  if (!h0->batch_exec || h0->batch_key != key) {
+    if (h0->batch_exec) cudaGraphExecDestroy(h0->batch_exec);
+    h0->batch_exec = nullptr;
+    h0->batch_key.clear();
+    PASE_TRY(batch_record(hs, count, [&](int i) -> int {
+      return record_solve(hs[i], nev[i], tol[i], (const double*)dU0[i], (double*)dl[i], (double*)dU[i]);
+    }, &h0->batch_exec));
+    h0->batch_key = key;
+  }
+  // order: the staged inputs of every handle, the graph on the first handle's stream, then
+  // the copies back on every handle's stream
+  cudaEvent_t e = nullptr;
+  PASE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  struct EvFree {
+    cudaEvent_t e;
+    ~EvFree() { cudaEventDestroy(e); }
+  } evfree{e};
+  for (int i = 1; i < count; ++i) {
+    PASE_CUDA(cudaEventRecord(e, hs[i]->stream));
+    PASE_CUDA(cudaStreamWaitEvent(h0->stream, e, 0));
+  }
+  PASE_CUDA(cudaGraphLaunch(h0->batch_exec, h0->stream));
+  h0->graph_launches++;
+  PASE_CUDA(cudaEventRecord(e, h0->stream));
+  for (int i = 0; i < count; ++i) {
+    hs[i]->launches += hs[i]->g_batch.top_kernels;
+    hs[i]->replayed += hs[i]->g_batch.top_kernels;
+    if (i) PASE_CUDA(cudaStreamWaitEvent(hs[i]->stream, e, 0));
+  }
+  int rc = PASE_OK;
+  for (int i = 0; i < count; ++i) {
+    pase_ctx* h = hs[i];
+    PASE_TRY(sg[i]->finish());
+    PASE_TRY(sync_ctl(h));
+    pase_stats s;
+    memset(&s, 0, sizeof(s));
+    int ri = solve_outcome(h, &s);
+    h->aug_nconv = 0;
+    if (ri == PASE_OK && sm_active(h)) ri = sm_check_timeout(h);
+    if (ri == PASE_OK) ri = tc_check(h);
+    s.kernel_launches = (int)(h->launches - l0[i]);
+    s.graph_launches = i == 0 ? 1 : 0;
+    if (st) st[i] = s;
+    if (ri != PASE_OK && ri != PASE_ERR_NOT_CONVERGED && (rc == PASE_OK || rc == PASE_ERR_NOT_CONVERGED)) {
+      rc = fail(ri, "problem " + std::to_string(i) + ": " + pase_last_error());
+    } else if (ri == PASE_ERR_NOT_CONVERGED && rc == PASE_OK) {
+      rc = PASE_ERR_NOT_CONVERGED;
+    }
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (st)
+    for (int i = 0; i < count; ++i) st[i].solve_ms = ms;
+  if (rc == PASE_ERR_NOT_CONVERGED) pase::set_error("some problems reached max_iter");
+  return rc;
+}
+
 }  // namespace pase
 
 using namespace pase;
@@ -1143,6 +1485,7 @@ void pase_default_options(pase_options* o) {
   o->post_solve = 0;
   o->aug_transform = PASE_AUG_PLAIN;
   o->spmm_df64 = 1;
+  o->graph_solve = 0;
 }
 
 const char* pase_status_string(int code) {
@@ -1176,7 +1519,9 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
   if ((o.precision != PASE_PREC_FP64 && o.precision != PASE_PREC_MIXED) || o.inner_steps < 1 || o.nu1 < 0 ||
       o.linear_solver < PASE_SOLVER_VCYCLE || o.linear_solver > PASE_SOLVER_MGCG ||
       (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
-      (o.post_solve != 0 && o.post_solve != 1) || o.aug_transform < PASE_AUG_PLAIN ||
+      (o.post_solve != 0 && o.post_solve != 1) || (o.graph_solve != 0 && o.graph_solve != 1) ||
+      o.graph_pass_limit < 0 ||
+      o.aug_transform < PASE_AUG_PLAIN ||
       o.aug_transform > PASE_AUG_PRECOND_BA ||
       o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||
       !(o.aug_tol > 0.0)) {
@@ -1184,6 +1529,8 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
     return fail(PASE_ERR_INVALID_ARG, "pase_create: invalid options");
   }
   h->stream = (cudaStream_t)stream;
+  static std::atomic<uint64_t> serials(0);
+  h->serial = ++serials;
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -1201,11 +1548,16 @@ int pase_destroy(pase_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->ls_graph) cudaGraphExecDestroy(h->ls_graph);
+  for (pase::GraphRec* g : {&h->g_stepc, &h->g_start, &h->g_solve, &h->g_batch}) pase::graph_free(*g);
+  if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+  for (cudaStream_t s : h->cap_streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   sm_free(h);
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.h_small) cudaFreeHost(h->w.h_small);
   if (h->w.h_status) cudaFreeHost(h->w.h_status);
+  if (h->w.h_ci) cudaFreeHost(h->w.h_ci);
+  if (h->w.h_cd) cudaFreeHost(h->w.h_cd);
   delete h;
   return PASE_OK;
 }
@@ -1406,11 +1758,15 @@ int pase_augmented_eig(pase_handle h, int m, const double* aH, const double* bH,
   PASE_TRY(st.out(lambda, m * sizeof(double), &dl));
   PASE_TRY(st.out(C_H, hm, &dch));
   PASE_TRY(st.out(C_W, mm, &dcw));
-  int it = 0;
+  Work& w = h->w;
+  PASE_TRY(launch_ctl_put(h, w.ci + CI_AUG_IT, 0, false, w.cd + CD_AUG_TOL, h->opt.aug_tol));
   PASE_TRY(step_augmented_eig(h, (const double*)da, (const double*)db, (const double*)dga, (const double*)dgm,
-                              (double*)dl, (double*)dch, (double*)dcw, &it));
-  if (aug_iters) *aug_iters = it;
-  return st.finish();
+                              (double*)dl, (double*)dch, (double*)dcw));
+  PASE_TRY(st.finish());
+  PASE_TRY(sync_ctl(h));
+  if (w.h_ci[CI_ERR]) return ctl_error(h, w.h_ci[CI_ERR]);
+  if (aug_iters) *aug_iters = w.h_ci[CI_AUG_IT];
+  return PASE_OK;
 }
 
 int pase_prolongate(pase_handle h, int m, const double* W, const double* C_H, const double* C_W, double* U) {
@@ -1442,24 +1798,22 @@ int pase_iterate(pase_handle h, int nev, int m, double* U, double* lambda, int d
   PASE_TRY(st.out(lambda, m * sizeof(double), &dl, true));
   PASE_TRY(st.out(relres, m * sizeof(double), &drr));
   h->aug_nconv = std::min(m, nev + std::max(1, (m - nev) / 2));
-  h->aug_tol_now = h->opt.aug_tol;
+  Work& w = h->w;
+  const double* dUc = (const double*)dU;
   if (do_linear_solve || drr) {
-    PASE_TRY(step_residual(h, (const double*)dU, (const double*)dl, h->w.R));
-    if (drr) PASE_CUDA(cudaMemcpyAsync(drr, h->w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    if (do_linear_solve && h->opt.aug_adaptive) {
-      PASE_TRY(sync_small(h, h->w.relres, m, nullptr, 0));
-      double worst = 0.0;
-      for (int j = 0; j < nev; ++j) worst = std::max(worst, h->w.h_small[j]);
-      h->aug_tol_now = std::max(h->opt.aug_tol, 1e-3 * worst);
-    }
-  } else if (h->opt.aug_adaptive) {
-    h->aug_tol_now = std::max(h->opt.aug_tol, 1e-6);
+    PASE_TRY(step_residual(h, dUc, (const double*)dl, w.R));
+    if (drr) PASE_CUDA(cudaMemcpyAsync(drr, w.relres, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   }
-  const int rc = iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, nullptr, true);
-  h->aug_tol_now = 0;
+  if (do_linear_solve && h->opt.aug_adaptive) PASE_TRY(launch_ctl_aug_tol(h, nev));
+  else
+    PASE_TRY(launch_ctl_put(h, nullptr, 0, false, w.cd + CD_AUG_TOL,
+                            (!drr && h->opt.aug_adaptive) ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol));
+  const int rc = iterate_body(h, (double*)dU, (double*)dl, do_linear_solve != 0, nullptr, true);
   h->aug_nconv = 0;
   PASE_TRY(rc);
   PASE_TRY(st.finish());
+  PASE_TRY(sync_ctl(h));
+  if (w.h_ci[CI_ERR]) return ctl_error(h, w.h_ci[CI_ERR]);
   PASE_TRY(df_check(h));
   return tc_check(h);
 }
@@ -1513,6 +1867,14 @@ int pase_smoother_form(pase_handle h) {
 }
 
 int64_t pase_kernel_count(pase_handle h) { return h ? h->launches : 0; }
+
+int pase_launch_counts(pase_handle h, int64_t* kernels, int64_t* kernels_in_graphs, int64_t* graph_launches) {
+  if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
+  if (kernels) *kernels = h->launches;
+  if (kernels_in_graphs) *kernels_in_graphs = h->replayed;
+  if (graph_launches) *graph_launches = h->graph_launches;
+  return PASE_OK;
+}
 
 int pase_time_kernel(pase_handle h, int kernel, int m, int reps, double* ms_per_launch) {
   PASE_TRY(check_m(h, m));
@@ -1607,16 +1969,14 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   if (!h) return fail(PASE_ERR_INVALID_ARG, "null handle");
   if (!h->ready) return fail(PASE_ERR_STATE, "pase_setup has not completed");
   if (nev < 1 || !(tol > 0.0) || !lambda || !U) return fail(PASE_ERR_INVALID_ARG, "pase_solve: bad arguments");
-  if (m == 0) {
-    int g = nev + std::max(4, (nev + 9) / 10);
-    m = (g + 7) / 8 * 8;
-  }
+  m = default_block(nev, m);
   if (m <= nev) return fail(PASE_ERR_INVALID_ARG, "pase_solve: m must exceed nev");
   PASE_TRY(reserve(h, m));
+  if (!U0 && h->NH < m) return fail(PASE_ERR_INVALID_ARG, "coarse start needs N_H >= m");
   Work& w = h->w;
   pase_stats st;
   memset(&st, 0, sizeof(st));
-  const int64_t launches0 = h->launches;
+  const int64_t launches0 = h->launches, graphs0 = h->graph_launches;
   Stage sg(h);
   const size_t nm = (size_t)h->N * m * sizeof(double);
   const void* dU0;
@@ -1624,99 +1984,36 @@ int pase_solve(pase_handle h, int nev, double tol, int m, const double* U0, doub
   PASE_TRY(sg.in(U0, nm, &dU0));
   PASE_TRY(sg.out(lambda, m * sizeof(double), &dl));
   PASE_TRY(sg.out(U, nm, &dU));
-  cudaEvent_t ev[6];
-  for (auto& e : ev) PASE_CUDA(cudaEventCreate(&e));
-  PASE_CUDA(cudaEventRecord(ev[5], h->stream));
-  auto t0 = std::chrono::steady_clock::now();
-  bool first_solve = true;
-  if (dU0) {
-    PASE_CUDA(cudaMemcpyAsync(w.U, dU0, nm, cudaMemcpyDeviceToDevice, h->stream));
-    first_solve = false;
-  } else {
-    int it = 0;
-    PASE_TRY(coarse_start(h, w.U, w.lam, &it));
-    st.aug_iterations += it;
-  }
   h->aug_nconv = std::min(m, nev + std::max(1, (m - nev) / 2));
+  auto t0 = std::chrono::steady_clock::now();
   int rc = PASE_OK;
-  double worst = INFINITY;
-  int iter = 0;
-  for (iter = 0; iter <= h->opt.max_iter; ++iter) {
-    const bool do_solve = (iter > 0) || first_solve;
-    if (do_solve) {
-      // residual + convergence test of the current block
-      cudaEvent_t r0, r1;
-      PASE_CUDA(cudaEventCreate(&r0));
-      PASE_CUDA(cudaEventCreate(&r1));
-      PASE_CUDA(cudaEventRecord(r0, h->stream));
-      PASE_TRY(step_residual(h, w.U, w.lam, w.R));
-      PASE_CUDA(cudaEventRecord(r1, h->stream));
-      PASE_TRY(sync_small(h, w.relres, m, w.df_flag, w.df_flag ? 1 : 0));
-      if (w.df_flag && w.h_status[0]) PASE_TRY(df_check(h));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, r0, r1);
-      st.phase_ms[4] += ms;
-      cudaEventDestroy(r0);
-      cudaEventDestroy(r1);
-      worst = 0.0;
-      int conv = 0;
-      for (int j = 0; j < nev; ++j) {
-        const double r = w.h_small[j];
-        if (!(r == r)) {
-          worst = NAN;
-          break;
-        }
-        worst = std::max(worst, r);
-        if (r <= tol) ++conv;
-      }
-      st.converged = conv;
-      st.max_residual = worst;
-      if (!(worst == worst)) {
-        rc = fail(PASE_ERR_NAN, "NaN in the eigen-residual");
-        break;
-      }
-      if (h->opt.verbose)
-        fprintf(stderr, "[pase] iter %d  max relres(first %d) %.3e  aug_iters %d\n", iter, nev, worst, st.aug_iterations);
-      if (worst <= tol) break;
-      if (iter == h->opt.max_iter) {
-        rc = PASE_ERR_NOT_CONVERGED;
-        pase::set_error("maximum number of iterations reached");
-        break;
-      }
-      h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-3 * worst) : h->opt.aug_tol;
-      if (h->opt.post_solve && iter > 0) {
-        // Alg. 3 step 7: A_h u = lambda M_h u-hat from the Rayleigh-Ritz block u-hat (its
-        // residual is in w.R), then the residual of the new block for step 3
-        PASE_CUDA(cudaEventRecord(ev[0], h->stream));
-        PASE_TRY(step_linear_solve_graphed(h, w.U, w.W));
-        PASE_CUDA(cudaMemcpyAsync(w.U, w.W, nm, cudaMemcpyDeviceToDevice, h->stream));
-        PASE_TRY(step_residual(h, w.U, w.lam, w.R));
-        PASE_CUDA(cudaEventRecord(ev[1], h->stream));
-        PASE_CUDA(cudaEventSynchronize(ev[1]));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        st.phase_ms[0] += ms;
-      }
-    } else {
-      h->aug_tol_now = h->opt.aug_adaptive ? std::max(h->opt.aug_tol, 1e-6) : h->opt.aug_tol;
+  if (h->opt.graph_solve) {
+    // the whole solve is one graph launch
+    const std::vector<uint64_t> key = solve_key(h, nev, tol, dU0, dl, dU);
+    if (!h->g_solve.exec || h->g_solve.key != key) {
+      PASE_TRY(graph_record(h, h->g_solve, [&]() -> int {
+        return record_solve(h, nev, tol, (const double*)dU0, (double*)dl, (double*)dU);
+      }));
+      h->g_solve.key = key;
     }
-    PASE_TRY(iterate_body(h, w.U, w.lam, do_solve, &st, ev, true));
-    PASE_CUDA(cudaEventSynchronize(ev[4]));
-    for (int p = 0; p < 4; ++p) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
-      st.phase_ms[p] += ms;
+    PASE_TRY(graph_launch(h, h->g_solve));
+    PASE_TRY(sg.finish());
+    PASE_TRY(sync_ctl(h));
+    rc = solve_outcome(h, &st);
+  } else {
+    rc = solve_stepwise(h, nev, tol, (const double*)dU0, &st);
+    if (rc == PASE_OK || rc == PASE_ERR_NOT_CONVERGED) {
+      PASE_CUDA(cudaMemcpyAsync(dl, w.lam, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      PASE_CUDA(cudaMemcpyAsync(dU, w.U, nm, cudaMemcpyDeviceToDevice, h->stream));
     }
-    st.iterations++;
+    PASE_TRY(sg.finish());
+    PASE_TRY(sync_ctl(h));
+    st.aug_iterations = w.h_ci[CI_AUG_IT];
   }
-  PASE_CUDA(cudaMemcpyAsync(dl, w.lam, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  PASE_CUDA(cudaMemcpyAsync(dU, w.U, nm, cudaMemcpyDeviceToDevice, h->stream));
-  PASE_TRY(sg.finish());
   auto t1 = std::chrono::steady_clock::now();
   st.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   st.kernel_launches = (int)(h->launches - launches0);
-  for (auto& e : ev) cudaEventDestroy(e);
-  h->aug_tol_now = 0;
+  st.graph_launches = (int)(h->graph_launches - graphs0);
   h->aug_nconv = 0;
   if (stp) *stp = st;
   if (sm_active(h)) PASE_TRY(sm_check_timeout(h));
@@ -2086,6 +2383,7 @@ int pase_solve_batched(pase_handle* hs, int count, const int* nev, const double*
   if (count < 0 || (count > 0 && (!hs || !nev || !tol || !lambda || !U)))
     return fail(PASE_ERR_INVALID_ARG, "pase_solve_batched: bad arguments");
   if (count == 0) return PASE_OK;
+  if (batch_graph_ok(hs, count)) return solve_batched_graph(hs, count, nev, tol, m, U0, lambda, U, st);
   std::vector<int> rcs(count, PASE_OK);
   std::vector<std::string> msgs(count);
   // Problems whose handles share a CUDA stream run one after another on one thread (a

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -114,12 +115,68 @@ struct Work {
   int* colexp = nullptr;                                // split Gram column exponents [3][128]
   float *dfh = nullptr, *dfl = nullptr;                 // double-float split of a block [N][m]
   int* df_flag = nullptr;                               // a split value was outside 2^+-100
+  // small spaces solved densely: the coarse pencil [N_H][N_H] (filled at reserve) when
+  // N_H <= 3m; the augmented pencil [n_c][n_c] and its m smallest eigenvectors [n_c][m]
+  // when n_c = N_H + m <= 3m
+  bool coarse_dense = false, aug_dense = false;
+  double *AHd = nullptr, *MHd = nullptr, *Ad = nullptr, *Bd = nullptr, *Cd = nullptr;
   // step-(c) congruences (aug_transform): Z, the transformed blocks, coarse CG buffers
   double *Zt = nullptr, *aT = nullptr, *bT = nullptr, *GAT = nullptr, *GMT = nullptr;  // [N_H][m], [m][m]
   double *tr = nullptr, *tz = nullptr, *tp = nullptr, *tq = nullptr, *tsc = nullptr;   // [N_H][m] x4, [4m]
+  // control block of the device-decided loops (flow.cu): ints [kCtlInts], doubles [CD_COUNT]
+  int* ci = nullptr;
+  double* cd = nullptr;
   // host pinned mirror for small readbacks
   double* h_small = nullptr;
   int* h_status = nullptr;
+  int* h_ci = nullptr;
+  double* h_cd = nullptr;
+};
+
+// ------------------------------------------------------------------ device control block
+// Integer words of Work::ci.  The first CI_EXEC0 words are zeroed at the start of a solve;
+// the words from CI_EXEC0 on count executions of conditional graph bodies (one per body).
+enum CtlInt {
+  CI_ERR = 0,    // pending error: a PASE_ERR_* code, or kCtlErrDfRange
+  CI_OUT_CONT,   // outer loop goes on
+  CI_OUT_GO,     // this outer pass runs an iteration
+  CI_ITER,       // outer iterations done
+  CI_CONV,       // pairs at tol after the last test
+  CI_POST,       // this pass runs the second linear solve of Alg. 3 (post_solve)
+  CI_IN_CONT,    // inner (step-(c)) loop goes on
+  CI_IN_GO,      // this inner pass updates the block
+  CI_IN_OK,      // the pass's small eigensolve succeeded
+  CI_IN_IT,      // inner passes of the current step (c)
+  CI_AUG_IT,     // inner passes, summed since the solve began
+  CI_HIST_N,     // inner residual history length
+  CI_MAXED,      // max_iter reached without convergence
+  CI_EXEC0 = 16,
+};
+enum CtlDbl { CD_WORST = 0, CD_AUG_TOL, CD_IN_WORST, CD_HIST = 8, CD_COUNT = 16 };
+constexpr int kCtlHist = 8;                       // ring of inner residuals (stagnation test)
+constexpr int kCtlSlots = 240;                    // conditional bodies with a counter
+constexpr int CI_GUARD0 = CI_EXEC0 + kCtlSlots;  // pass guards of the WHILE nodes, one per slot
+constexpr int kCtlInts = CI_GUARD0 + kCtlSlots;
+constexpr int kCtlErrDfRange = 1;                 // a double-float split met |x| > 2^100
+constexpr int kCapMaxDepth = 8;
+// counter slots of the recorded graphs of a handle
+constexpr int kSlotStepC = 0, kSlotStart = 16, kSlotSolve = 32, kSlotBatch = 136, kSlotsPerSolve = 104;
+
+// A recorded and instantiated CUDA graph with what is needed to count its kernels.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> key;  // what the recording depends on
+  int slot0 = 0, nslots = 0;  // its counter slots
+  int64_t top_kernels = 0;    // kernels outside conditional bodies (run once per launch)
+  int64_t nodes_recorded = 0; // kernels recorded, bodies included
+};
+// State of a recording in progress.
+struct Capture {
+  GraphRec* rec = nullptr;
+  int depth = 0;
+  int slot_next = 0, slot_end = 0;
+  std::vector<int64_t> child;                   // kernels recorded in nested bodies, per level
+  std::vector<std::pair<int, int64_t>> bodies;  // (slot, kernels of that body alone)
 };
 
 // learned fine-level smoother (smoother.cu)
@@ -214,6 +271,21 @@ struct pase_ctx {
     int* idx = nullptr;
   } bb;
   std::vector<void*> allocations;
+  // recorded graphs (flow.cu): step (c), the coarse start, a whole solve, a solve inside
+  // a batch graph; the private streams that recordings capture on
+  pase::GraphRec g_stepc{nullptr, {}, pase::kSlotStepC, 16, 0, 0};
+  pase::GraphRec g_start{nullptr, {}, pase::kSlotStart, 16, 0, 0};
+  pase::GraphRec g_solve{nullptr, {}, pase::kSlotSolve, pase::kSlotsPerSolve, 0, 0};
+  pase::GraphRec g_batch{nullptr, {}, pase::kSlotBatch, pase::kSlotsPerSolve, 0, 0};
+  pase::Capture cap;
+  std::vector<cudaStream_t> cap_streams;
+  int64_t body_kernels[pase::kCtlSlots] = {};  // kernels of the body that owns each slot
+  int ci_last[pase::kCtlSlots] = {};           // execution counts at the last read
+  int64_t graph_launches = 0;                  // CUDA graph launches issued
+  int64_t replayed = 0;                        // kernels (of `launches`) run inside graph replays
+  uint64_t serial = 0;                         // unique id of the handle (batch graph keys)
+  cudaGraphExec_t batch_exec = nullptr;        // batch graph led by this handle
+  std::vector<uint64_t> batch_key;
 };
 
 namespace pase {
@@ -271,7 +343,7 @@ int launch_copy_cols(pase_ctx* h, int64_t n, int k, const double* src, int lds, 
                      int ldd);
 int launch_fill(pase_ctx* h, int64_t count, double v, double* x);
 int launch_zero_cols_if(pase_ctx* h, int64_t n, int m, int64_t ld, const double* crit, double thresh,
-                        double* X);
+                        double* X, const double* thresh_dev = nullptr);  // thresh_dev: read instead
 int launch_hash_fill(pase_ctx* h, int64_t rows, int cols, int64_t ld, unsigned seed, double* X);
 int launch_set_identity_rows(pase_ctx* h, int64_t row0, int k, int64_t ld, double* X);
 int launch_geam(pase_ctx* h, int64_t rows, int cols, double a, const double* A, int64_t lda,
@@ -321,6 +393,25 @@ constexpr int kReduceBlocksHost = 152 * 8;
 // FP64 FMA-rate launch (pase_time_kernel PASE_KERNEL_FMA_FP64): 2 * 8 * iters * threads * blocks flops
 constexpr int kFmaBlocks = 152 * 8, kFmaThreads = 256, kFmaIters = 4096;
 int launch_fma_fp64(pase_ctx* h, double* out);
+// device-decided control flow (flow.cu)
+bool recording(const pase_ctx* h);
+// A conditional node at the current point of the recording: IF (loop false) runs body once
+// when *flag != 0; WHILE runs it while *flag != 0 after each pass, at most max_passes
+// passes (then PASE_ERR_TIMEOUT in the control block).
+int cond_node(pase_ctx* h, bool loop, int* flag, const std::function<int()>& body, int max_passes = 0);
+int graph_record(pase_ctx* h, GraphRec& rec, const std::function<int()>& fn);
+int batch_record(pase_ctx* const* hs, int count, const std::function<int(int)>& fn, cudaGraphExec_t* out);
+int graph_launch(pase_ctx* h, GraphRec& rec);
+void graph_free(GraphRec& rec);
+int sync_ctl(pase_ctx* h, const double* src = nullptr, int count = 0);
+int launch_ctl_init(pase_ctx* h);
+int launch_ctl_put(pase_ctx* h, int* pi, int vi, bool add, double* pd, double vd);
+int launch_ctl_outer_check(pase_ctx* h, int nev, double tol);
+int launch_ctl_aug_tol(pase_ctx* h, int nev);
+int launch_ctl_inner_init(pase_ctx* h);
+int launch_ctl_inner_check(pase_ctx* h, int nconv, const double* relres, const double* tol_dev, double tol_fixed,
+                           int maxit);
+int launch_ctl_status(pase_ctx* h, const int* status, bool fatal);
 // column-wise residual of a block eigenproblem: R = AX - BX diag(lam), partial norms
 int launch_block_resid(pase_ctx* h, int64_t n, int m, const double* AX, const double* BX,
                        int64_t ldin, const double* lam, double* R, int64_t ldr, int* nblk_out);

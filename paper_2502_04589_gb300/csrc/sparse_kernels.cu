@@ -549,7 +549,8 @@ int launch_set_identity_rows(pase_ctx* h, int64_t row0, int k, int64_t ld, doubl
 
 // Column j of X (rows 0..n-1, stride ld) is zeroed where crit[j] <= thresh.
 __global__ void k_zero_cols_if(int64_t n, int m, int64_t ld, const double* __restrict__ crit,
-                               double thresh, double* __restrict__ X) {
+                               double thresh, const double* __restrict__ thresh_dev, double* __restrict__ X) {
+  if (thresh_dev) thresh = *thresh_dev;
   const int64_t total = n * m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -558,9 +559,9 @@ __global__ void k_zero_cols_if(int64_t n, int m, int64_t ld, const double* __res
   }
 }
 int launch_zero_cols_if(pase_ctx* h, int64_t n, int m, int64_t ld, const double* crit, double thresh,
-                        double* X) {
+                        double* X, const double* thresh_dev) {
   if (n * m == 0) return PASE_OK;
-  k_zero_cols_if<<<ew_grid(n * m), 256, 0, h->stream>>>(n, m, ld, crit, thresh, X);
+  k_zero_cols_if<<<ew_grid(n * m), 256, 0, h->stream>>>(n, m, ld, crit, thresh, thresh_dev, X);
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;

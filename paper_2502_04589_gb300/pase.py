@@ -13,7 +13,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpase.so")
 
 PASE_OK = 0
+PASE_ERR_NAN = -5
 PASE_ERR_NOT_CONVERGED = -6
+PASE_ERR_TIMEOUT = -7
 PASE_PREC_FP64 = 0
 PASE_PREC_MIXED = 1
 PASE_SOLVER_VCYCLE = 0
@@ -41,7 +43,8 @@ class PaseOptions(ctypes.Structure):
                 ("aug_tol", ctypes.c_double), ("aug_adaptive", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int), ("spmm_df64", ctypes.c_int)]
+                ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int), ("spmm_df64", ctypes.c_int),
+                ("graph_solve", ctypes.c_int), ("graph_pass_limit", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):
@@ -54,13 +57,13 @@ class PaseStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("max_residual", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 5), ("aug_iterations", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("graph_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "converged": self.converged,
                 "max_residual": self.max_residual, "solve_ms": self.solve_ms,
                 "phase_ms": list(self.phase_ms), "aug_iterations": self.aug_iterations,
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches, "graph_launches": self.graph_launches}
 
 
 class PaseError(RuntimeError):
@@ -79,7 +82,7 @@ EXPORTED = ["pase_default_options", "pase_create", "pase_setup", "pase_reserve",
             "pase_time_kernel", "pase_set_grid", "pase_smoother_nparams", "pase_smoother_state",
             "pase_smoother_apply", "pase_smoother_step", "pase_default_train_options",
             "pase_train_smoother",
-            "pase_kernel_count",
+            "pase_kernel_count", "pase_launch_counts",
             "pase_destroy", "pase_status_string", "pase_last_error"]
 
 
@@ -128,6 +131,7 @@ def load_library(path=LIB_PATH):
     L.pase_train_smoother.argtypes = [vp, ctypes.POINTER(PaseTrainOptions), vp]
     L.pase_kernel_count.argtypes = [vp]
     L.pase_kernel_count.restype = i64
+    L.pase_launch_counts.argtypes = [vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.pase_destroy.argtypes = [vp]
     L.pase_status_string.argtypes = [i32]
     L.pase_status_string.restype = ctypes.c_char_p
@@ -140,7 +144,7 @@ def load_library(path=LIB_PATH):
                  "pase_time_kernel",
                  "pase_profile_kernel", "pase_profile_read", "pase_set_grid", "pase_smoother_nparams",
                  "pase_smoother_state", "pase_smoother_apply", "pase_smoother_step", "pase_train_smoother",
-                 "pase_destroy"]:
+                 "pase_launch_counts", "pase_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -397,6 +401,13 @@ def pase_train_smoother(h, opt=None, **kw):
 
 def pase_kernel_count(h):
     return int(load_library().pase_kernel_count(h))
+
+
+def pase_launch_counts(h):
+    """(kernels, kernels run inside graph replays, graph launches) of the handle so far."""
+    k, g, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().pase_launch_counts(h, ctypes.byref(k), ctypes.byref(g), ctypes.byref(n)))
+    return k.value, g.value, n.value
 
 
 def pase_destroy(h):

@@ -112,4 +112,4 @@ def test_default_options_of_the_later_fields(lib):
     from paper_2502_04589_gb300 import pase as P
     o = P.pase_default_options()
     assert (o.use_graphs, o.autotune, o.smoother, o.split_gemm, o.aug_adaptive) == (1, 1, P.PASE_SMOOTHER_JACOBI, 1, 1)
-    assert (o.stencil, o.post_solve, o.aug_transform, o.spmm_df64) == (1, 0, P.PASE_AUG_PLAIN, 1)
+    assert (o.stencil, o.post_solve, o.aug_transform, o.spmm_df64, o.graph_solve) == (1, 0, P.PASE_AUG_PLAIN, 1, 0)

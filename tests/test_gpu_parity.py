@@ -287,6 +287,34 @@ def test_augmented_eig_transform_parity(which, m, transform, request):
     _augmented_eig_check(request.getfixturevalue(which), m, aug_transform=transform)
 
 
+@pytest.fixture(scope="module")
+def p3d_small():
+    return pin.build_problem(3, 16, 4, kappa_seed=7, mg_min=4)
+
+
+def test_augmented_eig_dense_small_space(p3d_small):
+    """N_H + m = 27 + 16 <= 3m: the augmented pencil is assembled densely and solved in one
+    generalized eigensolve (the block eigensolver's basis would exceed the space)."""
+    _augmented_eig_check(p3d_small, 16)
+
+
+@pytest.mark.parametrize("graph_solve", [0, 1])
+def test_solve_small_coarse_space_dense_steps(p3d_small, graph_solve):
+    """Coarse start and every step (c) dense (N_H = 27 <= 3m): pairs against shift-invert,
+    M-orthonormal block."""
+    pb, nev, m = p3d_small, 5, 16
+    c = Ctx(pb, graph_solve=graph_solve)
+    try:
+        U = torch.empty(pb.N, m, dtype=torch.float64, device="cuda")
+        lam = torch.empty(m, dtype=torch.float64, device="cuda")
+        rc, st = P.pase_solve(c.h, nev, 1e-9, m, None, lam, U)
+        assert rc == P.PASE_OK
+        ref, _ = dense.smallest_pairs_shift_invert(pb.A, pb.M, nev)
+        _check_pairs(pb, host(lam), host(U), nev, ref, 1e-9)
+    finally:
+        c.close()
+
+
 def _augmented_eig_check(pb, m, **kw):
     c = Ctx(pb, aug_adaptive=0, aug_max_iter=200, **kw)
     try:
