@@ -3,10 +3,11 @@
 
 A recorded solve runs the same kernels in the same order as the host-driven solve; only
 who evaluates the stopping tests differs (a one-thread kernel instead of the host, on the
-same numbers).  So it must take the same number of outer and inner iterations and return
-the same pairs to rounding; the pairs are also checked against the closed form or a
-shift-invert reference (1e-10 relative), their residuals recomputed by the oracle and the
-block's M-orthonormality.
+same numbers).  So, with the block-size autotuner off (its timing-based choices change
+summation orders between handles), it must take the same number of outer and inner
+iterations and return the same pairs to rounding.  The pairs are also checked against the
+closed form or a shift-invert reference (1e-10 relative), their residuals recomputed by the
+oracle, and the block's M-orthonormality.
 """
 import numpy as np
 import pytest
@@ -43,6 +44,7 @@ def _check(pb, lam, U, nev, ref, tol):
 
 
 def _run(pb, nev, tol, m, start_seed=0, repeats=1, **kw):
+    kw.setdefault("autotune", 0)
     h = _handle(pb, **kw)
     try:
         U0 = None if start_seed is None else torch.from_numpy(pin.start_vectors(start_seed, pb.N, m)).cuda()
@@ -158,7 +160,7 @@ def test_batched_one_graph_matches_single_solves():
         (pin.build_problem(2, 128, 16, mg_min=4), 8, 1e-9, "closed"),
         (pin.build_problem(3, 16, 4, kappa_seed=7, mg_min=4), 5, 1e-9, "si"),
     ]
-    runs, ms = _batch(probs, graph_solve=1)
+    runs, ms = _batch(probs, graph_solve=1, autotune=0)
     for rc, sts, lams, Us in runs:
         assert rc == P.PASE_OK, sts
         assert sum(s["graph_launches"] for s in sts) == 1

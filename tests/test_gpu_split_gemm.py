@@ -33,10 +33,12 @@ def p3d():
     return pin.build_problem(3, 32, 8, kappa_seed=5, mg_min=4)
 
 
-def _handle(pb, split):
+def _handle(pb, split, **kw):
     opt = P.pase_default_options()
     opt.coarse_level = pb.coarse_level
     opt.split_gemm = split
+    for k, v in kw.items():
+        setattr(opt, k, v)
     h = P.pase_create(opt, torch.cuda.current_stream().cuda_stream)
     try:
         P.pase_setup(h, pb.A, pb.M, pb.chain, pb.A_H, pb.M_H)
@@ -224,13 +226,15 @@ def test_split_gram_no_worse_than_fp64(p3d, m):
 
 
 def test_split_gram_nonfinite(p3d):
-    """A NaN in W gives the same NaN entries of the Gram blocks as the FP64 kernel."""
+    """A NaN in W gives the same NaN entries of the Gram blocks as the FP64 kernel.  The
+    fine-level products run in FP64 here (spmm_df64 = 0): their double-float form reports a
+    non-finite block entry as PASE_ERR_NAN instead of propagating it."""
     pb, m = p3d, 16
     W = pin.start_vectors(70, pb.N, m)
     W[1234, 5] = np.nan
     res = {}
     for split in (1, 0):
-        h = _handle(pb, split)
+        h = _handle(pb, split, spmm_df64=0)
         try:
             res[split] = _project(h, pb, m, W)
         finally:
