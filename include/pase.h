@@ -129,6 +129,10 @@ typedef struct {
                           (max_iter + 1 outer, aug_max_iter inner); n > 0: at most n passes,
                           after which the loop ends and the call returns PASE_ERR_TIMEOUT
                           (a bound on device-side iteration for callers that want one)   */
+  int stencil_columns; /* columns per consumer thread of the structured FP32 kernel: 0
+                          (default) the autotuner's choice (4 without it), or 2 / 4 fixed;
+                          2 runs twice the threads at half the registers (block widths up
+                          to 60)                                                          */
 } pase_options;
 
 /* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the
@@ -295,9 +299,10 @@ int pase_solve_batches(pase_handle h, int nev, int k, int m, double tol, double*
  * otherwise.  B, X: [N][m]; X is updated in place.  For tests and measurement. */
 int pase_smooth(pase_handle h, int m, int sweeps, const double* B, double* X);
 
-/* Which form the FP32 fine-level sweeps take after pase_setup: 3 or 2 when the fine
- * matrix was recognised as a grid-neighbour stencil in that many dimensions (structured
- * kernel), 0 for the CSR kernel. */
+/* Which form the FP32 fine-level sweeps take: 3 or 2 when the fine matrix was
+ * recognised as a grid-neighbour stencil in that many dimensions and the structured
+ * kernel serves it (after pase_reserve the autotuner may have chosen the CSR kernel for
+ * the level instead), 0 for the CSR kernel. */
 int pase_smoother_form(pase_handle h);
 
 /* Residual of a block, for callers that cannot allocate device memory.  Has no

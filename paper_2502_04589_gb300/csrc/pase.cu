@@ -177,8 +177,11 @@ void prof_end(pase_ctx* h, int id) {
 
 // ------------------------------------------------------------------ autotuner
 // For every multigrid matrix, time the damped-Jacobi sweep (the precision the linear solve
-// runs in) at 128, 256 and 512 threads per block and keep the fastest.  Deterministic
-// operands; a few launches each, once per handle and block width.
+// runs in) under each candidate schedule and keep the fastest: the CSR kernel at 128, 256
+// and 512 threads per block and, for FP32 sweeps on a level the structured kernel serves,
+// that kernel with one or two resident CTAs per SM, 3, 6 or 12 work items (plane chunks)
+// per resident CTA, and 4 or 2 columns per consumer thread.  Deterministic operands; a few launches each, once per handle
+// and block width.
 static int autotune(pase_ctx* h) {
   Work& w = h->w;
   const int m = w.m;
@@ -202,9 +205,28 @@ static int autotune(pase_ctx* h) {
       PASE_TRY(launch_f64_to_f32(h, nl * m, b, bf));
     }
     float best = 1e30f;
-    int best_bs = 256;
-    for (int c : cand) {
-      L.A.block = c;
+    int best_bs = 256, best_use = 0, best_psm = 0, best_items = 6, best_cw = 4;
+    // candidates: (structured kernel?, threads per block or CTAs per SM, items per CTA)
+    struct Cand {
+      int use, bs, psm, items, cw;
+    };
+    std::vector<Cand> cands;
+    const int fixed_cw = h->opt.stencil_columns;  // 0: the autotuner chooses
+    for (int c : cand) cands.push_back({0, c, 0, 6, fixed_cw ? fixed_cw : 4});
+    const bool st = mixed && h->opt.stencil && L.A.st_val && h->tc_err && stencil_ok(L.A, CSR_JACOBI, m, 0, 0);
+    if (st) {
+      if (fixed_cw != 2)
+        for (int psm : {2, 1})
+          for (int items : {3, 6, 12}) cands.push_back({1, 256, psm, items, 4});
+      if (fixed_cw != 4 && 16 * (m / 2) + 32 <= 512)
+        for (int items : {3, 6, 12}) cands.push_back({1, 256, 2, items, 2});
+    }
+    for (const Cand& cd : cands) {
+      L.A.block = cd.bs;
+      L.A.st_use = cd.use;
+      L.A.st_per_sm = cd.psm;
+      L.A.st_items = cd.items;
+      L.A.st_cw = cd.cw;
       for (int rep = 0; rep < 2; ++rep) {
         if (rep == 1) PASE_CUDA(cudaEventRecord(e0, h->stream));
         for (int it = 0; it < 3; ++it) {
@@ -222,11 +244,21 @@ static int autotune(pase_ctx* h) {
       PASE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) {
         best = ms;
-        best_bs = c;
+        best_bs = cd.bs;
+        best_use = cd.use;
+        best_psm = cd.psm;
+        best_items = cd.items;
+        best_cw = cd.cw;
       }
     }
     L.A.block = best_bs;
-    if (h->opt.verbose) fprintf(stderr, "[pase] autotune level %d: %d threads/block (%.3f ms for 3 sweeps)\n", l, best_bs, best);
+    L.A.st_use = st ? best_use : 1;
+    L.A.st_per_sm = best_psm;
+    L.A.st_items = best_items;
+    L.A.st_cw = best_cw;
+    if (h->opt.verbose)
+      fprintf(stderr, "[pase] autotune level %d: %s, %d threads/block, %d CTAs/SM, %d items, %d columns/thread "
+              "(%.3f ms for 3 sweeps)\n", l, best_use ? "structured" : "CSR", best_bs, best_psm, best_items, best_cw, best);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1520,6 +1552,7 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
       o.linear_solver < PASE_SOLVER_VCYCLE || o.linear_solver > PASE_SOLVER_MGCG ||
       (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
       (o.post_solve != 0 && o.post_solve != 1) || (o.graph_solve != 0 && o.graph_solve != 1) ||
+      (o.stencil_columns != 0 && o.stencil_columns != 2 && o.stencil_columns != 4) ||
       o.graph_pass_limit < 0 ||
       o.aug_transform < PASE_AUG_PLAIN ||
       o.aug_transform > PASE_AUG_PRECOND_BA ||
@@ -1628,6 +1661,7 @@ int pase_setup(pase_handle h, const pase_csr* A_h, const pase_csr* M_h, int n_in
       std::vector<float> d32(dinv.begin(), dinv.end());
       PASE_TRY(upload_vec(h, d32, &L.dinv32));
       if (h->opt.stencil) PASE_TRY(stencil_setup(h, Al[l], dinv, L.A));
+      if (h->opt.stencil_columns) L.A.st_cw = h->opt.stencil_columns;
     }
     if (l < n_interp) {
       PASE_TRY(upload_csr(h, Pc[l], L.P, mixed, false, nullptr));
@@ -1863,7 +1897,7 @@ int pase_smooth(pase_handle h, int m, int sweeps, const double* B, double* X) {
 
 int pase_smoother_form(pase_handle h) {
   if (!h || !h->ready || h->lv.empty()) return 0;
-  return h->lv[0].A.st_val ? h->lv[0].A.st_dim : 0;
+  return (h->opt.stencil && h->lv[0].A.st_val && h->lv[0].A.st_use) ? h->lv[0].A.st_dim : 0;
 }
 
 int64_t pase_kernel_count(pase_handle h) { return h ? h->launches : 0; }

@@ -70,6 +70,11 @@ struct DevCSR {
   // x extent padded to st_xp; null when the matrix is not a grid-neighbour stencil
   float* st_val = nullptr;
   int st_dim = 0, st_n1 = 0, st_xp = 0;
+  // schedule of the FP32 sweeps on this level, set by the autotuner: structured kernel or
+  // CSR; resident CTAs per SM of the structured kernel (0 = as many as fit, up to 2); work
+  // items per resident CTA (plane chunks of a tile); columns per consumer thread (4, or 2:
+  // twice the threads at half the registers)
+  int st_use = 1, st_per_sm = 0, st_items = 6, st_cw = 4;
 };
 
 struct Level {

@@ -60,6 +60,38 @@ __device__ __forceinline__ void fma4(float4& a, float s, const float4& x) {
   a.z = fmaf(s, x.z, a.z);
   a.w = fmaf(s, x.w, a.w);
 }
+// a consumer thread's column slice: 4 (float4) or 2 (float2) columns
+template <int CW>
+struct StVec;
+template <>
+struct StVec<4> {
+  using T = float4;
+  static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ T ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
+  static __device__ __forceinline__ void st(float* p, const T& v) { *reinterpret_cast<float4*>(p) = v; }
+  static __device__ __forceinline__ void fma(T& a, float s, const T& x) { fma4(a, s, x); }
+  static __device__ __forceinline__ T sub(const T& b, const T& o) {
+    return make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
+  }
+  static __device__ __forceinline__ T axpy(float d, const T& o, const T& x) {  // d o + x
+    return make_float4(fmaf(d, o.x, x.x), fmaf(d, o.y, x.y), fmaf(d, o.z, x.z), fmaf(d, o.w, x.w));
+  }
+};
+template <>
+struct StVec<2> {
+  using T = float2;
+  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ T ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ void st(float* p, const T& v) { *reinterpret_cast<float2*>(p) = v; }
+  static __device__ __forceinline__ void fma(T& a, float s, const T& x) {
+    a.x = fmaf(s, x.x, a.x);
+    a.y = fmaf(s, x.y, a.y);
+  }
+  static __device__ __forceinline__ T sub(const T& b, const T& o) { return make_float2(b.x - o.x, b.y - o.y); }
+  static __device__ __forceinline__ T axpy(float d, const T& o, const T& x) {
+    return make_float2(fmaf(d, o.x, x.x), fmaf(d, o.y, x.y));
+  }
+};
 __device__ __forceinline__ float vcomp(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
@@ -139,14 +171,17 @@ __device__ __forceinline__ void stage_fill(int lane, int n1, int m, int x0t, int
 // stage is filled once its "empty" barrier shows that every consumer warp has released its
 // previous plane, and read once its "full" barrier shows the copies landed; no CTA-wide
 // barrier in the loop, so consumer warps never wait for each other.
-// WIDE: up to 512 threads (m > 64), one CTA per SM; otherwise up to 256 threads and two
-// CTAs per SM; 128 registers per thread either way.
-template <int DIM, int MODE, bool WIDE>
-__global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
+// CW: columns per consumer thread (4, or 2 for twice the threads at half the registers).
+// MAXT, MINB: launch bounds - (256, 2) and (512, 1) give 128 registers per thread,
+// (512, 2) 64.
+template <int DIM, int MODE, int CW, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
     k_stencil(int n1, int m, int tpr, int ntx, int nty, int pch, int npc, int NS, const float* __restrict__ V,
               const float* __restrict__ X, const float* __restrict__ B, float omega, float* __restrict__ Y,
               int* __restrict__ err) {
   using Gm = StGeo<DIM>;
+  using SV = StVec<CW>;
+  using VT = typename SV::T;
   constexpr int T = Gm::T;
   constexpr bool WB = MODE == CSR_RESID || MODE == CSR_JACOBI;
   extern __shared__ __align__(128) float st_smem[];
@@ -203,7 +238,7 @@ __global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
       if (g >= 0) mbar_wait_bounded(smem_u32(&full[g % NS]), (uint32_t)((g / NS) & 1), kStWaitLimit);
   } else {
     const int g = tid / tpr;  // 4-row group of this thread
-    const int col = 4 * (tid - g * tpr);
+    const int col = CW * (tid - g * tpr);
     const bool active = g < Gm::G;
     const int rx = g % Gm::RUNS, ly = g / Gm::RUNS;
     bool failed = false;
@@ -216,9 +251,9 @@ __global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
       const int pb = pc * pch, pe = min(n1, pb + pch);
       const int x0 = x0t + 4 * rx, y = DIM == 3 ? y0t + ly : 0;
       const bool rows = active && x0 < n1 && y < n1;
-      float4 aP[4], aC[4], aN[4], xo[4];  // xo: X of the own rows on the previous plane
+      VT aP[4], aC[4], aN[4], xo[4];  // xo: X of the own rows on the previous plane
 #pragma unroll
-      for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = xo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = xo[i] = SV::zero();
       for (int p = pb - 1; p <= pe; ++p, ++gstep) {
         const int s = (int)(gstep % NS);
         const bool hasN = p + 1 >= pb && p + 1 < pe;
@@ -245,17 +280,10 @@ __global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             if (x0 + i >= n1) break;
-            float4 o = aP[i];
-            if (WB) {
-              const float4 b = lds4(bs + ((int64_t)ly * Gm::TX + 4 * rx + i) * m + col);
-              o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
-            }
-            if (MODE == CSR_JACOBI) {
-              const float d = omega * vcomp(dv, i);
-              o = make_float4(fmaf(d, o.x, xo[i].x), fmaf(d, o.y, xo[i].y), fmaf(d, o.z, xo[i].z),
-                              fmaf(d, o.w, xo[i].w));
-            }
-            *reinterpret_cast<float4*>(Y + (rbase + i) * m + col) = o;
+            VT o = aP[i];
+            if (WB) o = SV::sub(SV::ld(bs + ((int64_t)ly * Gm::TX + 4 * rx + i) * m + col), o);
+            if (MODE == CSR_JACOBI) o = SV::axpy(omega * vcomp(dv, i), o, xo[i]);
+            SV::st(Y + (rbase + i) * m + col, o);
           }
         };
         if (rows && p >= 0 && p < n1) {
@@ -264,22 +292,22 @@ __global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
             const int dy = dl == 0 ? -1 : (dl == 1 ? 1 : 0);
             if (DIM == 2 && dy != 0) continue;
             const int hl = DIM == 3 ? ly + 1 + dy : 0;  // staged line
-            float4 xl[6];
+            VT xl[6];
             const float* xrow = xs + ((int64_t)hl * (Gm::TX + 2) + 4 * rx) * m + col;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) xl[j] = lds4(xrow + (int64_t)j * m);
+            for (int j = 0; j < 6; ++j) xl[j] = SV::ld(xrow + (int64_t)j * m);
             const int tl = DIM == 3 ? 3 * (dy + 1) : 0;
             const int tz = DIM == 3 ? 9 : 3;
 #pragma unroll
             for (int role = 0; role < 3; ++role) {  // 0: plane p+1 (offset -1), 1: p, 2: p-1 (offset +1)
               if ((role == 0 && !hasN) || (role == 1 && !hasC) || (role == 2 && !hasP)) continue;
-              float4(&acc)[4] = role == 0 ? aN : (role == 1 ? aC : aP);
+              VT(&acc)[4] = role == 0 ? aN : (role == 1 ? aC : aP);
 #pragma unroll
               for (int dx = 0; dx < 3; ++dx) {
                 const int t = tl + role * tz + dx;
                 const float4 v = lds4(vs + ((int64_t)t * Gm::TY + ly) * Gm::TX + 4 * rx);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) fma4(acc[i], vcomp(v, i), xl[i + dx]);
+                for (int i = 0; i < 4; ++i) SV::fma(acc[i], vcomp(v, i), xl[i + dx]);
               }
             }
             if (dy == 0) {  // last line: plane p-1 is complete; the own rows of plane p are kept
@@ -295,7 +323,7 @@ __global__ void __launch_bounds__(WIDE ? 512 : 256, WIDE ? 1 : 2)
         for (int i = 0; i < 4; ++i) {
           aP[i] = aC[i];
           aC[i] = aN[i];
-          aN[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          aN[i] = SV::zero();
         }
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
@@ -381,7 +409,10 @@ bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy) {
 // ------------------------------------------------------------------ launch
 int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X, const float* B, double omega,
                    float* Y) {
-  const int tpr = m / 4;
+  // two columns per thread (twice the consumer warps at 64 registers) when chosen by the
+  // autotuner and the threads fit in 512; else four
+  const int cw = (A.st_cw == 2 && 16 * (m / 2) + 32 <= 512) ? 2 : 4;
+  const int tpr = m / cw;
   const int dim = A.st_dim, n1 = A.st_n1;
   const int TX = dim == 3 ? 16 : 64, TY = dim == 3 ? 4 : 1;
   const int ntx = (n1 + TX - 1) / TX, nty = dim == 3 ? (n1 + TY - 1) / TY : 1;
@@ -392,16 +423,18 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
   // one CTA per SM 0.55 ms with 2 to 4 stages, two CTAs per SM 0.37 ms with 2), so two
   // CTAs per SM when their registers (128 per thread) and stages fit, each with as many
   // stages as shared memory leaves.
-  int per_sm = threads <= 256 ? 2 : 1;
+  int per_sm = (threads <= 256 || cw == 2) ? 2 : 1;
+  if (A.st_per_sm == 1) per_sm = 1;
   int NS = (int)std::min<size_t>(kStMaxStages, (200 * 1024) / per_sm / stage);
   if (NS < 2) {
     per_sm = 1;
     NS = (int)std::min<size_t>(kStMaxStages, (200 * 1024) / stage);
   }
   const size_t smem = (size_t)NS * stage;
-  // planes per work item: about six items per resident CTA, at least 8 planes per item
+  // planes per work item: about st_items items per resident CTA (6 unless the autotuner
+  // chose otherwise), at least 8 planes per item
   const int64_t tiles = (int64_t)ntx * nty;
-  const int64_t want = (int64_t)h->num_sms * per_sm * 6;
+  const int64_t want = (int64_t)h->num_sms * per_sm * std::max(1, A.st_items);
   int npc = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, n1 / 8), (want + tiles - 1) / tiles));
   const int pch = (n1 + npc - 1) / npc;
   npc = (n1 + pch - 1) / pch;
@@ -409,17 +442,19 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
   const int grid = (int)std::min<int64_t>(items, (int64_t)h->num_sms * per_sm);
   auto s = h->stream;
   const float om = (float)omega;
-#define PASE_ST_LAUNCH(D, MD)                                                                                 \
+#define PASE_ST_GO(D, MD, CWV, MT, MB)                                                                        \
   do {                                                                                                        \
-    if (threads > 256) {                                                                                      \
-      PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, true>, 200 * 1024));                              \
-      k_stencil<D, MD, true><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B, om, \
-                                                          Y, h->tc_err);                                      \
-    } else {                                                                                                  \
-      PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, false>, 200 * 1024));                             \
-      k_stencil<D, MD, false><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B,    \
-                                                           om, Y, h->tc_err);                                 \
-    }                                                                                                         \
+    PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, CWV, MT, MB>, 200 * 1024));                        \
+    k_stencil<D, MD, CWV, MT, MB><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B, \
+                                                               om, Y, h->tc_err);                             \
+  } while (0)
+#define PASE_ST_LAUNCH(D, MD)                 \
+  do {                                        \
+    if (cw == 2) PASE_ST_GO(D, MD, 2, 512, 2); \
+    else if (threads > 256)                   \
+      PASE_ST_GO(D, MD, 4, 512, 1);           \
+    else                                      \
+      PASE_ST_GO(D, MD, 4, 256, 2);           \
   } while (0)
   if (dim == 3) {
     if (mode == CSR_JACOBI) PASE_ST_LAUNCH(3, CSR_JACOBI);
@@ -431,6 +466,7 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
     else PASE_ST_LAUNCH(2, CSR_MV);
   }
 #undef PASE_ST_LAUNCH
+#undef PASE_ST_GO
   h->launches++;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;

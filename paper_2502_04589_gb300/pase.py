@@ -44,7 +44,8 @@ class PaseOptions(ctypes.Structure):
                 ("verbose", ctypes.c_int), ("use_graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int), ("stencil", ctypes.c_int),
                 ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int), ("spmm_df64", ctypes.c_int),
-                ("graph_solve", ctypes.c_int), ("graph_pass_limit", ctypes.c_int)]
+                ("graph_solve", ctypes.c_int), ("graph_pass_limit", ctypes.c_int),
+                ("stencil_columns", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):

@@ -69,12 +69,15 @@ def test_graph_replay_matches_eager(precision):
     _check(pb, l1, U1, 6, spectrum.q1_laplace_eigenvalues(2, 64, 6), 1e-9)
 
 
-def test_autotuned_block_sizes_keep_results():
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+def test_autotuned_block_sizes_keep_results(precision):
+    """The autotuner's choices (block sizes; in the mixed form also CSR vs the structured
+    kernel and the latter's schedule per level) leave the solution within the gates."""
     pb = pin.build_problem(3, 32, 8, mg_min=4)
     s = torch.cuda.Stream()
     ref = spectrum.q1_laplace_eigenvalues(3, 32, 8)
     for tune in (0, 1):
-        rc, st, lam, U = _solve_one(pb, 8, 1e-9, 16, s, autotune=tune)
+        rc, st, lam, U = _solve_one(pb, 8, 1e-9, 16, s, autotune=tune, precision=precision)
         assert rc == P.PASE_OK
         _check(pb, lam, U, 8, ref, 1e-9)
 

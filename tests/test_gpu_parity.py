@@ -683,21 +683,23 @@ def _jacobi_bound(A, b, x, omega, gamma):
 
 @pytest.mark.parametrize("d,n,kseed", [(3, 32, 5), (3, 20, 6), (2, 64, 7), (2, 38, 8)])
 @pytest.mark.parametrize("m", [8, 56])
-@pytest.mark.parametrize("stencil", [1, 0])
-def test_fp32_smoothing_parity(d, n, kseed, m, stencil):
+@pytest.mark.parametrize("stencil,cols", [(1, 4), (1, 2), (0, 0)])
+def test_fp32_smoothing_parity(d, n, kseed, m, stencil, cols):
     """Two FP32 damped-Jacobi sweeps on the fine level (the mixed form's smoother) against
     the oracle's FP64 sweeps, entry by entry, within the FP32 rounding bound of the two
     sweeps (the first sweep's error carried through the second by |I| + omega |D^-1||A|).
     stencil=1 runs the structured-grid kernel (grids of 31^3, 19^3, 63^2, 37^2 nodes: ragged
-    against its 16 x 4 / 64-node tiles), stencil=0 the CSR kernel."""
+    against its 16 x 4 / 64-node tiles) with 4 or 2 columns per thread, stencil=0 the CSR
+    kernel (the autotuner, which may pick either per level, is off)."""
     pb = pin.build_problem(d, n, n // 2, kappa_seed=kseed)
-    c = Ctx(pb, precision=P.PASE_PREC_MIXED, stencil=stencil)
+    c = Ctx(pb, precision=P.PASE_PREC_MIXED, stencil=stencil, autotune=0, stencil_columns=cols)
     try:
         assert P.pase_smoother_form(c.h) == (d if stencil else 0)
         B = pin.start_vectors(30 + m, pb.N, m)
         X0 = pin.start_vectors(31 + m, pb.N, m)
         X = X0.copy()
         P.pase_smooth(c.h, m, 2, B, X)
+        assert P.pase_smoother_form(c.h) == (d if stencil else 0)
     finally:
         c.close()
     hier = mg.Hierarchy(pb.A, pb.chain)
