@@ -213,7 +213,8 @@ static int autotune(pase_ctx* h) {
     std::vector<Cand> cands;
     const int fixed_cw = h->opt.stencil_columns;  // 0: the autotuner chooses
     for (int c : cand) cands.push_back({0, c, 0, 6, fixed_cw ? fixed_cw : 4});
-    const bool st = mixed && h->opt.stencil && L.A.st_val && h->tc_err && stencil_ok(L.A, CSR_JACOBI, m, 0, 0);
+    const bool st =
+        mixed && h->opt.stencil && L.A.st_val && h->tc_err && stencil_ok(L.A, CSR_JACOBI, m, 0, 0, h->opt.omega);
     if (st) {
       if (fixed_cw != 2)
         for (int psm : {2, 1})

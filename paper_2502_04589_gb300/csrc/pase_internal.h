@@ -69,6 +69,8 @@ struct DevCSR {
   // structured-grid form of the FP32 values (stencil.cu): 3^d tap planes then 1 / a_ii,
   // x extent padded to st_xp; null when the matrix is not a grid-neighbour stencil
   float* st_val = nullptr;
+  float* st_jval = nullptr;  // the same for the damped-Jacobi iteration matrix at omega st_omega
+  double st_omega = 0.0;
   int st_dim = 0, st_n1 = 0, st_xp = 0;
   // schedule of the FP32 sweeps on this level, set by the autotuner: structured kernel or
   // CSR; resident CTAs per SM of the structured kernel (0 = as many as fit, up to 2); work
@@ -331,7 +333,7 @@ int launch_csr_df64(pase_ctx* h, int mode, int m, const DevCSR& A, const float* 
 
 // structured-grid FP32 kernels (stencil.cu)
 int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv, DevCSR& d);
-bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy);
+bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy, double omega);
 int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X, const float* B, double omega,
                    float* Y);
 

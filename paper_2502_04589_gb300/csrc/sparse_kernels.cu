@@ -187,7 +187,7 @@ int launch_csr(pase_ctx* h, int mode, int m, const DevCSR& A, const T* va, const
     if (mode == CSR_MV_AM && sizeof(T) == 8) prof_id = PASE_KERNEL_SPMM_AM_FP64;
     if (mode == CSR_JACOBI) prof_id = sizeof(T) == 8 ? PASE_KERNEL_JACOBI_FP64 : PASE_KERNEL_JACOBI_FP32;
   }
-  if (sizeof(T) == 4 && h->opt.stencil && A.st_use && h->tc_err && stencil_ok(A, mode, m, ldx, ldy)) {
+  if (sizeof(T) == 4 && h->opt.stencil && A.st_use && h->tc_err && stencil_ok(A, mode, m, ldx, ldy, omega)) {
     // grid-neighbour operator: the structured FP32 kernel (no column indices, X reuse in registers)
     prof_begin(h, prof_id);
     const int rc = launch_stencil(h, mode, m, A, (const float*)X, (const float*)B, omega, (float*)Y1);

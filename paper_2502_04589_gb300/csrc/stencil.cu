@@ -18,16 +18,19 @@
 // completion counted on an mbarrier), several planes ahead of the computation, in a ring
 // of stages.  A thread owns 4 consecutive x rows and one 16-byte column slice; X values of
 // plane p feed the three output planes p-1, p, p+1 through three rolling register
-// accumulators, so each X value is read from shared memory once per (line, x window), and
-// the thread keeps its own rows of plane p in registers for the update of that plane one
-// step later.  Every operand stream (X, b, coefficients, y) crosses HBM once.
+// accumulators, so each X value is read from shared memory once per (line, x window).  The
+// damped-Jacobi sweep runs on the coefficients of its iteration matrix J = I - omega D^-1 A
+// (y = J x + omega D^-1 b), so no copy of the old x is held for the update.  Every operand
+// stream (X, b, coefficients, y) crosses HBM once.
 //
 // Coefficient layout ("step-major"), built at setup: the coefficient of row q's tap
 // t = (dx+1) + 3(dy+1) + 9(dz+1) (2D: (dx+1) + 3(dy+1), dy the marching offset) is needed
 // while plane q + dz is staged, so it is stored with step s = q + dz + 1, tile-blocked:
 //   [s = 0 .. n1+1][tile y][tile x][slot 0 .. T][TY][TX]   (zeros outside the grid)
 // slot T holding 1 / a_qq for plane q = s - 2 (the plane whose sweep completes then).  One
-// bulk copy of (T+1) TY TX floats per tile and step.
+// bulk copy of (T+1) TY TX floats per tile and step.  A second array in the same layout
+// holds J's coefficients (1 - omega a_qq / a_qq on the centre tap, -omega a_qj / a_qq
+// elsewhere) with omega / a_qq in slot T, for the handle's omega.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -251,9 +254,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
       const int pb = pc * pch, pe = min(n1, pb + pch);
       const int x0 = x0t + 4 * rx, y = DIM == 3 ? y0t + ly : 0;
       const bool rows = active && x0 < n1 && y < n1;
-      VT aP[4], aC[4], aN[4], xo[4];  // xo: X of the own rows on the previous plane
+      VT aP[4], aC[4], aN[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = xo[i] = SV::zero();
+      for (int i = 0; i < 4; ++i) aP[i] = aC[i] = aN[i] = SV::zero();
       for (int p = pb - 1; p <= pe; ++p, ++gstep) {
         const int s = (int)(gstep % NS);
         const bool hasN = p + 1 >= pb && p + 1 < pe;
@@ -271,7 +274,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
         const float* xs = xs_base + s * xs_floats;
         const float* vs = vs_base + (int64_t)s * Gm::VF;
         const float* bs = bs_base + s * bs_floats;
-        // the update of plane p-1, complete once plane p's lines have been applied
+        // the update of plane p-1, complete once plane p's lines have been applied.  JACOBI
+        // runs on the coefficients of the iteration matrix I - omega D^-1 A (slot T: omega /
+        // a_qq), so y = aP + (omega / a_qq) b needs no copy of the old x.
         auto epilogue = [&]() {
           const int q = p - 1;
           const int64_t rbase = DIM == 3 ? ((int64_t)q * n1l + y) * n1l + x0 : (int64_t)q * n1l + x0;
@@ -281,8 +286,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
           for (int i = 0; i < 4; ++i) {
             if (x0 + i >= n1) break;
             VT o = aP[i];
-            if (WB) o = SV::sub(SV::ld(bs + ((int64_t)ly * Gm::TX + 4 * rx + i) * m + col), o);
-            if (MODE == CSR_JACOBI) o = SV::axpy(omega * vcomp(dv, i), o, xo[i]);
+            if (WB) {
+              const VT b = SV::ld(bs + ((int64_t)ly * Gm::TX + 4 * rx + i) * m + col);
+              o = MODE == CSR_JACOBI ? SV::axpy(vcomp(dv, i), b, o) : SV::sub(b, o);
+            }
             SV::st(Y + (rbase + i) * m + col, o);
           }
         };
@@ -310,11 +317,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 for (int i = 0; i < 4; ++i) SV::fma(acc[i], vcomp(v, i), xl[i + dx]);
               }
             }
-            if (dy == 0) {  // last line: plane p-1 is complete; the own rows of plane p are kept
-              if (hasP) epilogue();
-#pragma unroll
-              for (int i = 0; i < 4; ++i) xo[i] = xl[i + 1];
-            }
+            if (dy == 0 && hasP) epilogue();  // last line: plane p-1 is complete
           }
         } else if (rows && hasP) {
           epilogue();
@@ -377,6 +380,10 @@ int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv
       const int64_t tx = x / TX, ty = dim == 3 ? y / TY : 0, lx = x % TX, lyy = dim == 3 ? y % TY : 0;
       return (size_t)(((((s * nty + ty) * ntx + tx) * (T + 1) + t) * TY + lyy) * TX + lx);
     };
+    // the same layout for the damped-Jacobi iteration matrix I - omega D^-1 A (slot T:
+    // omega / a_qq), so that a sweep is y = J x + (omega D^-1) b
+    const double om = h->opt.omega;
+    std::vector<float> sj(sv.size(), 0.f);
     for (int64_t i = 0; i < N; ++i) {
       const int64_t xi = i % n1, yi = (i / n1) % n1, zi = dim == 3 ? i / (n1 * n1) : 0;
       const int64_t qi = dim == 3 ? zi : yi;  // plane along the marching axis
@@ -386,11 +393,16 @@ int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv
         const int64_t off = dim == 3 ? dz : dy;  // offset along the marching axis
         const int t = (int)((dx + 1) + 3 * (dy + 1) + (dim == 3 ? 9 * (dz + 1) : 0));
         sv[slot(qi + off + 1, xi, yi, t)] = (float)A.val[k];
+        sj[slot(qi + off + 1, xi, yi, t)] = (float)((j == i ? 1.0 : 0.0) - om * dinv[i] * A.val[k]);
       }
       sv[slot(qi + 2, xi, yi, T)] = (float)dinv[i];
+      sj[slot(qi + 2, xi, yi, T)] = (float)(om * dinv[i]);
     }
     PASE_TRY(dev_alloc_t(h, &d.st_val, sv.size()));
     PASE_CUDA(cudaMemcpy(d.st_val, sv.data(), sizeof(float) * sv.size(), cudaMemcpyHostToDevice));
+    PASE_TRY(dev_alloc_t(h, &d.st_jval, sj.size()));
+    PASE_CUDA(cudaMemcpy(d.st_jval, sj.data(), sizeof(float) * sj.size(), cudaMemcpyHostToDevice));
+    d.st_omega = om;
     d.st_dim = dim;
     d.st_n1 = (int)n1;
     d.st_xp = 0;
@@ -399,8 +411,9 @@ int stencil_setup(pase_ctx* h, const HostCSR& A, const std::vector<double>& dinv
   return PASE_OK;
 }
 
-bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy) {
+bool stencil_ok(const DevCSR& A, int mode, int m, int64_t ldx, int64_t ldy, double omega) {
   if (A.st_val == nullptr || !(mode == CSR_MV || mode == CSR_RESID || mode == CSR_JACOBI)) return false;
+  if (mode == CSR_JACOBI && (A.st_jval == nullptr || omega != A.st_omega)) return false;  // J built for this omega
   if (m % 8 != 0 || m < 8 || m > 128 || (ldx > 0 && ldx != m) || (ldy > 0 && ldy != m)) return false;
   const size_t stage = A.st_dim == 3 ? st_stage_bytes<3>(m, true) : st_stage_bytes<2>(m, true);
   return 2 * stage <= 200 * 1024;
@@ -442,11 +455,12 @@ int launch_stencil(pase_ctx* h, int mode, int m, const DevCSR& A, const float* X
   const int grid = (int)std::min<int64_t>(items, (int64_t)h->num_sms * per_sm);
   auto s = h->stream;
   const float om = (float)omega;
+  const float* coef = mode == CSR_JACOBI ? A.st_jval : A.st_val;
 #define PASE_ST_GO(D, MD, CWV, MT, MB)                                                                        \
   do {                                                                                                        \
     PASE_TRY(ensure_max_smem((const void*)k_stencil<D, MD, CWV, MT, MB>, 200 * 1024));                        \
-    k_stencil<D, MD, CWV, MT, MB><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, A.st_val, X, B, \
-                                                               om, Y, h->tc_err);                             \
+    k_stencil<D, MD, CWV, MT, MB><<<grid, threads, smem, s>>>(n1, m, tpr, ntx, nty, pch, npc, NS, coef, X, B, om, \
+                                                               Y, h->tc_err);                                 \
   } while (0)
 #define PASE_ST_LAUNCH(D, MD)                 \
   do {                                        \
