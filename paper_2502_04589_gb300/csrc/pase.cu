@@ -243,6 +243,9 @@ static int autotune(pase_ctx* h) {
       PASE_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
       PASE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (h->opt.verbose >= 2)
+        fprintf(stderr, "[pase]   level %d candidate: %s bs %d psm %d items %d cw %d: %.4f ms\n", l,
+                cd.use ? "structured" : "CSR", cd.bs, cd.psm, cd.items, cd.cw, ms);
       if (ms < best) {
         best = ms;
         best_bs = cd.bs;
