@@ -1404,6 +1404,12 @@ size_t small_sygv_work_doubles(int n, int k) {
 int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,
                double* lam, double* C, int ldc, int* status_dev) {
   if (n <= 0 || k <= 0 || k > n || k > 1024) return fail(PASE_ERR_INVALID_ARG, "small_sygv: bad size");
+  // threads of the single-CTA stages (Cholesky, tridiagonalisation, multisection): the
+  // FP64 pipe of one SM bounds them, so fewer threads (cheaper barriers) can be faster;
+  // the autotuner picks per size, at least k (one multisection lane per eigenvalue)
+  int thr = 1024;
+  for (int i = 0; i < 3; ++i)
+    if (h->sygv_n[i] == n && h->sygv_thr[i] >= k) thr = h->sygv_thr[i];
   if (small_sygv_work_doubles(n, k) > h->w.eigwork_doubles)
     return fail(PASE_ERR_INVALID_ARG, "small_sygv: workspace too small");
   const size_t smem_tri = (size_t)(2 * n + 1024) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
@@ -1425,9 +1431,9 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   const size_t smem_tri_s = (tri + 2 * n) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   const bool packed = smem_tri_s <= 200 * 1024 && smem_chol_s <= 200 * 1024;
   if (packed)
-    k_sygv_chol_s<<<1, 1024, smem_chol_s, s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
+    k_sygv_chol_s<<<1, thr, smem_chol_s, s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   else
-    k_sygv_chol<<<1, 1024, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
+    k_sygv_chol<<<1, thr, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, status_dev);
   k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, status_dev);
   const size_t smem_c = tri_cluster_smem(n);
@@ -1435,12 +1441,12 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   if (n >= kTriClusterMin && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
     PASE_TRY(ensure_max_smem((const void*)k_sygv_tridiag_c, 200 * 1024));
     k_sygv_tridiag_c<<<kTriC, 256, smem_c, s>>>(n, k, w, status_dev);
-    k_sygv_multisect<<<1, 1024, smem_ms, s>>>(n, k, w, status_dev);
+    k_sygv_multisect<<<1, thr, smem_ms, s>>>(n, k, w, status_dev);
     h->launches++;
   } else if (packed) {
-    k_sygv_tridiag_s<<<1, 1024, smem_tri_s, s>>>(n, k, w, status_dev);
+    k_sygv_tridiag_s<<<1, thr, smem_tri_s, s>>>(n, k, w, status_dev);
   } else {
-    k_sygv_tridiag<<<1, 1024, smem_tri, s>>>(n, k, w, status_dev);
+    k_sygv_tridiag<<<1, thr, smem_tri, s>>>(n, k, w, status_dev);
   }
   k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
   k_sygv_back<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);

@@ -19,7 +19,9 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <array>
 #include <memory>
+#include <mutex>
 #include <thread>
 
 #include "pase_internal.h"
@@ -176,6 +178,70 @@ void prof_end(pase_ctx* h, int id) {
 }
 
 // ------------------------------------------------------------------ autotuner
+// Threads of the small eigensolver's single-CTA stages for the three sizes the step-(c)
+// block eigensolver uses (n = m, 2m, 3m; k = m): timed on a synthetic Gram pair at 256,
+// 512 and 1024 threads, once per (n, k) in the process.
+static int tune_sygv(pase_ctx* h) {
+  Work& w = h->w;
+  const int m = w.m, m3 = 3 * m;
+  const int64_t nc = h->NH + m;
+  if (w.aug_dense || nc < m3) return PASE_OK;  // the iterative step (c) does not run
+  static std::mutex mu;
+  static std::vector<std::array<int, 3>> cache;  // (n, k, threads)
+  PASE_TRY(launch_hash_fill(h, nc, m3, m3, 10u, w.S));
+  PASE_TRY(launch_hash_fill(h, nc, m3, m3, 11u, w.AS));
+  PASE_TRY(ts_gram(h, nc, m3, m3, w.AS, m3, w.AS, m3, w.Gq, m3, true));
+  PASE_TRY(ts_gram(h, nc, m3, m3, w.S, m3, w.S, m3, w.Gb, m3, true));
+  cudaEvent_t e0, e1;
+  PASE_CUDA(cudaEventCreate(&e0));
+  PASE_CUDA(cudaEventCreate(&e1));
+  int rc = PASE_OK;
+  for (int i = 0; i < 3 && rc == PASE_OK; ++i) {
+    const int n = (i + 1) * m;
+    h->sygv_n[i] = n;
+    int found = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (const auto& c : cache)
+        if (c[0] == n && c[1] == m) found = c[2];
+    }
+    if (found) {
+      h->sygv_thr[i] = found;
+      continue;
+    }
+    float best = 1e30f;
+    int best_thr = 1024;
+    for (int thr : {1024, 512, 256}) {
+      if (thr < m) continue;
+      h->sygv_thr[i] = thr;
+      for (int rep = 0; rep < 2 && rc == PASE_OK; ++rep) {
+        if (rep == 1) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? PASE_OK : PASE_ERR_CUDA;
+        for (int it = 0; it < 2 && rc == PASE_OK; ++it)
+          rc = small_sygv(h, n, m, w.Gq, m3, w.Gb, m3, w.smallvec, w.Cs, m, w.status);
+      }
+      if (rc != PASE_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = fail(PASE_ERR_CUDA, "tune_sygv: event timing failed");
+        break;
+      }
+      if (h->opt.verbose >= 2) fprintf(stderr, "[pase]   small eigensolver n %d: %d threads %.4f ms\n", n, thr, ms / 2);
+      if (ms < best) {
+        best = ms;
+        best_thr = thr;
+      }
+    }
+    h->sygv_thr[i] = best_thr;
+    if (h->opt.verbose) fprintf(stderr, "[pase] autotune small eigensolver n %d: %d threads\n", n, best_thr);
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back({n, m, best_thr});
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 // For every multigrid matrix, time the damped-Jacobi sweep (the precision the linear solve
 // runs in) under each candidate schedule and keep the fastest: the CSR kernel at 128, 256
 // and 512 threads per block and, for FP32 sweeps on a level the structured kernel serves,
@@ -267,7 +333,7 @@ static int autotune(pase_ctx* h) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->tuned_m = m;
-  return PASE_OK;
+  return tune_sygv(h);
 }
 
 // ------------------------------------------------------------------ workspace
