@@ -1120,7 +1120,7 @@ __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work,
 //     exchange.  d, e, tau and the reflectors go to the workspace exactly as in kernel 3;
 //     the eigenvalue brackets are computed afterwards by k_sygv_multisect.
 constexpr int kTriC = 8;
-constexpr int kTriClusterMin = 64;  // below this the single-CTA kernels are faster
+constexpr int kTriClusterMin = 64;  // default: below this the single-CTA kernels (the autotuner may choose)
 __host__ __device__ inline size_t tri_cluster_smem(int n) {
   const int rows = (n + kTriC - 1) / kTriC;
   return ((size_t)rows * n + 4 * (size_t)n + 4 * kTriC + 8) * sizeof(double);
@@ -1408,8 +1408,12 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   // FP64 pipe of one SM bounds them, so fewer threads (cheaper barriers) can be faster;
   // the autotuner picks per size, at least k (one multisection lane per eigenvalue)
   int thr = 1024;
+  bool cl = n >= kTriClusterMin;  // tridiagonalisation on a cluster of SMs
   for (int i = 0; i < 3; ++i)
-    if (h->sygv_n[i] == n && h->sygv_thr[i] >= k) thr = h->sygv_thr[i];
+    if (h->sygv_n[i] == n) {
+      if (h->sygv_thr[i] >= k) thr = h->sygv_thr[i];
+      if (h->sygv_cl[i] >= 0 && n >= 16) cl = h->sygv_cl[i] != 0;
+    }
   if (small_sygv_work_doubles(n, k) > h->w.eigwork_doubles)
     return fail(PASE_ERR_INVALID_ARG, "small_sygv: workspace too small");
   const size_t smem_tri = (size_t)(2 * n + 1024) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
@@ -1438,7 +1442,7 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, status_dev);
   const size_t smem_c = tri_cluster_smem(n);
   const size_t smem_ms = (size_t)1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
-  if (n >= kTriClusterMin && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
+  if (cl && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
     PASE_TRY(ensure_max_smem((const void*)k_sygv_tridiag_c, 200 * 1024));
     k_sygv_tridiag_c<<<kTriC, 256, smem_c, s>>>(n, k, w, status_dev);
     k_sygv_multisect<<<1, thr, smem_ms, s>>>(n, k, w, status_dev);

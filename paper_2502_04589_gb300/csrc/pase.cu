@@ -178,16 +178,17 @@ void prof_end(pase_ctx* h, int id) {
 }
 
 // ------------------------------------------------------------------ autotuner
-// Threads of the small eigensolver's single-CTA stages for the three sizes the step-(c)
-// block eigensolver uses (n = m, 2m, 3m; k = m): timed on a synthetic Gram pair at 256,
-// 512 and 1024 threads, once per (n, k) in the process.
+// Threads of the small eigensolver's single-CTA stages (256, 512 or 1024) and the form of
+// its tridiagonalisation (one CTA or a cluster of SMs) for the three sizes the step-(c)
+// block eigensolver uses (n = m, 2m, 3m; k = m): timed on a synthetic Gram pair, once per
+// (n, k) in the process.
 static int tune_sygv(pase_ctx* h) {
   Work& w = h->w;
   const int m = w.m, m3 = 3 * m;
   const int64_t nc = h->NH + m;
   if (w.aug_dense || nc < m3) return PASE_OK;  // the iterative step (c) does not run
   static std::mutex mu;
-  static std::vector<std::array<int, 3>> cache;  // (n, k, threads)
+  static std::vector<std::array<int, 4>> cache;  // (n, k, threads, cluster)
   PASE_TRY(launch_hash_fill(h, nc, m3, m3, 10u, w.S));
   PASE_TRY(launch_hash_fill(h, nc, m3, m3, 11u, w.AS));
   PASE_TRY(ts_gram(h, nc, m3, m3, w.AS, m3, w.AS, m3, w.Gq, m3, true));
@@ -199,21 +200,28 @@ static int tune_sygv(pase_ctx* h) {
   for (int i = 0; i < 3 && rc == PASE_OK; ++i) {
     const int n = (i + 1) * m;
     h->sygv_n[i] = n;
-    int found = 0;
+    int found = 0, found_cl = -1;
     {
       std::lock_guard<std::mutex> lk(mu);
       for (const auto& c : cache)
-        if (c[0] == n && c[1] == m) found = c[2];
+        if (c[0] == n && c[1] == m) {
+          found = c[2];
+          found_cl = c[3];
+        }
     }
     if (found) {
       h->sygv_thr[i] = found;
+      h->sygv_cl[i] = found_cl;
       continue;
     }
     float best = 1e30f;
-    int best_thr = 1024;
-    for (int thr : {1024, 512, 256}) {
-      if (thr < m) continue;
+    int best_thr = 1024, best_cl = -1;
+    for (int cand = 0; cand < 6; ++cand) {
+      const int thr = (cand % 3 == 0) ? 1024 : (cand % 3 == 1 ? 512 : 256);
+      const int cl = cand / 3;
+      if (thr < m || (cl && n < 16)) continue;
       h->sygv_thr[i] = thr;
+      h->sygv_cl[i] = cl;
       for (int rep = 0; rep < 2 && rc == PASE_OK; ++rep) {
         if (rep == 1) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? PASE_OK : PASE_ERR_CUDA;
         for (int it = 0; it < 2 && rc == PASE_OK; ++it)
@@ -226,16 +234,22 @@ static int tune_sygv(pase_ctx* h) {
         rc = fail(PASE_ERR_CUDA, "tune_sygv: event timing failed");
         break;
       }
-      if (h->opt.verbose >= 2) fprintf(stderr, "[pase]   small eigensolver n %d: %d threads %.4f ms\n", n, thr, ms / 2);
+      if (h->opt.verbose >= 2)
+        fprintf(stderr, "[pase]   small eigensolver n %d: %d threads, %s tridiagonalisation %.4f ms\n", n, thr,
+                cl ? "cluster" : "one-CTA", ms / 2);
       if (ms < best) {
         best = ms;
         best_thr = thr;
+        best_cl = cl;
       }
     }
     h->sygv_thr[i] = best_thr;
-    if (h->opt.verbose) fprintf(stderr, "[pase] autotune small eigensolver n %d: %d threads\n", n, best_thr);
+    h->sygv_cl[i] = best_cl;
+    if (h->opt.verbose)
+      fprintf(stderr, "[pase] autotune small eigensolver n %d: %d threads, %s tridiagonalisation\n", n, best_thr,
+              best_cl ? "cluster" : "one-CTA");
     std::lock_guard<std::mutex> lk(mu);
-    cache.push_back({n, m, best_thr});
+    cache.push_back({n, m, best_thr, best_cl});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -288,7 +288,9 @@ struct pase_ctx {
   std::vector<cudaStream_t> cap_streams;
   int64_t body_kernels[pase::kCtlSlots] = {};  // kernels of the body that owns each slot
   int ci_last[pase::kCtlSlots] = {};           // execution counts at the last read
-  int sygv_n[3] = {0, 0, 0}, sygv_thr[3] = {1024, 1024, 1024};  // tuned threads of the small eigensolver
+  // tuned small eigensolver per Rayleigh-Ritz size: threads of its single-CTA stages, and
+  // whether the tridiagonalisation runs on a cluster (-1: by size)
+  int sygv_n[3] = {0, 0, 0}, sygv_thr[3] = {1024, 1024, 1024}, sygv_cl[3] = {-1, -1, -1};
   int64_t graph_launches = 0;                  // CUDA graph launches issued
   int64_t replayed = 0;                        // kernels (of `launches`) run inside graph replays
   uint64_t serial = 0;                         // unique id of the handle (batch graph keys)
