@@ -514,39 +514,49 @@ __global__ void __launch_bounds__(1024) k_sygv_chol(int n, int k, const double* 
 // 2. out[c-th vector] = L^-1 in[c-th vector], one CTA per vector.  pass 0: input row c of
 //    K (= column c, K symmetric), output column c of Y; pass 1: input row c of Y, output
 //    row c of K (K <- L^-1 K L^-T since K' = (L^-1 Y^T)^T and K' is symmetric).
-__global__ void __launch_bounds__(128) k_sygv_trsm(int n, int k, double* work, int pass, int stage_l,
+__global__ void __launch_bounds__(128) k_sygv_trsm(int n, int k, double* work, int pass, int stage_l, int cpc,
                                                    const int* status) {
+  // the four warps stage the right-hand sides, the reciprocal pivots and (stage_l) the
+  // packed L in shared memory; warps 0..cpc-1 then each run one column's n dependent
+  // substitution steps with shuffles only (no block barrier in the loop).  cpc columns per
+  // CTA keep the grid within one wave of the SMs.
   if (status[0] != 0) return;
-  extern __shared__ double sy[];  // n solution entries, 4 warp partials, [packed L]
-  double* red = sy + n;
-  double* Lp = red + 8;           // row i of L at Lp + i(i+1)/2 when staged
+  extern __shared__ double sy[];  // per column: n solution and n right-hand side entries; n reciprocal pivots; [packed L]
+  double* rinv = sy + (size_t)2 * cpc * n;
+  double* Lp = rinv + n;          // row i of L at Lp + i(i+1)/2 when staged
   SygvWork W = sygv_work(work, n, k);
-  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* in = (pass == 0) ? W.K + (int64_t)c * n : W.Y + (int64_t)c * n;
-  if (stage_l) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = blockIdx.x * cpc;
+  for (int q = 0; q < cpc && c0 + q < n; ++q) {
+    const double* in = (pass == 0) ? W.K + (int64_t)(c0 + q) * n : W.Y + (int64_t)(c0 + q) * n;
+    for (int i = tid; i < n; i += blockDim.x) sy[(size_t)(2 * q + 1) * n + i] = in[i];
+  }
+  for (int i = tid; i < n; i += blockDim.x) rinv[i] = 1.0 / W.L[(int64_t)i * n + i];
+  if (stage_l)
     for (int i = warp; i < n; i += (int)(blockDim.x >> 5))
       for (int l = lane; l <= i; l += 32) Lp[i * (i + 1) / 2 + l] = W.L[(int64_t)i * n + l];
-    __syncthreads();
-  }
+  __syncthreads();
+  const int c = c0 + warp;
+  if (warp >= cpc || c >= n) return;
+  double* x = sy + (size_t)2 * warp * n;
+  double* rhs = x + n;
+  // column-oriented substitution: lane r % 32 owns row r of the right-hand side; step i
+  // computes x_i on its owner lane, broadcasts it, and every lane takes L[r][i] x_i off
+  // its rows r > i, so the dependent chain of a step is one multiply, one shuffle and one
+  // FMA (no reduction)
   for (int i = 0; i < n; ++i) {
-    const double* Li = stage_l ? Lp + i * (i + 1) / 2 : W.L + (int64_t)i * n;
-    double acc = 0.0;
-    for (int l = tid; l < i; l += blockDim.x) acc = fma(Li[l], sy[l], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      sy[i] = (in[i] - t) / Li[i];
+    const double xi = __shfl_sync(0xffffffffu, rhs[i] * rinv[i], i & 31);
+    if (lane == (i & 31)) x[i] = xi;
+    for (int r = i + 1 + ((lane - (i + 1)) & 31); r < n; r += 32) {
+      const double lri = stage_l ? Lp[r * (r + 1) / 2 + i] : W.L[(int64_t)r * n + i];
+      rhs[r] = fma(-lri, xi, rhs[r]);
     }
-    __syncthreads();
   }
+  __syncwarp();
   if (pass == 0)
-    for (int i = tid; i < n; i += blockDim.x) W.Y[(int64_t)i * n + c] = sy[i];
+    for (int i = lane; i < n; i += 32) W.Y[(int64_t)i * n + c] = x[i];
   else
-    for (int i = tid; i < n; i += blockDim.x) W.K[(int64_t)c * n + i] = sy[i];
+    for (int i = lane; i < n; i += 32) W.K[(int64_t)c * n + i] = x[i];
 }
 
 // 3. Householder tridiagonalisation and FP32 multisection (one CTA of 1024 threads).
@@ -1331,34 +1341,36 @@ __global__ void __launch_bounds__(1024) k_sygv_multisect(int n, int k, double* w
   if (tid == 0) W.lamx[k] = fmax(fabs(s_lo), fabs(s_hi));  // |T| bound
 }
 
-// 5. back-transform: each warp takes one column of Z through z <- H_0 ... H_{n-3} z,
-//    then c = D L^-T z.
-constexpr int kBtWarps = 8;  // columns (one warp each) per CTA of the back-transform
-__global__ void __launch_bounds__(kBtWarps * 32) k_sygv_back(int n, int k, double* work, double* __restrict__ C,
-                                                             int ldc, int stage, const int* status) {
-  // one warp per eigenvector column: the reflector sweep and the triangular solve are
-  // sequences of n dependent steps, each a dot product and an update over one column, so
-  // a warp runs them with shuffles and no block barrier
+// 5. back-transform: one CTA per column of Z; its four warps stage the reflectors (then
+//    L) in shared memory and warp 0 takes the column through z <- H_0 ... H_{n-3} z, then
+//    c = D L^-T z.  One column per CTA spreads the FP64 work of the k columns over k SMs.
+constexpr int kBtThreads = 128;
+__global__ void __launch_bounds__(kBtThreads) k_sygv_back(int n, int k, double* work, double* __restrict__ C,
+                                                         int ldc, int stage, const int* status) {
+  // the reflector sweep and the triangular solve are sequences of n dependent steps, each
+  // a dot product and an update over one column: one warp runs them with shuffles
   if (status[0] != 0) return;
-  extern __shared__ double zc[];  // kBtWarps * n, then [packed reflectors | packed L]
+  extern __shared__ double zc[];  // z [n], reciprocal pivots [n], then [packed reflectors | packed L]
   SygvWork W = sygv_work(work, n, k);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* pk = zc + kBtWarps * n;
-  const int col = blockIdx.x * kBtWarps + warp;
-  const bool have = col < k;
-  double* z = zc + warp * n;
-  if (have)
-    for (int r = lane; r < n; r += 32) z[r] = W.Z[(int64_t)r * k + col];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  double* z = zc;
+  double* rinv = zc + n;
+  double* pk = zc + 2 * n;
+  const int col = blockIdx.x;
+  for (int r = tid; r < n; r += blockDim.x) {
+    z[r] = W.Z[(int64_t)r * k + col];
+    rinv[r] = 1.0 / W.L[(int64_t)r * n + r];
+  }
   // reflector j (rows j+1..n-1): v[0] = 1, v[r] = K[j][j+1+r] for r >= 1, packed at
   // pk + off(j), off(j) = j(n-2) - j(j-1)/2, n-j-2 entries
   if (stage) {
-    for (int j = warp; j + 2 < n; j += kBtWarps) {
+    for (int j = warp; j + 2 < n; j += nwarps) {
       const int off = j * (n - 2) - j * (j - 1) / 2;
       for (int r = lane; r < n - j - 2; r += 32) pk[off + r] = W.K[(int64_t)j * n + (j + 2 + r)];
     }
   }
   __syncthreads();
-  if (have) {
+  if (warp == 0) {
     for (int j = n - 3; j >= 0; --j) {
       const double t = W.tau[j];
       if (t == 0.0) continue;
@@ -1376,24 +1388,24 @@ __global__ void __launch_bounds__(kBtWarps * 32) k_sygv_back(int n, int k, doubl
   // L^T x = z, rows from the bottom (column i of L = L[l][i], l > i); L packed by rows,
   // row l at off(l) = l(l+1)/2, when staged
   if (stage) {
-    __syncthreads();  // every warp is done with the reflectors
-    for (int l = warp; l < n; l += kBtWarps)
+    __syncthreads();  // the reflector sweep is done
+    for (int l = warp; l < n; l += nwarps)
       for (int c = lane; c <= l; c += 32) pk[l * (l + 1) / 2 + c] = W.L[(int64_t)l * n + c];
     __syncthreads();
   }
-  if (!have) return;
+  if (warp != 0) return;
+  __syncwarp();
+  // column-oriented back substitution: lane l % 32 owns z[l]; step i takes x_i = z_i / L_ii
+  // on its owner lane, broadcasts it, and every lane takes L[i][l] x_i off its rows l < i
   for (int i = n - 1; i >= 0; --i) {
-    double acc = 0.0;
-    for (int l = i + 1 + lane; l < n; l += 32)
-      acc = fma(stage ? pk[l * (l + 1) / 2 + i] : W.L[(int64_t)l * n + i], z[l], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const double lii = stage ? pk[i * (i + 1) / 2 + i] : W.L[(int64_t)i * n + i];
-      z[i] = (z[i] - acc) / lii;
+    const double xi = __shfl_sync(0xffffffffu, z[i] * rinv[i], i & 31);
+    if (lane == (i & 31)) z[i] = xi;
+    for (int l = lane; l < i; l += 32) {
+      const double lil = stage ? pk[i * (i + 1) / 2 + l] : W.L[(int64_t)i * n + l];
+      z[l] = fma(-lil, xi, z[l]);
     }
-    __syncwarp();
   }
+  __syncwarp();
   for (int r = lane; r < n; r += 32) C[(int64_t)r * ldc + col] = W.sc[r] * z[r];
 }
 
@@ -1425,12 +1437,15 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   double* w = h->w.eigwork;
   auto s = h->stream;
   const size_t tri = (size_t)n * (n + 1) / 2;
-  const size_t smem_trsm_st = (size_t)(n + 8 + tri) * sizeof(double);
+  // columns per CTA of the triangular solves: one wave of the SMs (at most 4, one warp each)
+  const int cpc = std::min(4, std::max(1, (n + h->num_sms - 1) / h->num_sms));
+  const int trsm_grid = (n + cpc - 1) / cpc;
+  const size_t smem_trsm_st = (size_t)((2 * cpc + 1) * n + tri) * sizeof(double);
   const int stage_l = smem_trsm_st <= 200 * 1024 ? 1 : 0;
-  const size_t smem_trsm = stage_l ? smem_trsm_st : (size_t)(n + 8) * sizeof(double);
-  const size_t smem_back_st = (size_t)(kBtWarps * n + tri) * sizeof(double);
+  const size_t smem_trsm = stage_l ? smem_trsm_st : (size_t)((2 * cpc + 1) * n) * sizeof(double);
+  const size_t smem_back_st = (size_t)(2 * n + tri) * sizeof(double);
   const int stage_b = smem_back_st <= 200 * 1024 ? 1 : 0;
-  const size_t smem_back = stage_b ? smem_back_st : (size_t)kBtWarps * n * sizeof(double);
+  const size_t smem_back = stage_b ? smem_back_st : (size_t)2 * n * sizeof(double);
   const size_t smem_chol_s = (tri + n) * sizeof(double);
   const size_t smem_tri_s = (tri + 2 * n) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   const bool packed = smem_tri_s <= 200 * 1024 && smem_chol_s <= 200 * 1024;
@@ -1438,8 +1453,8 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     k_sygv_chol_s<<<1, thr, smem_chol_s, s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   else
     k_sygv_chol<<<1, thr, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
-  k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, status_dev);
-  k_sygv_trsm<<<n, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, status_dev);
+  k_sygv_trsm<<<trsm_grid, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, cpc, status_dev);
+  k_sygv_trsm<<<trsm_grid, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, cpc, status_dev);
   const size_t smem_c = tri_cluster_smem(n);
   const size_t smem_ms = (size_t)1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   if (cl && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
@@ -1453,7 +1468,7 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
     k_sygv_tridiag<<<1, thr, smem_tri, s>>>(n, k, w, status_dev);
   }
   k_sygv_inviter<<<k, 32, (size_t)inviter_lanes(n) * (4 * n + 1) * sizeof(double), s>>>(n, k, w, lam, status_dev);
-  k_sygv_back<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
+  k_sygv_back<<<k, kBtThreads, smem_back, s>>>(n, k, w, C, ldc, stage_b, status_dev);
   h->launches += 6;
   PASE_CUDA(cudaGetLastError());
   return PASE_OK;
