@@ -78,7 +78,10 @@ typedef struct {
   int max_iter;        /* outer iterations (default 100)                                       */
   int aug_max_iter;    /* inner iterations of the step-(c) block eigensolver (default 60)      */
   double aug_tol;      /* inner relative residual target (default 1e-12)                       */
-  int aug_adaptive;    /* 1 (default): inner target max(aug_tol, 1e-3 x current outer residual);
+  int aug_adaptive;    /* 1 (default): inner target max(aug_tol, f x current outer residual),
+                          f = aug_factor, made ten times smaller after an iteration whose
+                          residual rose (down to aug_factor / 1000) and ten times larger
+                          after one that cut it by more than five (up to aug_factor);      
                           0: always aug_tol                                                     */
   int verbose;         /* 0 silent, 1 per-iteration line on stderr, 2 also inner iterations    */
   int use_graphs;      /* 1 (default): inside pase_solve the step-(a) linear solve is captured
@@ -133,6 +136,7 @@ typedef struct {
                           (default) the autotuner's choice (4 without it), or 2 / 4 fixed;
                           2 runs twice the threads at half the registers (block widths up
                           to 60)                                                          */
+  double aug_factor;   /* the adaptive inner target's factor (default 1e-4), in (0, 1]      */
 } pase_options;
 
 /* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the

@@ -51,11 +51,12 @@ __global__ void k_ctl_put(int* pi, int vi, int add, double* pd, double vd) {
 }
 
 // Outer stopping test (§6: every one of the first nev pairs at relative residual <= tol)
-// and the inner tolerance of the next step (c).  A pending error or a finite-range flag
+// and the inner tolerance of the next step (c): max(aug_tol, f x worst residual), f the
+// adaptive factor.  A pending error or a finite-range flag
 // of the double-float products stops the loop too.
 __global__ void k_ctl_outer_check(int nev, const double* __restrict__ relres, double tol, double aug_tol,
-                                  int adaptive, int max_iter, int post_solve, const int* __restrict__ df_flag,
-                                  int* __restrict__ ci, double* __restrict__ cd) {
+                                  int adaptive, double factor, int max_iter, int post_solve,
+                                  const int* __restrict__ df_flag, int* __restrict__ ci, double* __restrict__ cd) {
   double worst = 0.0;
   int conv = 0;
   bool nan = false;
@@ -80,17 +81,31 @@ __global__ void k_ctl_outer_check(int nev, const double* __restrict__ relres, do
     if (it >= max_iter) ci[CI_MAXED] = 1;
     else go = 1;
   }
-  if (go) cd[CD_AUG_TOL] = adaptive ? fmax(aug_tol, 1e-3 * worst) : aug_tol;
+  if (go && adaptive) {
+    // safeguarded factor: a pass whose residual rose above the previous one tightens it
+    // tenfold (down to 1e-3 of the base); a drop by more than five relaxes it tenfold (up
+    // to the base)
+    double f = cd[CD_FACTOR] > 0.0 ? cd[CD_FACTOR] : factor;
+    const double prev = cd[CD_PREV_WORST];
+    if (prev > 0.0 && worst > prev) f = fmax(0.1 * f, 1e-3 * factor);
+    else if (prev > 0.0 && worst < 0.2 * prev) f = fmin(10.0 * f, factor);
+    cd[CD_FACTOR] = f;
+    cd[CD_AUG_TOL] = fmax(aug_tol, f * worst);
+  } else if (go) {
+    cd[CD_AUG_TOL] = aug_tol;
+  }
+  if (!nan) cd[CD_PREV_WORST] = worst;
   ci[CI_OUT_GO] = go;
   ci[CI_OUT_CONT] = go;
   ci[CI_POST] = go && post_solve && it > 0;
 }
 
 // inner tolerance from the current residuals (the adaptive rule of the outer test)
-__global__ void k_ctl_aug_tol(int nev, const double* __restrict__ relres, double aug_tol, double* __restrict__ cd) {
+__global__ void k_ctl_aug_tol(int nev, const double* __restrict__ relres, double aug_tol, double factor,
+                              double* __restrict__ cd) {
   double worst = 0.0;
   for (int j = 0; j < nev; ++j) worst = fmax(worst, relres[j]);
-  cd[CD_AUG_TOL] = fmax(aug_tol, 1e-3 * worst);
+  cd[CD_AUG_TOL] = fmax(aug_tol, factor * worst);
 }
 
 __global__ void k_ctl_inner_init(int* __restrict__ ci) {
@@ -160,12 +175,12 @@ int launch_ctl_put(pase_ctx* h, int* pi, int vi, bool add, double* pd, double vd
 }
 int launch_ctl_outer_check(pase_ctx* h, int nev, double tol) {
   const pase_options& o = h->opt;
-  k_ctl_outer_check<<<1, 1, 0, h->stream>>>(nev, h->w.relres, tol, o.aug_tol, o.aug_adaptive, o.max_iter,
-                                            o.post_solve, h->w.df_flag, h->w.ci, h->w.cd);
+  k_ctl_outer_check<<<1, 1, 0, h->stream>>>(nev, h->w.relres, tol, o.aug_tol, o.aug_adaptive, o.aug_factor,
+                                            o.max_iter, o.post_solve, h->w.df_flag, h->w.ci, h->w.cd);
   return launched(h);
 }
 int launch_ctl_aug_tol(pase_ctx* h, int nev) {
-  k_ctl_aug_tol<<<1, 1, 0, h->stream>>>(nev, h->w.relres, h->opt.aug_tol, h->w.cd);
+  k_ctl_aug_tol<<<1, 1, 0, h->stream>>>(nev, h->w.relres, h->opt.aug_tol, h->opt.aug_factor, h->w.cd);
   return launched(h);
 }
 int launch_ctl_inner_init(pase_ctx* h) {

@@ -1602,6 +1602,7 @@ void pase_default_options(pase_options* o) {
   o->aug_transform = PASE_AUG_PLAIN;
   o->spmm_df64 = 1;
   o->graph_solve = 0;
+  o->aug_factor = 1e-4;
 }
 
 const char* pase_status_string(int code) {
@@ -1637,7 +1638,7 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
       (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
       (o.post_solve != 0 && o.post_solve != 1) || (o.graph_solve != 0 && o.graph_solve != 1) ||
       (o.stencil_columns != 0 && o.stencil_columns != 2 && o.stencil_columns != 4) ||
-      o.graph_pass_limit < 0 ||
+      o.graph_pass_limit < 0 || !(o.aug_factor > 0.0 && o.aug_factor <= 1.0) ||
       o.aug_transform < PASE_AUG_PLAIN ||
       o.aug_transform > PASE_AUG_PRECOND_BA ||
       o.nu2 < 0 || !(o.omega > 0.0 && o.omega < 2.0) || o.max_iter < 1 || o.aug_max_iter < 1 ||

@@ -159,7 +159,7 @@ enum CtlInt {
   CI_MAXED,      // max_iter reached without convergence
   CI_EXEC0 = 16,
 };
-enum CtlDbl { CD_WORST = 0, CD_AUG_TOL, CD_IN_WORST, CD_HIST = 8, CD_COUNT = 16 };
+enum CtlDbl { CD_WORST = 0, CD_AUG_TOL, CD_IN_WORST, CD_PREV_WORST, CD_FACTOR, CD_HIST = 8, CD_COUNT = 16 };
 constexpr int kCtlHist = 8;                       // ring of inner residuals (stagnation test)
 constexpr int kCtlSlots = 240;                    // conditional bodies with a counter
 constexpr int CI_GUARD0 = CI_EXEC0 + kCtlSlots;  // pass guards of the WHILE nodes, one per slot
