@@ -137,6 +137,14 @@ typedef struct {
                           2 runs twice the threads at half the registers (block widths up
                           to 60)                                                          */
   double aug_factor;   /* the adaptive inner target's factor (default 1e-4), in (0, 1]      */
+  int sygv_tridiag;    /* form of the small eigensolver's Householder tridiagonalisation:
+                          -1 (default) the autotuner's choice per Rayleigh-Ritz size (without
+                          it: one CTA below n = 64, else a cluster of 8 SMs); 0 one CTA;
+                          1 a cluster of 8 SMs; 2 a cluster of 16 SMs (8 where the device
+                          cannot schedule 16); cluster forms apply from n = 16           */
+  int sygv_cholesky;   /* form of its Cholesky factorisation of the Gram matrix: -1 (default)
+                          the autotuner's choice (without it: as sygv_tridiag's default);
+                          0 one CTA; 1 a cluster of 8 SMs (from n = 16)                  */
 } pase_options;
 
 /* Step-(c) variants (§4, Alg. 5).  Each solves the same augmented eigenproblem through the

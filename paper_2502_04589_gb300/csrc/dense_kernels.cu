@@ -10,6 +10,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pase_internal.h"
 
@@ -1122,22 +1123,26 @@ __global__ void __launch_bounds__(32) k_sygv_inviter(int n, int k, double* work,
 
 // 3b. Householder tridiagonalisation on a thread-block cluster of kTriC CTAs (one SM
 //     each): CTA c keeps the full rows r = c, c + kTriC, ... of the symmetric matrix in
-//     its shared memory.  Step j: the owner of row j forms the reflector (as kernel 3) and
-//     writes it into every CTA's shared memory; each CTA computes p = t A22 v for its own
-//     rows and writes those entries (and its share of p.v) into every CTA; every CTA then
-//     applies the rank-2 update to its own rows.  Reflector, p and partial sums are double
-//     buffered by step parity, so two hardware cluster barriers per step order the
-//     exchange.  d, e, tau and the reflectors go to the workspace exactly as in kernel 3;
-//     the eigenvalue brackets are computed afterwards by k_sygv_multisect.
+//     its shared memory.  Step j: each CTA computes p = t A22 v for its own rows and
+//     writes those entries (and its share of p.v) into every CTA (one cluster barrier);
+//     every CTA then applies the rank-2 update to its own rows, the owner of row j+1 that
+//     row first, from which it forms reflector j+1 (as kernel 3) and writes it into every
+//     CTA before arriving on a split cluster barrier; the other rows' updates run before
+//     the wait.  Reflector, p and partial sums are double buffered by step parity.  d, e,
+//     tau and the reflectors go to the workspace exactly as in kernel 3; the eigenvalue
+//     brackets are computed afterwards by k_sygv_multisect.
+//     The cluster has kTriC CTAs (portable size) or 2 kTriC (a non-portable size, where
+//     the part can schedule it); the launch sets the cluster shape.
 constexpr int kTriC = 8;
 constexpr int kTriClusterMin = 64;  // default: below this the single-CTA kernels (the autotuner may choose)
-__host__ __device__ inline size_t tri_cluster_smem(int n) {
-  const int rows = (n + kTriC - 1) / kTriC;
-  return ((size_t)rows * n + 4 * (size_t)n + 4 * kTriC + 8) * sizeof(double);
+__host__ __device__ inline size_t tri_cluster_smem(int n, int C) {
+  const int rows = (n + C - 1) / C;
+  return ((size_t)rows * n + 4 * (size_t)n + 4 * C + 8) * sizeof(double);
 }
 
-__global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
-    k_sygv_tridiag_c(int n, int k, double* work, const int* status) {
+template <int C>
+__global__ void __launch_bounds__(256) k_sygv_tridiag_c(int n, int k, double* work, const int* status) {
+  constexpr int kTriC = C;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   if (status[0] != 0) return;  // uniform over the cluster (written by an earlier kernel)
@@ -1182,6 +1187,53 @@ __global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
     }
   }
   cluster.sync();  // the drop mask in tau is read above and overwritten below
+  // reflector j from row j (kernel 3's form), written into every CTA with its t and beta;
+  // a step of the whole owner CTA
+  __shared__ double s_hh[3];
+  auto reflector = [&](int j) {
+    const int par = j & 1;
+    const int len = n - j - 1, j1 = j + 1;
+    double* v = vb + par * n;
+    double* sc = scal + par * 2;
+    const double* x = Arow + (size_t)(j / kTriC) * n + j1;
+    double ps = 0.0;
+    for (int r = 1 + tid; r < len; r += nt) ps += x[r] * x[r];
+    const double sig = block_sum(ps, red);
+    if (tid == 0) {
+      const double x0 = x[0];
+      double beta = x0, t = 0.0, sl = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(x0 * x0 + sig);
+        beta = (x0 >= 0.0) ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        sl = 1.0 / (x0 - beta);
+      }
+      s_hh[0] = beta;
+      s_hh[1] = t;
+      s_hh[2] = sl;
+      W.d[j] = Arow[(size_t)(j / kTriC) * n + j];
+      W.e[j] = beta;
+      W.tau[j] = t;
+    }
+    __syncthreads();
+    const double t = s_hh[1], sl = s_hh[2];
+    for (int r = tid; r < len; r += nt) {
+      const double vr = (r == 0) ? 1.0 : x[r] * sl;
+      if (r >= 1) W.K[(int64_t)j * n + (j1 + r)] = vr;  // reflector store
+      for (int q = 0; q < kTriC; ++q) *cluster.map_shared_rank(v + r, q) = vr;
+    }
+    if (tid < kTriC) {
+      *cluster.map_shared_rank(sc, tid) = t;
+      *cluster.map_shared_rank(sc + 1, tid) = s_hh[0];
+    }
+  };
+  if (rank == 0 && n > 2) reflector(0);
+  cluster.sync();
+  // Step j: p = t A22 v and p.v over the cluster (one barrier); then the owner of row j+1
+  // applies the rank-2 update to that row alone, forms reflector j+1 and arrives on the
+  // split cluster barrier while every CTA applies the update to its other rows, so the
+  // reflector's exchange overlaps the update.  v, p and the partial sums are double
+  // buffered by step parity.
   for (int j = 0; j + 2 < n; ++j) {
     const int par = j & 1;
     const int len = n - j - 1, j1 = j + 1;
@@ -1189,41 +1241,6 @@ __global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
     double* pp = pb + par * n;
     double* pt = part + par * kTriC;
     double* sc = scal + par * 2;
-    if (j % kTriC == rank) {  // owner of row j: the reflector
-      const double* x = Arow + (size_t)(j / kTriC) * n + j1;
-      double ps = 0.0;
-      for (int r = 1 + tid; r < len; r += nt) ps += x[r] * x[r];
-      const double sig = block_sum(ps, red);
-      __shared__ double s_hh[3];
-      if (tid == 0) {
-        const double x0 = x[0];
-        double beta = x0, t = 0.0, sl = 0.0;
-        if (sig != 0.0) {
-          const double nrm = sqrt(x0 * x0 + sig);
-          beta = (x0 >= 0.0) ? -nrm : nrm;
-          t = (beta - x0) / beta;
-          sl = 1.0 / (x0 - beta);
-        }
-        s_hh[0] = beta;
-        s_hh[1] = t;
-        s_hh[2] = sl;
-        W.d[j] = Arow[(size_t)(j / kTriC) * n + j];
-        W.e[j] = beta;
-        W.tau[j] = t;
-      }
-      __syncthreads();
-      const double t = s_hh[1], sl = s_hh[2];
-      for (int r = tid; r < len; r += nt) {
-        const double vr = (r == 0) ? 1.0 : x[r] * sl;
-        if (r >= 1) W.K[(int64_t)j * n + (j1 + r)] = vr;  // reflector store
-        for (int q = 0; q < kTriC; ++q) *cluster.map_shared_rank(v + r, q) = vr;
-      }
-      if (tid < kTriC) {
-        *cluster.map_shared_rank(sc, tid) = t;
-        *cluster.map_shared_rank(sc + 1, tid) = s_hh[0];
-      }
-    }
-    cluster.sync();
     const double t = sc[0];
     if (t != 0.0) {
       // p = t A22 v for this CTA's rows R >= j1; share of p.v
@@ -1244,21 +1261,35 @@ __global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
       if (tid < kTriC) *cluster.map_shared_rank(pt + rank, tid) = pvs;
     }
     cluster.sync();
+    const bool next = j + 3 < n;                              // a reflector j+1 follows
+    const bool owner_next = next && (j1 % kTriC == rank);     // this CTA forms it
     if (t != 0.0) {
       double pv = 0.0;
       for (int q = 0; q < kTriC; ++q) pv += pt[q];
       const double Kc = 0.5 * t * pv;
       for (int r = tid; r < len; r += nt) pp[r] -= Kc * v[r];
       __syncthreads();
+      if (owner_next) {  // row j+1 first
+        double* row = Arow + (size_t)(j1 / kTriC) * n + j1;
+        const double vR = v[0], pR = pp[0];
+        for (int c = tid; c < len; c += nt) row[c] -= vR * pp[c] + pR * v[c];
+        __syncthreads();
+      }
+    }
+    if (owner_next) reflector(j1);
+    if (next) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+    if (t != 0.0) {
       const int lr0 = (j1 - rank + kTriC - 1) / kTriC;
       for (int lr = lr0 + warp; lr < nrows; lr += nwarps) {
         const int R = lr * kTriC + rank;
+        if (owner_next && R == j1) continue;  // done above
         double* row = Arow + (size_t)lr * n + j1;
         const double vR = v[R - j1], pR = pp[R - j1];
         for (int c = lane; c < len; c += 32) row[c] -= vR * pp[c] + pR * v[c];
       }
     }
-    __syncthreads();
+    __syncthreads();  // own rows complete before the next step's products read them
+    if (next) asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
   }
   // the trailing 2 x 2 block
   if (tid == 0) {
@@ -1271,6 +1302,139 @@ __global__ void __cluster_dims__(kTriC, 1, 1) __launch_bounds__(256)
       W.d[n - 1] = Arow[(size_t)((n - 1) / kTriC) * n + (n - 1)];
       W.e[n - 1] = 0.0;
       W.tau[n - 1] = 0.0;
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still address its shared memory
+}
+
+// 1c. Scaling + Cholesky with dropping (the result of kernel 1) on a thread-block cluster
+//     of C CTAs (one SM each, launch-set cluster shape): CTA c keeps the lower parts of rows
+//     r = c, c + C, ... in shared memory.  Step j (right-looking, unscaled: a_rc -= a_rj
+//     a_cj / d_j over j < c <= r, d_j the pivot): every CTA first updates column j+1 of its
+//     own rows and writes those entries (and, on the owner of row j+1, the next pivot's
+//     reciprocal) into every CTA, arrives on the cluster barrier, applies the rest of the
+//     step to its own rows, and waits; so the barrier's latency hides behind the update.
+//     Columns rotate through three buffers, which keeps a fast CTA's writes off a buffer
+//     a slow one still reads.  L = a_rj / sqrt(d_j) is formed once at the end.  The drop
+//     rule, outputs and status are those of kernel 1.
+__host__ __device__ inline size_t chol_cluster_smem(int n, int C) {
+  const int rows = (n + C - 1) / C;
+  return ((size_t)rows * n + 7 * (size_t)n + 4) * sizeof(double);
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_sygv_chol_c(int n, int k, const double* __restrict__ GA, int lda,
+                                                     const double* __restrict__ GB, int ldb, double* work,
+                                                     int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double smh[];
+  __shared__ int s_fail;
+  SygvWork W = sygv_work(work, n, k);
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  const int nrows = (n - rank + C - 1) / C;  // rows owned by this CTA
+  double* Ar = smh;                                      // [rows][n], lower parts
+  double* cb = Ar + (size_t)((n + C - 1) / C) * n;       // [3][n] column j (unscaled)
+  double* sc = cb + 3 * (size_t)n;                       // [n] diagonal scaling
+  double* piv = sc + n;                                  // [n] pivots d_j
+  double* sq = piv + n;                                  // [n] sqrt(d_j) (1 if dropped)
+  double* rs = sq + n;                                   // [n] 1 / sqrt(d_j) (0 if dropped)
+  double* rdb = rs + n;                                  // [3] 1 / d_j (0 if dropped)
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {  // every CTA checks every pivot, so all leave together
+    const double g = GB[(int64_t)i * ldb + i];
+    if (!(g >= 0.0) || !isfinite(g)) s_fail = 1;
+    sc[i] = (g > 0.0) ? rsqrt(g) : 0.0;
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (rank == 0 && tid == 0) status[0] = 1;
+    return;
+  }
+  if (rank == 0)
+    for (int i = tid; i < n; i += nt) W.sc[i] = sc[i];
+  for (int lr = warp; lr < nrows; lr += nwarps) {
+    const int r = lr * C + rank;
+    for (int c = lane; c < n; c += 32) {
+      const double t = sc[r] * sc[c];
+      W.K[(int64_t)r * n + c] = t * 0.5 * (GA[(int64_t)r * lda + c] + GA[(int64_t)c * lda + r]);
+      if (c <= r) Ar[(size_t)lr * n + c] = t * 0.5 * (GB[(int64_t)r * ldb + c] + GB[(int64_t)c * ldb + r]);
+    }
+  }
+  __syncthreads();
+  for (int lr = tid; lr < nrows; lr += nt) {  // column 0 and the first pivot to every CTA
+    const int r = lr * C + rank;
+    const double v = Ar[(size_t)lr * n];
+    for (int q = 0; q < C; ++q) *cluster.map_shared_rank(cb + r, q) = v;
+    if (r == 0) {
+      const double rd = (v > kPivTol && isfinite(v)) ? fast_rcp(v) : 0.0;
+      for (int q = 0; q < C; ++q) *cluster.map_shared_rank(rdb, q) = rd;
+    }
+  }
+  cluster.sync();
+  for (int j = 0; j < n; ++j) {
+    const double* col = cb + (size_t)(j % 3) * n;
+    const double rdj = rdb[j % 3];
+    const bool drop = rdj == 0.0;
+    if (tid == 0) piv[j] = col[j];
+    if (j + 1 < n) {
+      // column j+1 of the own rows r >= j+1, then to every CTA
+      double* nxt = cb + (size_t)((j + 1) % 3) * n;
+      const double t = col[j + 1] * rdj;
+      const int lr0 = (j + 1 - rank + C - 1) / C;
+      for (int lr = lr0 + tid; lr < nrows; lr += nt) {
+        const int r = lr * C + rank;
+        double v = Ar[(size_t)lr * n + j + 1];
+        if (!drop) v = fma(-col[r], t, v);
+        Ar[(size_t)lr * n + j + 1] = v;
+        for (int q = 0; q < C; ++q) *cluster.map_shared_rank(nxt + r, q) = v;
+        if (r == j + 1) {
+          const double rd = (v > kPivTol && isfinite(v)) ? fast_rcp(v) : 0.0;
+          for (int q = 0; q < C; ++q) *cluster.map_shared_rank(rdb + (j + 1) % 3, q) = rd;
+        }
+      }
+      asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+    }
+    // the rest of step j on the own rows r >= j+2: columns j+2 .. r
+    if (!drop) {
+      const int lr0 = (j + 2 - rank + C - 1) / C;
+      for (int lr = lr0 + warp; lr < nrows; lr += nwarps) {
+        const int r = lr * C + rank;
+        double* row = Ar + (size_t)lr * n;
+        const double tr = col[r] * rdj;
+        for (int c = j + 2 + lane; c <= r; c += 32) row[c] = fma(-tr, col[c], row[c]);
+      }
+    }
+    __syncthreads();  // own rows complete before the next step's column update reads them
+    if (j + 1 < n) asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+  }
+  // L from the unscaled columns: L_rc = a_rc / sqrt(d_c), L_cc = sqrt(d_c); dropped: 0, 1
+  int nd = 0;
+  for (int c = tid; c < n; c += nt) {
+    const double d = piv[c];
+    const bool dr = !(d > kPivTol) || !isfinite(d);
+    sq[c] = dr ? 1.0 : sqrt(d);
+    rs[c] = dr ? 0.0 : 1.0 / sq[c];
+    if (rank == 0) W.tau[c] = dr ? 1.0 : 0.0;
+    nd += dr ? 1 : 0;
+  }
+  __syncthreads();
+  for (int lr = warp; lr < nrows; lr += nwarps) {
+    const int r = lr * C + rank;
+    for (int c = lane; c < n; c += 32) {
+      const double v = (c < r) ? Ar[(size_t)lr * n + c] * rs[c] : (c == r ? sq[r] : 0.0);
+      W.L[(int64_t)r * n + c] = v;
+    }
+  }
+  if (rank == 0) {
+    __shared__ double red[40];
+    const double ndrop = block_sum((double)nd, red);
+    if (tid == 0) {
+      W.info[0] = (int)ndrop;
+      status[0] = (n - (int)ndrop < k) ? 1 : 0;
     }
   }
   cluster.sync();  // no CTA leaves while another may still address its shared memory
@@ -1413,6 +1577,64 @@ size_t small_sygv_work_doubles(int n, int k) {
   return (size_t)3 * n * n + (size_t)n * k + 4 * (size_t)n + k + 8;
 }
 
+// Launch one of the cluster kernels (k_sygv_chol_c, k_sygv_tridiag_c) as a single cluster
+// of csize CTAs of 256 threads.
+template <typename... KArgs, typename... Args>
+static int launch_sygv_cluster(void (*kern)(KArgs...), int csize, size_t smem, cudaStream_t s, Args... args) {
+  PASE_TRY(ensure_max_smem((const void*)kern, 200 * 1024));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)csize, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  PASE_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+  return PASE_OK;
+}
+
+// Whether this device schedules one cluster of 2 kTriC CTAs of the tridiagonalisation
+// (a non-portable cluster size), asked once per device.
+static bool tri16_available(int device, size_t smem) {
+  static std::mutex mu;
+  static int avail[64];
+  static bool init = false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!init) {
+    for (int& a : avail) a = -1;
+    init = true;
+  }
+  if (device < 0 || device >= 64) return false;
+  if (avail[device] < 0) {
+    int ok = 0;
+    const void* f = (const void*)k_sygv_tridiag_c<2 * kTriC>;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        ensure_max_smem(f, 200 * 1024) == PASE_OK) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2 * kTriC, 1, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2 * kTriC;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_sygv_tridiag_c<2 * kTriC>, &cfg) == cudaSuccess && nc >= 1) ok = 1;
+    }
+    cudaGetLastError();
+    avail[device] = ok;
+  }
+  return avail[device] == 1;
+}
+
 int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,
                double* lam, double* C, int ldc, int* status_dev) {
   if (n <= 0 || k <= 0 || k > n || k > 1024) return fail(PASE_ERR_INVALID_ARG, "small_sygv: bad size");
@@ -1420,12 +1642,18 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   // FP64 pipe of one SM bounds them, so fewer threads (cheaper barriers) can be faster;
   // the autotuner picks per size, at least k (one multisection lane per eigenvalue)
   int thr = 1024;
-  bool cl = n >= kTriClusterMin;  // tridiagonalisation on a cluster of SMs
+  // tridiagonalisation: 0 one CTA, 1 a cluster of kTriC SMs, 2 of 2 kTriC SMs; Cholesky:
+  // 0 one CTA, 1 a cluster of kTriC SMs
+  int tform = n >= kTriClusterMin ? 1 : 0;
+  int cform = n >= kTriClusterMin ? 1 : 0;
   for (int i = 0; i < 3; ++i)
     if (h->sygv_n[i] == n) {
       if (h->sygv_thr[i] >= k) thr = h->sygv_thr[i];
-      if (h->sygv_cl[i] >= 0 && n >= 16) cl = h->sygv_cl[i] != 0;
+      if (h->sygv_cl[i] >= 0 && n >= 16) tform = h->sygv_cl[i];
+      if (h->sygv_ch[i] >= 0 && n >= 16) cform = h->sygv_ch[i];
     }
+  if (h->opt.sygv_tridiag >= 0) tform = n >= 16 ? h->opt.sygv_tridiag : 0;  // fixed by the caller
+  if (h->opt.sygv_cholesky >= 0) cform = n >= 16 ? h->opt.sygv_cholesky : 0;
   if (small_sygv_work_doubles(n, k) > h->w.eigwork_doubles)
     return fail(PASE_ERR_INVALID_ARG, "small_sygv: workspace too small");
   const size_t smem_tri = (size_t)(2 * n + 1024) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
@@ -1449,17 +1677,24 @@ int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const doubl
   const size_t smem_chol_s = (tri + n) * sizeof(double);
   const size_t smem_tri_s = (tri + 2 * n) * sizeof(double) + 1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
   const bool packed = smem_tri_s <= 200 * 1024 && smem_chol_s <= 200 * 1024;
-  if (packed)
+  const size_t smem_chc = chol_cluster_smem(n, kTriC);
+  if (cform == 1 && smem_chc <= 200 * 1024)
+    PASE_TRY(launch_sygv_cluster(k_sygv_chol_c<kTriC>, kTriC, smem_chc, s, n, k, GA, lda, GB, ldb, w, status_dev));
+  else if (packed)
     k_sygv_chol_s<<<1, thr, smem_chol_s, s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   else
     k_sygv_chol<<<1, thr, (size_t)n * sizeof(double), s>>>(n, k, GA, lda, GB, ldb, w, status_dev);
   k_sygv_trsm<<<trsm_grid, 128, smem_trsm, s>>>(n, k, w, 0, stage_l, cpc, status_dev);
   k_sygv_trsm<<<trsm_grid, 128, smem_trsm, s>>>(n, k, w, 1, stage_l, cpc, status_dev);
-  const size_t smem_c = tri_cluster_smem(n);
+  const size_t smem_c = tri_cluster_smem(n, kTriC), smem_c2 = tri_cluster_smem(n, 2 * kTriC);
   const size_t smem_ms = (size_t)1024 * sizeof(int) + (size_t)(2 * n + 2 * k) * sizeof(float);
-  if (cl && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
-    PASE_TRY(ensure_max_smem((const void*)k_sygv_tridiag_c, 200 * 1024));
-    k_sygv_tridiag_c<<<kTriC, 256, smem_c, s>>>(n, k, w, status_dev);
+  if (tform == 2 && (smem_c2 > 200 * 1024 || !tri16_available(h->device, smem_c2))) tform = 1;
+  if (tform >= 1 && smem_c <= 200 * 1024) {  // reduction spread over a cluster of SMs
+    if (tform == 2)
+      PASE_TRY(launch_sygv_cluster(k_sygv_tridiag_c<2 * kTriC>, 2 * kTriC, smem_c2, s, n, k, w,
+                                   (const int*)status_dev));
+    else
+      PASE_TRY(launch_sygv_cluster(k_sygv_tridiag_c<kTriC>, kTriC, smem_c, s, n, k, w, (const int*)status_dev));
     k_sygv_multisect<<<1, thr, smem_ms, s>>>(n, k, w, status_dev);
     h->launches++;
   } else if (packed) {

@@ -178,17 +178,20 @@ void prof_end(pase_ctx* h, int id) {
 }
 
 // ------------------------------------------------------------------ autotuner
-// Threads of the small eigensolver's single-CTA stages (256, 512 or 1024) and the form of
-// its tridiagonalisation (one CTA or a cluster of SMs) for the three sizes the step-(c)
-// block eigensolver uses (n = m, 2m, 3m; k = m): timed on a synthetic Gram pair, once per
-// (n, k) in the process.
+// Threads of the small eigensolver's single-CTA stages (256, 512 or 1024), the form of
+// its tridiagonalisation (one CTA, or a cluster of 8 or 16 SMs) and of its Cholesky
+// factorisation (one CTA or a cluster of 8 SMs) for the three sizes the step-(c) block
+// eigensolver uses (n = m, 2m, 3m; k = m): timed on a synthetic Gram pair, once per (n, k)
+// in the process.
 static int tune_sygv(pase_ctx* h) {
   Work& w = h->w;
   const int m = w.m, m3 = 3 * m;
   const int64_t nc = h->NH + m;
   if (w.aug_dense || nc < m3) return PASE_OK;  // the iterative step (c) does not run
   static std::mutex mu;
-  static std::vector<std::array<int, 4>> cache;  // (n, k, threads, cluster)
+  // (n, k, fixed tridiagonalisation form, fixed Cholesky form; threads, forms chosen)
+  static std::vector<std::array<int, 7>> cache;
+  const int ftri = h->opt.sygv_tridiag, fch = h->opt.sygv_cholesky;
   PASE_TRY(launch_hash_fill(h, nc, m3, m3, 10u, w.S));
   PASE_TRY(launch_hash_fill(h, nc, m3, m3, 11u, w.AS));
   PASE_TRY(ts_gram(h, nc, m3, m3, w.AS, m3, w.AS, m3, w.Gq, m3, true));
@@ -200,28 +203,32 @@ static int tune_sygv(pase_ctx* h) {
   for (int i = 0; i < 3 && rc == PASE_OK; ++i) {
     const int n = (i + 1) * m;
     h->sygv_n[i] = n;
-    int found = 0, found_cl = -1;
+    int found = 0, found_cl = -1, found_ch = -1;
     {
       std::lock_guard<std::mutex> lk(mu);
       for (const auto& c : cache)
-        if (c[0] == n && c[1] == m) {
-          found = c[2];
-          found_cl = c[3];
+        if (c[0] == n && c[1] == m && c[2] == ftri && c[3] == fch) {
+          found = c[4];
+          found_cl = c[5];
+          found_ch = c[6];
         }
     }
     if (found) {
       h->sygv_thr[i] = found;
       h->sygv_cl[i] = found_cl;
+      h->sygv_ch[i] = found_ch;
       continue;
     }
     float best = 1e30f;
-    int best_thr = 1024, best_cl = -1;
-    for (int cand = 0; cand < 6; ++cand) {
+    int best_thr = 1024, best_cl = -1, best_ch = -1;
+    for (int cand = 0; cand < 18; ++cand) {
       const int thr = (cand % 3 == 0) ? 1024 : (cand % 3 == 1 ? 512 : 256);
-      const int cl = cand / 3;
-      if (thr < m || (cl && n < 16)) continue;
+      const int cl = (cand / 3) % 3, ch = cand / 9;
+      if (thr < m || ((cl || ch) && n < 16) || (cl == 2 && n < kTri16Min)) continue;
+      if ((ftri >= 0 && cl != ftri) || (fch >= 0 && ch != fch)) continue;
       h->sygv_thr[i] = thr;
       h->sygv_cl[i] = cl;
+      h->sygv_ch[i] = ch;
       for (int rep = 0; rep < 2 && rc == PASE_OK; ++rep) {
         if (rep == 1) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? PASE_OK : PASE_ERR_CUDA;
         for (int it = 0; it < 2 && rc == PASE_OK; ++it)
@@ -234,22 +241,25 @@ static int tune_sygv(pase_ctx* h) {
         rc = fail(PASE_ERR_CUDA, "tune_sygv: event timing failed");
         break;
       }
+      static const char* tri_form[3] = {"one-CTA", "8-SM cluster", "16-SM cluster"};
       if (h->opt.verbose >= 2)
-        fprintf(stderr, "[pase]   small eigensolver n %d: %d threads, %s tridiagonalisation %.4f ms\n", n, thr,
-                cl ? "cluster" : "one-CTA", ms / 2);
+        fprintf(stderr, "[pase]   small eigensolver n %d: %d threads, %s tridiagonalisation, %s Cholesky %.4f ms\n",
+                n, thr, tri_form[cl], ch ? "8-SM cluster" : "one-CTA", ms / 2);
       if (ms < best) {
         best = ms;
         best_thr = thr;
         best_cl = cl;
+        best_ch = ch;
       }
     }
     h->sygv_thr[i] = best_thr;
     h->sygv_cl[i] = best_cl;
+    h->sygv_ch[i] = best_ch;
     if (h->opt.verbose)
-      fprintf(stderr, "[pase] autotune small eigensolver n %d: %d threads, %s tridiagonalisation\n", n, best_thr,
-              best_cl ? "cluster" : "one-CTA");
+      fprintf(stderr, "[pase] autotune small eigensolver n %d: %d threads, tridiagonalisation form %d, Cholesky "
+              "form %d\n", n, best_thr, best_cl, best_ch);
     std::lock_guard<std::mutex> lk(mu);
-    cache.push_back({n, m, best_thr, best_cl});
+    cache.push_back({n, m, ftri, fch, best_thr, best_cl, best_ch});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1603,6 +1613,8 @@ void pase_default_options(pase_options* o) {
   o->spmm_df64 = 1;
   o->graph_solve = 0;
   o->aug_factor = 1e-4;
+  o->sygv_tridiag = -1;
+  o->sygv_cholesky = -1;
 }
 
 const char* pase_status_string(int code) {
@@ -1638,6 +1650,7 @@ int pase_create(pase_handle* out, const pase_options* opt, void* stream) {
       (o.smoother != PASE_SMOOTHER_JACOBI && o.smoother != PASE_SMOOTHER_LEARNED) ||
       (o.post_solve != 0 && o.post_solve != 1) || (o.graph_solve != 0 && o.graph_solve != 1) ||
       (o.stencil_columns != 0 && o.stencil_columns != 2 && o.stencil_columns != 4) ||
+      o.sygv_tridiag < -1 || o.sygv_tridiag > 2 || o.sygv_cholesky < -1 || o.sygv_cholesky > 1 ||
       o.graph_pass_limit < 0 || !(o.aug_factor > 0.0 && o.aug_factor <= 1.0) ||
       o.aug_transform < PASE_AUG_PLAIN ||
       o.aug_transform > PASE_AUG_PRECOND_BA ||

@@ -288,9 +288,10 @@ struct pase_ctx {
   std::vector<cudaStream_t> cap_streams;
   int64_t body_kernels[pase::kCtlSlots] = {};  // kernels of the body that owns each slot
   int ci_last[pase::kCtlSlots] = {};           // execution counts at the last read
-  // tuned small eigensolver per Rayleigh-Ritz size: threads of its single-CTA stages, and
-  // whether the tridiagonalisation runs on a cluster (-1: by size)
-  int sygv_n[3] = {0, 0, 0}, sygv_thr[3] = {1024, 1024, 1024}, sygv_cl[3] = {-1, -1, -1};
+  // tuned small eigensolver per Rayleigh-Ritz size: threads of its single-CTA stages, the
+  // tridiagonalisation's form (0 one CTA, 1 a cluster of 8 SMs, 2 of 16) and the Cholesky
+  // factorisation's (0 one CTA, 1 a cluster of 8 SMs); -1: by size
+  int sygv_n[3] = {0, 0, 0}, sygv_thr[3] = {1024, 1024, 1024}, sygv_cl[3] = {-1, -1, -1}, sygv_ch[3] = {-1, -1, -1};
   int64_t graph_launches = 0;                  // CUDA graph launches issued
   int64_t replayed = 0;                        // kernels (of `launches`) run inside graph replays
   uint64_t serial = 0;                         // unique id of the handle (batch graph keys)
@@ -390,6 +391,8 @@ int launch_gather_cols(pase_ctx* h, int64_t n, int k, const double* src, int64_t
                        int64_t ldd);
 
 // small dense matrices on one CTA
+// smallest Rayleigh-Ritz size the autotuner tries the 16-SM cluster tridiagonalisation on
+constexpr int kTri16Min = 96;
 int small_sygv(pase_ctx* h, int n, int k, const double* GA, int lda, const double* GB, int ldb,
                double* lam, double* C, int ldc, int* status_dev);
 int small_gemm(pase_ctx* h, int m, int n, int k, double alpha, const double* A, int lda,

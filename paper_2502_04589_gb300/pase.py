@@ -45,7 +45,8 @@ class PaseOptions(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("split_gemm", ctypes.c_int), ("stencil", ctypes.c_int),
                 ("post_solve", ctypes.c_int), ("aug_transform", ctypes.c_int), ("spmm_df64", ctypes.c_int),
                 ("graph_solve", ctypes.c_int), ("graph_pass_limit", ctypes.c_int),
-                ("stencil_columns", ctypes.c_int), ("aug_factor", ctypes.c_double)]
+                ("stencil_columns", ctypes.c_int), ("aug_factor", ctypes.c_double),
+                ("sygv_tridiag", ctypes.c_int), ("sygv_cholesky", ctypes.c_int)]
 
 
 class PaseTrainOptions(ctypes.Structure):

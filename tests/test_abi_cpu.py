@@ -113,3 +113,4 @@ def test_default_options_of_the_later_fields(lib):
     o = P.pase_default_options()
     assert (o.use_graphs, o.autotune, o.smoother, o.split_gemm, o.aug_adaptive) == (1, 1, P.PASE_SMOOTHER_JACOBI, 1, 1)
     assert (o.stencil, o.post_solve, o.aug_transform, o.spmm_df64, o.graph_solve) == (1, 0, P.PASE_AUG_PLAIN, 1, 0)
+    assert (o.graph_pass_limit, o.stencil_columns, o.aug_factor, o.sygv_tridiag, o.sygv_cholesky) == (0, 0, 1e-4, -1, -1)

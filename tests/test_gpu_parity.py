@@ -279,6 +279,16 @@ def test_augmented_eig_parity(which, m, request):
     _augmented_eig_check(request.getfixturevalue(which), m)
 
 
+@pytest.mark.parametrize("tri,chol", [(0, 0), (1, 0), (0, 1), (1, 1), (2, 1), (2, 0)])
+@pytest.mark.parametrize("which,m", [("p2d", 16), ("p3d", 24), ("p3d", 96)])
+def test_augmented_eig_small_eigensolver_forms(which, m, tri, chol, request):
+    """Every form of the Rayleigh-Ritz eigensolver, fixed for all its sizes (m, 2m, 3m):
+    tridiagonalisation on one CTA, a cluster of 8 or of 16 SMs; Cholesky on one CTA or a
+    cluster of 8 SMs.  Late passes soft-lock converged columns, so the Gram matrices carry
+    dropped directions through every form."""
+    _augmented_eig_check(request.getfixturevalue(which), m, sygv_tridiag=tri, sygv_cholesky=chol)
+
+
 @pytest.mark.parametrize("transform", [P.PASE_AUG_PRECOND_A, P.PASE_AUG_PRECOND_B, P.PASE_AUG_PRECOND_BA])
 @pytest.mark.parametrize("which,m", [("p2d", 16), ("p3d", 24)])
 def test_augmented_eig_transform_parity(which, m, transform, request):
@@ -464,6 +474,18 @@ def test_solve_laplace_3d_32_cluster():
     pb = pin.build_problem(3, 32, 8, mg_min=4)
     nev = 10
     rc, st, lam, U = _solve(pb, nev, 1e-8)
+    assert rc == P.PASE_OK, st
+    _check_pairs(pb, lam, U, nev, spectrum.q1_laplace_eigenvalues(3, 32, nev), 1e-8)
+
+
+@pytest.mark.parametrize("precision", [P.PASE_PREC_FP64, P.PASE_PREC_MIXED])
+@pytest.mark.parametrize("tri,chol", [(1, 1), (2, 1)])
+def test_solve_cluster_small_eigensolver(precision, tri, chol):
+    """Whole solves (3D Laplace 32^3, nev 12) with the cluster Cholesky and an 8- or 16-SM
+    tridiagonalisation forced for every Rayleigh-Ritz size, against the closed form."""
+    pb = pin.build_problem(3, 32, 8, mg_min=4)
+    nev = 12
+    rc, st, lam, U = _solve(pb, nev, 1e-8, precision, sygv_tridiag=tri, sygv_cholesky=chol)
     assert rc == P.PASE_OK, st
     _check_pairs(pb, lam, U, nev, spectrum.q1_laplace_eigenvalues(3, 32, nev), 1e-8)
 
