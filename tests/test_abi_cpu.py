@@ -54,6 +54,20 @@ def test_create_without_gpu_reports_error(lib):
     assert e.value.code == -8
 
 
+@pytest.mark.parametrize("field,value", [("sygv_tridiag", 3), ("sygv_tridiag", -2), ("sygv_cholesky", 2),
+                                         ("stencil_columns", 3), ("aug_factor", 0.0), ("omega", 2.0)])
+def test_create_rejects_invalid_options_before_any_device_call(lib, field, value):
+    """Options are validated before the device is touched, so a bad field is reported as an
+    invalid argument on any machine (a valid set on a machine without a GPU is a CUDA
+    error, as above)."""
+    from paper_2502_04589_gb300 import pase as P
+    o = P.pase_default_options()
+    setattr(o, field, value)
+    with pytest.raises(P.PaseError) as e:
+        P.pase_create(o)
+    assert e.value.code == -1  # PASE_ERR_INVALID_ARG
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2502_04589_gb300 import pase as P
     saved = P._lib
